@@ -1,0 +1,224 @@
+/*
+ * sp.h — C ABI of the GB300 (sm_103a) Spatial Pooler library, libsp_gb300.so.
+ *
+ * The library runs the data-parallel hot path of the HTM Spatial Pooler of
+ * Wielgosz & Pietron, "OpenCL-accelerated object classification in video
+ * streams using Spatial Pooler of Hierarchical Temporal Memory":
+ *
+ *   overlap     Alg. 1 (Section 1.1): per column, the number of connected
+ *               potential synapses (permanence >= connect_threshold, fp32)
+ *               whose input bit is 1; zero when below min_overlap, else
+ *               multiplied by the column's boost (one fp32 multiply, as the
+ *               paper's overlap unit does, Section 3 "Hardware architecture");
+ *   inhibition  Alg. 2 (Section 1.1) read as a rank count: a column is active
+ *               iff its overlap is > 0 and fewer than winners_set_size columns
+ *               of its neighbourhood beat it (higher overlap, or equal overlap
+ *               and lower index); the neighbourhood is the whole SP (global)
+ *               or the (2r+1)^2 window on the column grid, clipped at the
+ *               edges (local);
+ *   learning    Section 1.1 (kept on the CPU in the paper; increments of
+ *               Table 2): every potential synapse of an active column moves
+ *               to min(1, p + perm_inc) when its input bit is 1, else to
+ *               max(0, p - perm_dec), each add one fp32 round-to-nearest op.
+ *
+ * A binary frame goes in, the sparse set of active columns comes out
+ * (Section 2, "Processing flow"), in learning or inference mode (Section 4.1).
+ * Results are bit-identical to the plain CPU definition: overlaps are integer
+ * counts, fp32 steps are single round-to-nearest operations (no FMA), and
+ * the winner set is unique under the total order above.
+ *
+ * Input format (Section 4.4 proposes boolean instead of integer input to cut
+ * transfers ~32x): input bit i is bit (i & 31) of 32-bit word i >> 5, LSB
+ * first; a W x H frame is flattened row-major, i = y*W + x.  A frame is
+ * n_words = ceil(W*H / 32) words; unused high bits of the last word are
+ * ignored.  Active-column masks use the same packing over columns,
+ * mask_words = ceil(C / 32) words.
+ *
+ * State: each handle owns its state on the GPU it was created on (the
+ * current CUDA device at sp_create): pools idx[C][S] (uint32), permanences perm[C][S] (fp32), boost[C] (fp32),
+ * the last frame's overlaps, and double-buffered masks/inputs.  State never
+ * returns to the host except through the getters.
+ *
+ * Ordering: a handle is bound to one CUDA stream (its own, or the one passed
+ * to the *_device calls) and is NOT thread-safe; separate handles are
+ * independent.  Compute calls are asynchronous; sp_active_columns, the
+ * getters and sp_sync wait (bounded, see sp_set_timeout_ms) for the work
+ * they read.  Learning of a frame is applied lazily, before the next frame's
+ * overlap on the same pass over the state, or by any getter that reads
+ * permanences; the observable results are those of applying it at the end
+ * of its own frame.
+ *
+ * Buffers: caller buffers are borrowed only for the call, or, for the
+ * asynchronous calls, until the next sp_sync / sp_active_columns / getter /
+ * sp_destroy of that handle.  The library never frees caller memory.
+ *
+ * Errors: every call returns an sp_status; no C++ exception crosses the
+ * ABI.  On error nothing observable changes unless stated.  sp_last_error()
+ * gives a human-readable message for the calling thread's last failure.
+ */
+#ifndef SP_H
+#define SP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(SP_BUILD_LIBRARY)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#define SP_ABI_VERSION 1u
+#define SP_MAX_COLUMNS 16384u        /* per SP instance */
+#define SP_MAX_SYNAPSES 65536u       /* per column */
+#define SP_MAX_INPUT_BITS (1u << 28) /* per frame */
+
+typedef struct sp_handle sp_handle; /* opaque, owned by the library */
+
+typedef enum {
+  SP_OK = 0,
+  SP_EINVAL = 1,   /* invalid argument or configuration */
+  SP_ENOMEM = 2,   /* device or pinned host allocation failed */
+  SP_ECUDA = 3,    /* a CUDA runtime call failed (see sp_last_error) */
+  SP_ETIMEOUT = 4, /* a bounded wait on device work expired */
+  SP_EBUSY = 5,    /* resource in use (e.g. capacity exhausted) */
+  SP_ENOTSUP = 6   /* valid but unsupported combination */
+} sp_status;
+
+enum { SP_POOL_UNIFORM = 0, SP_POOL_WINDOW = 1, SP_POOL_DENSE = 2 };
+enum { SP_INHIBIT_GLOBAL = 0, SP_INHIBIT_LOCAL = 1 };
+
+/* Configuration of one SP (Table 2 names the paper's defaults). */
+typedef struct {
+  uint32_t abi_version;         /* must be SP_ABI_VERSION */
+  uint32_t input_w, input_h;    /* n_in = input_w * input_h bits; h = 1 for flat input */
+  uint32_t num_columns;         /* C */
+  uint32_t col_grid_w, col_grid_h; /* column grid (C = w*h) for windowed pools and
+                                      local inhibition; 0,0 = none */
+  uint32_t synapses_per_column; /* S (= n_in for SP_POOL_DENSE) */
+  uint32_t pool_mode;           /* SP_POOL_* (sp_create only) */
+  uint32_t rf_w, rf_h;          /* receptive-field window for SP_POOL_WINDOW */
+  float connect_threshold;      /* connected iff perm >= threshold (fp32) */
+  float perm_inc, perm_dec;     /* learning steps */
+  float perm_init_lo, perm_init_hi; /* initial permanences U[lo, hi) (sp_create) */
+  uint32_t min_overlap;         /* counts below this are zeroed (Alg. 1) */
+  uint32_t winners_set_size;    /* k of Alg. 2 */
+  uint32_t inhibition;          /* SP_INHIBIT_* */
+  uint32_t local_radius;        /* r: (2r+1)^2 window for SP_INHIBIT_LOCAL */
+  uint64_t seed;                /* pools / permanences for sp_create */
+} sp_config;
+
+/* Sizes of a handle's state and buffers. */
+typedef struct {
+  uint32_t num_columns, synapses_per_column;
+  uint64_t input_bits;
+  uint32_t input_words;  /* ceil(input_bits / 32) */
+  uint32_t mask_words;   /* ceil(num_columns / 32) */
+  uint32_t max_active;   /* upper bound on active columns per frame */
+  int device;            /* CUDA device the state lives on */
+  uint64_t device_bytes; /* device memory held by the handle */
+  uint64_t frames;       /* frames computed so far */
+} sp_info;
+
+/* Fill *cfg with the paper's Table 2 defaults: 2048 columns, 128 synapses,
+ * perm_inc = perm_dec = 0.1, min_overlap 8, winners_set_size 40, initial
+ * permanence 0.21, over a 240 x 134 input (Table 1 frame size) with uniform
+ * pools and global inhibition; connect_threshold 0.2 (not given by the
+ * paper).  Returns SP_EINVAL if cfg is NULL. */
+SP_API sp_status sp_config_init(sp_config* cfg);
+
+/* Create an SP on the current CUDA device, drawing pools and permanences
+ * from cfg->seed (include/sp_synth.h recipes: uniform, windowed or dense
+ * pools; permanences U[perm_init_lo, perm_init_hi)); boosts start at 1.
+ * *out receives the handle (NULL on failure). SP_EINVAL on a bad config,
+ * SP_ENOMEM / SP_ECUDA on allocation failure. */
+SP_API sp_status sp_create(const sp_config* cfg, sp_handle** out);
+
+/* Create an SP from caller state (host arrays, copied as given): idx[C][S]
+ * input indices (each < n_in; ascending rows give the best locality),
+ * perm[C][S] in [0, 1], boost[C] finite and >= 0 (NULL = all 1). */
+SP_API sp_status sp_create_from_state(const sp_config* cfg, const uint32_t* idx,
+                                      const float* perm, const float* boost,
+                                      sp_handle** out);
+
+/* Free the handle and its device state after its pending work (bounded
+ * wait).  NULL-safe. */
+SP_API void sp_destroy(sp_handle* h);
+
+SP_API sp_status sp_get_info(const sp_handle* h, sp_info* out);
+
+/* One frame from host memory (input_words words; pinned memory gives a true
+ * asynchronous copy).  learn != 0 applies the learning rule for this frame.
+ * Asynchronous on the handle's stream. */
+SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn);
+
+/* One frame already on the device (input_words words at d_bits, 4-byte
+ * aligned), enqueued on `stream` (a cudaStream_t; NULL = the handle's own
+ * stream).  The handle then stays on that stream until its next call. */
+SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int learn,
+                                   void* stream);
+
+/* n_frames frames on the device, frame t at d_frames + t * frame_stride_words
+ * (stride >= input_words), in order, all with the same learn flag; one fused
+ * kernel per frame.  If d_active_masks is not NULL, frame t's active set is
+ * written there as mask_words words at d_active_masks + t * mask_words.
+ * Asynchronous on `stream` (NULL = the handle's stream). */
+SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames,
+                                          uint32_t n_frames, uint64_t frame_stride_words,
+                                          int learn, uint32_t* d_active_masks,
+                                          void* stream);
+
+/* n_frames frames from host memory (frame t at h_frames + t * stride words)
+ * with their active masks written to host memory h_active_masks
+ * ([n_frames][mask_words], NULL = not returned).  Copies are staged in
+ * chunks and overlapped with compute on a second stream.  Synchronous:
+ * returns when the masks are in host memory. */
+SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint32_t n_frames,
+                                   uint64_t frame_stride_words, int learn,
+                                   uint32_t* h_active_masks);
+
+/* Wait (bounded) for the last frame and copy its active columns, ascending,
+ * into out[0..n).  If cap < n, nothing is copied, *n is set and SP_EINVAL is
+ * returned. */
+SP_API sp_status sp_active_columns(sp_handle* h, uint32_t* out, uint32_t cap, uint32_t* n);
+
+/* Boosted overlaps of the last frame (C floats, host). */
+SP_API sp_status sp_get_overlaps(sp_handle* h, float* out);
+
+/* Permanences [C][S] (host), in the pool order, after all learning so far. */
+SP_API sp_status sp_get_permanences(sp_handle* h, float* out);
+
+/* Potential pools [C][S] (host). */
+SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out);
+
+/* Boosts [C] (host). */
+SP_API sp_status sp_get_boost(sp_handle* h, float* out);
+
+/* Replace the boosts (host array of C finite values >= 0). */
+SP_API sp_status sp_set_boost(sp_handle* h, const float* boost);
+
+/* Wait (bounded) until all work enqueued on the handle has finished. */
+SP_API sp_status sp_sync(sp_handle* h);
+
+/* Bound, in milliseconds, of every wait of this handle (default 10000;
+ * 0 restores the default).  An expired wait returns SP_ETIMEOUT and leaves
+ * the work running. */
+SP_API sp_status sp_set_timeout_ms(sp_handle* h, uint32_t ms);
+
+/* Number of kernels this library has launched in the calling process. */
+SP_API uint64_t sp_kernel_launch_count(void);
+
+SP_API const char* sp_status_str(sp_status s);
+
+/* Message of the calling thread's last failing call ("" if none). */
+SP_API const char* sp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP_H */

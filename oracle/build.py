@@ -1,13 +1,14 @@
-"""Build the CPU oracle (test infrastructure only) into oracle/_lib/.
+"""Build the CPU oracle (test infrastructure only) into oracle/_lib/<arch>/.
 
 The oracle is plain C++ compiled with -O2 -ffp-contract=off (no FMA
 contraction, no fast-math) so that its fp32 steps round exactly as written.
 """
 import os
+import platform
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_DIR = os.path.join(HERE, "_lib")
+LIB_DIR = os.path.join(HERE, "_lib", platform.machine())
 LIB_PATH = os.path.join(LIB_DIR, "libsp_oracle.so")
 SOURCES = [os.path.join(HERE, "sp_oracle.cpp")]
 HEADERS = [os.path.join(HERE, "sp_oracle.h")]

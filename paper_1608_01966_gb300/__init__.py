@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) Spatial Pooler hot path of Wielgosz & Pietron's
+OpenCL-accelerated HTM video classifier: overlap (Alg. 1), inhibition
+(Alg. 2) and winner-column permanence learning, as CUDA kernels behind the C
+ABI in include/sp.h.  This package holds the ctypes binding, the in-tree
+build and the seeded input generators."""
+from ._binding import (  # noqa: F401
+    SP_ABI_VERSION, SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL, SP_MAX_COLUMNS, SP_POOL_DENSE,
+    SP_POOL_UNIFORM, SP_POOL_WINDOW, SpConfig, SpError, SpatialPooler, lib, masks_to_dense,
+    sp_active_columns, sp_compute, sp_compute_device, sp_compute_frames,
+    sp_compute_frames_device, sp_config_init, sp_create, sp_create_from_state, sp_destroy,
+    sp_get_boost, sp_get_info, sp_get_overlaps, sp_get_permanences, sp_get_pool,
+    sp_kernel_launch_count, sp_last_error, sp_set_boost, sp_set_timeout_ms, sp_status_str,
+    sp_sync,
+)

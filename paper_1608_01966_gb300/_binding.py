@@ -1,0 +1,273 @@
+"""ctypes binding of include/sp.h (libsp_gb300.so), same names as the C ABI.
+
+Argument marshalling only: every step of the Spatial Pooler runs in the CUDA
+library.  Host arrays are numpy; device buffers are passed as integer
+addresses or as anything with ``data_ptr()`` (a torch CUDA tensor), streams as
+integer ``cudaStream_t`` handles or torch streams.  A failing call raises
+SpError carrying the status and the library's message.  There is no fallback:
+if the library cannot be built or loaded, every call raises.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+SP_ABI_VERSION = 1
+SP_MAX_COLUMNS = 16384
+SP_POOL_UNIFORM, SP_POOL_WINDOW, SP_POOL_DENSE = 0, 1, 2
+SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL = 0, 1
+STATUS = {0: "SP_OK", 1: "SP_EINVAL", 2: "SP_ENOMEM", 3: "SP_ECUDA", 4: "SP_ETIMEOUT",
+          5: "SP_EBUSY", 6: "SP_ENOTSUP"}
+
+
+class SpError(RuntimeError):
+    def __init__(self, status, where, message):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class SpConfig(ct.Structure):
+    _fields_ = [
+        ("abi_version", ct.c_uint32), ("input_w", ct.c_uint32), ("input_h", ct.c_uint32),
+        ("num_columns", ct.c_uint32), ("col_grid_w", ct.c_uint32), ("col_grid_h", ct.c_uint32),
+        ("synapses_per_column", ct.c_uint32), ("pool_mode", ct.c_uint32),
+        ("rf_w", ct.c_uint32), ("rf_h", ct.c_uint32), ("connect_threshold", ct.c_float),
+        ("perm_inc", ct.c_float), ("perm_dec", ct.c_float), ("perm_init_lo", ct.c_float),
+        ("perm_init_hi", ct.c_float), ("min_overlap", ct.c_uint32),
+        ("winners_set_size", ct.c_uint32), ("inhibition", ct.c_uint32),
+        ("local_radius", ct.c_uint32), ("seed", ct.c_uint64),
+    ]
+
+
+class SpInfo(ct.Structure):
+    _fields_ = [
+        ("num_columns", ct.c_uint32), ("synapses_per_column", ct.c_uint32),
+        ("input_bits", ct.c_uint64), ("input_words", ct.c_uint32), ("mask_words", ct.c_uint32),
+        ("max_active", ct.c_uint32), ("device", ct.c_int), ("device_bytes", ct.c_uint64),
+        ("frames", ct.c_uint64),
+    ]
+
+
+_lib = None
+_u32p = ct.POINTER(ct.c_uint32)
+_f32p = ct.POINTER(ct.c_float)
+
+
+def lib():
+    """Load libsp_gb300.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _b
+        path = _b.build_sp() if os.environ.get("SP_NO_BUILD") != "1" else _b.SP_LIB
+        L = ct.CDLL(path)
+        L.sp_status_str.restype = ct.c_char_p
+        L.sp_last_error.restype = ct.c_char_p
+        L.sp_kernel_launch_count.restype = ct.c_uint64
+        L.sp_destroy.restype = None
+        vp = ct.c_void_p
+        L.sp_create.argtypes = [ct.POINTER(SpConfig), ct.POINTER(vp)]
+        L.sp_create_from_state.argtypes = [ct.POINTER(SpConfig), _u32p, _f32p, _f32p,
+                                           ct.POINTER(vp)]
+        L.sp_destroy.argtypes = [vp]
+        L.sp_get_info.argtypes = [vp, ct.POINTER(SpInfo)]
+        L.sp_compute.argtypes = [vp, _u32p, ct.c_int]
+        L.sp_compute_device.argtypes = [vp, vp, ct.c_int, vp]
+        L.sp_compute_frames_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, ct.c_int, vp, vp]
+        L.sp_compute_frames.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p]
+        L.sp_active_columns.argtypes = [vp, _u32p, ct.c_uint32, _u32p]
+        L.sp_get_overlaps.argtypes = [vp, _f32p]
+        L.sp_get_permanences.argtypes = [vp, _f32p]
+        L.sp_get_pool.argtypes = [vp, _u32p]
+        L.sp_get_boost.argtypes = [vp, _f32p]
+        L.sp_set_boost.argtypes = [vp, _f32p]
+        L.sp_sync.argtypes = [vp]
+        L.sp_set_timeout_ms.argtypes = [vp, ct.c_uint32]
+        L.sp_status_str.argtypes = [ct.c_int]
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SpError(rc, where, lib().sp_last_error().decode())
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "cuda_stream"):
+        return x.cuda_stream
+    return int(x)
+
+
+def _np_u32(a):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return a, a.ctypes.data_as(_u32p)
+
+
+def _np_f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_f32p)
+
+
+def sp_config_init(**overrides):
+    cfg = SpConfig()
+    _check(lib().sp_config_init(ct.byref(cfg)), "sp_config_init")
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def sp_create(cfg):
+    h = ct.c_void_p()
+    _check(lib().sp_create(ct.byref(cfg), ct.byref(h)), "sp_create")
+    return h
+
+
+def sp_create_from_state(cfg, idx, perm, boost=None):
+    idx, pi = _np_u32(idx)
+    perm, pp = _np_f32(perm)
+    pb = None
+    if boost is not None:
+        boost, pb = _np_f32(boost)
+    h = ct.c_void_p()
+    _check(lib().sp_create_from_state(ct.byref(cfg), pi, pp, pb, ct.byref(h)),
+           "sp_create_from_state")
+    return h
+
+
+def sp_destroy(h):
+    lib().sp_destroy(h)
+
+
+def sp_get_info(h):
+    info = SpInfo()
+    _check(lib().sp_get_info(h, ct.byref(info)), "sp_get_info")
+    return {f: getattr(info, f) for f, _ in SpInfo._fields_}
+
+
+def sp_compute(h, input_bits, learn):
+    a, p = _np_u32(input_bits)
+    _check(lib().sp_compute(h, p, 1 if learn else 0), "sp_compute")
+    return a  # keep alive until the next sync
+
+
+def sp_compute_device(h, d_bits, learn, stream=None):
+    _check(lib().sp_compute_device(h, _addr(d_bits), 1 if learn else 0, _addr(stream)),
+           "sp_compute_device")
+
+
+def sp_compute_frames_device(h, d_frames, n_frames, stride_words, learn, d_active_masks=None,
+                             stream=None):
+    _check(lib().sp_compute_frames_device(h, _addr(d_frames), n_frames, stride_words,
+                                          1 if learn else 0, _addr(d_active_masks),
+                                          _addr(stream)), "sp_compute_frames_device")
+
+
+def sp_compute_frames(h, frames, learn, masks_out=None):
+    """frames: uint32 [n][stride] host array (pinned memory overlaps the copies);
+    masks_out: uint32 [n][mask_words] host array or None."""
+    if frames.dtype != np.uint32 or frames.ndim != 2 or not frames.flags.c_contiguous:
+        raise ValueError("frames must be a C-contiguous uint32 [n][stride] array")
+    pm = None
+    if masks_out is not None:
+        if masks_out.dtype != np.uint32 or not masks_out.flags.c_contiguous:
+            raise ValueError("masks_out must be a C-contiguous uint32 array")
+        pm = masks_out.ctypes.data_as(_u32p)
+    _check(lib().sp_compute_frames(h, frames.ctypes.data_as(_u32p), frames.shape[0],
+                                   frames.shape[1], 1 if learn else 0, pm), "sp_compute_frames")
+    return masks_out
+
+
+def sp_active_columns(h, cap=None):
+    if cap is None:
+        cap = sp_get_info(h)["max_active"]
+    out = np.zeros(max(cap, 1), np.uint32)
+    n = ct.c_uint32()
+    _check(lib().sp_active_columns(h, out.ctypes.data_as(_u32p), cap, ct.byref(n)),
+           "sp_active_columns")
+    return out[: n.value].copy()
+
+
+def _getter(name, dtype, shape_fn):
+    def get(h):
+        info = sp_get_info(h)
+        out = np.empty(shape_fn(info), dtype)
+        ptr = out.ctypes.data_as(_f32p if dtype == np.float32 else _u32p)
+        _check(getattr(lib(), name)(h, ptr), name)
+        return out
+    get.__name__ = name
+    return get
+
+
+sp_get_overlaps = _getter("sp_get_overlaps", np.float32, lambda i: (i["num_columns"],))
+sp_get_permanences = _getter("sp_get_permanences", np.float32,
+                             lambda i: (i["num_columns"], i["synapses_per_column"]))
+sp_get_pool = _getter("sp_get_pool", np.uint32,
+                      lambda i: (i["num_columns"], i["synapses_per_column"]))
+sp_get_boost = _getter("sp_get_boost", np.float32, lambda i: (i["num_columns"],))
+
+
+def sp_set_boost(h, boost):
+    b, p = _np_f32(boost)
+    _check(lib().sp_set_boost(h, p), "sp_set_boost")
+
+
+def sp_sync(h):
+    _check(lib().sp_sync(h), "sp_sync")
+
+
+def sp_set_timeout_ms(h, ms):
+    _check(lib().sp_set_timeout_ms(h, ms), "sp_set_timeout_ms")
+
+
+def sp_kernel_launch_count():
+    return lib().sp_kernel_launch_count()
+
+
+def sp_status_str(s):
+    return lib().sp_status_str(s).decode()
+
+
+def sp_last_error():
+    return lib().sp_last_error().decode()
+
+
+def masks_to_dense(masks, C):
+    """uint32 [..., mask_words] packed masks -> uint8 [..., C] (host helper)."""
+    m = np.ascontiguousarray(masks, dtype="<u4")
+    b = np.unpackbits(m.view(np.uint8), axis=-1, bitorder="little")
+    return b[..., :C]
+
+
+class SpatialPooler:
+    """Owner of one sp_handle (destroyed with the object)."""
+
+    def __init__(self, cfg=None, state=None, **overrides):
+        self.cfg = cfg if cfg is not None else sp_config_init(**overrides)
+        if state is None:
+            self.h = sp_create(self.cfg)
+        else:
+            self.h = sp_create_from_state(self.cfg, *state)
+        self.info = sp_get_info(self.h)
+        self._keep = None
+
+    def compute(self, input_bits, learn):
+        self._keep = sp_compute(self.h, input_bits, learn)
+        return self
+
+    def active_columns(self):
+        return sp_active_columns(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            sp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

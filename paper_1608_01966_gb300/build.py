@@ -6,19 +6,21 @@
                     one round-to-nearest op).
 
 Objects are compiled in parallel and cached by modification time under
-_build/; the shared objects land in _lib/.  Both directories are ignored by
+_build/<arch>/; the shared objects land in _lib/<arch>/.  Both directories are ignored by
 git.  Set SP_NVCC_EXTRA for extra nvcc flags.
 """
 import concurrent.futures as cf
 import os
+import platform
 import shlex
 import subprocess
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
-LIB_DIR = os.path.join(PKG, "_lib")
-BUILD_DIR = os.path.join(PKG, "_build")
+# per-architecture output folders: the same tree is built on x86 and Arm hosts
+LIB_DIR = os.path.join(PKG, "_lib", platform.machine())
+BUILD_DIR = os.path.join(PKG, "_build", platform.machine())
 CSRC = os.path.join(PKG, "csrc")
 SYNTH_SRC = os.path.join(PKG, "synth", "synth.c")
 
@@ -29,7 +31,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fvisibility=hidden"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler",
-                     "-fPIC,-fvisibility=hidden,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
+                     "-fPIC,-fvisibility=hidden,-ffp-contract=off", "-DSP_BUILD_LIBRARY",
+                     "-I", INCLUDE, "-I", CSRC]
 
 
 def _headers():
@@ -82,7 +85,8 @@ def build_sp(force=False, jobs=None):
     synth_obj = os.path.join(BUILD_DIR, "synth.c.o")
     objs.append(synth_obj)
     if force or _newer(synth_obj, [SYNTH_SRC, os.path.join(INCLUDE, "sp_synth.h")]):
-        jobs_list.append(["gcc", "-std=c99"] + CFLAGS + ["-c", SYNTH_SRC, "-o", synth_obj])
+        jobs_list.append(["gcc", "-std=c99", "-DSP_SYNTH_HIDDEN"] + CFLAGS
+                         + ["-c", SYNTH_SRC, "-o", synth_obj])
     if jobs_list:
         with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
             list(ex.map(_run, jobs_list))

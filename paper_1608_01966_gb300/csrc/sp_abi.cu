@@ -1,0 +1,660 @@
+// Host runtime behind include/sp.h: handle state on the device, stream
+// ordering, pinned staging, bounded waits and argument validation.
+//
+// Device layout of one handle (a single cudaMalloc, every part 256-byte
+// aligned): idx[C][S] u32 | perm[C][S] f32 | boost[C] | ov[C] |
+// xsave[2][n_words] | mask[2][mask_words] | result[1 + C] | counter.
+// The double-buffered input copies and winner masks carry one frame's
+// learning over to the next frame's kernel (deferred learning).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/sp.h"
+#include "../../include/sp_synth.h"
+#include "sp_kernels.cuh"
+
+namespace sp {
+extern std::atomic<uint64_t> g_launches;
+}
+
+namespace {
+
+thread_local std::string t_last_error;
+
+sp_status fail(sp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return s;
+}
+
+#define SP_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+uint32_t default_timeout_ms() {
+  const char* s = std::getenv("SP_TIMEOUT_MS");
+  if (s && *s) {
+    long v = std::strtol(s, nullptr, 10);
+    if (v > 0) return (uint32_t)v;
+  }
+  return 10000u;
+}
+
+// Make `dev` current for the scope and restore the caller's device after.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
+
+constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
+constexpr int kSlots = 2;
+
+}  // namespace
+
+struct sp_handle {
+  sp_config cfg{};
+  int device = 0;
+  uint32_t C = 0, S = 0, n_words = 0, mask_words = 0, max_active = 0;
+  uint64_t n_in = 0;
+  void* d_block = nullptr;
+  size_t device_bytes = 0;
+  uint32_t* d_idx = nullptr;
+  float* d_perm = nullptr;
+  float* d_boost = nullptr;
+  float* d_ov = nullptr;
+  uint32_t* d_xsave[2] = {nullptr, nullptr};
+  uint32_t* d_mask[2] = {nullptr, nullptr};
+  uint32_t* d_result = nullptr;
+  uint32_t* d_counter = nullptr;
+  uint32_t* h_result = nullptr;  // pinned [1 + C]
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;  // stream of the last call
+  cudaEvent_t ev_switch = nullptr;
+  cudaEvent_t ev_wait = nullptr;
+  int cur = 0;
+  bool pending = false;  // the previous frame's learning is not applied yet
+  uint64_t frames = 0;
+  uint32_t timeout_ms = 10000;
+  int grid = 1;
+  // sp_compute_frames staging (allocated on first use)
+  uint32_t* d_stage = nullptr;   // [kSlots][kChunkFrames][n_words]
+  uint32_t* d_mstage = nullptr;  // [kSlots][kChunkFrames][mask_words]
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
+};
+
+namespace {
+
+sp_status validate_config(const sp_config* c) {
+  if (!c) return fail(SP_EINVAL, "config is NULL");
+  if (c->abi_version != SP_ABI_VERSION)
+    return fail(SP_EINVAL, "abi_version %u, library is %u", c->abi_version, SP_ABI_VERSION);
+  const uint64_t n_in = (uint64_t)c->input_w * c->input_h;
+  if (n_in == 0 || n_in > SP_MAX_INPUT_BITS) return fail(SP_EINVAL, "input size %llu", (unsigned long long)n_in);
+  if (c->num_columns == 0 || c->num_columns > SP_MAX_COLUMNS)
+    return fail(SP_EINVAL, "num_columns %u not in [1, %u]", c->num_columns, SP_MAX_COLUMNS);
+  if (c->synapses_per_column == 0 || c->synapses_per_column > SP_MAX_SYNAPSES)
+    return fail(SP_EINVAL, "synapses_per_column %u not in [1, %u]", c->synapses_per_column,
+                SP_MAX_SYNAPSES);
+  if ((uint64_t)c->num_columns * c->synapses_per_column > (1ull << 31))
+    return fail(SP_EINVAL, "C*S too large");
+  if (!std::isfinite(c->connect_threshold)) return fail(SP_EINVAL, "connect_threshold not finite");
+  if (!(c->perm_inc >= 0.0f) || !(c->perm_dec >= 0.0f) || !std::isfinite(c->perm_inc) ||
+      !std::isfinite(c->perm_dec))
+    return fail(SP_EINVAL, "perm_inc / perm_dec must be finite and >= 0");
+  if (c->inhibition > SP_INHIBIT_LOCAL) return fail(SP_EINVAL, "inhibition %u", c->inhibition);
+  const bool grid = c->col_grid_w != 0 || c->col_grid_h != 0;
+  if (grid && (uint64_t)c->col_grid_w * c->col_grid_h != c->num_columns)
+    return fail(SP_EINVAL, "col_grid %ux%u != num_columns %u", c->col_grid_w, c->col_grid_h,
+                c->num_columns);
+  if (c->inhibition == SP_INHIBIT_LOCAL && !grid)
+    return fail(SP_EINVAL, "local inhibition needs a column grid");
+  return SP_OK;
+}
+
+sp_status validate_seeded(const sp_config* c) {
+  const uint64_t n_in = (uint64_t)c->input_w * c->input_h;
+  if (!(c->perm_init_lo >= 0.0f && c->perm_init_lo <= c->perm_init_hi && c->perm_init_hi <= 1.0f))
+    return fail(SP_EINVAL, "perm_init range [%g, %g] not inside [0, 1]", c->perm_init_lo,
+                c->perm_init_hi);
+  switch (c->pool_mode) {
+    case SP_POOL_UNIFORM:
+      if (c->synapses_per_column > n_in) return fail(SP_EINVAL, "S > n_in");
+      return SP_OK;
+    case SP_POOL_WINDOW:
+      if (c->col_grid_w == 0) return fail(SP_EINVAL, "windowed pools need a column grid");
+      if (c->rf_w == 0 || c->rf_h == 0 || c->rf_w > c->input_w || c->rf_h > c->input_h)
+        return fail(SP_EINVAL, "receptive field %ux%u does not fit the %ux%u input", c->rf_w,
+                    c->rf_h, c->input_w, c->input_h);
+      if ((uint64_t)c->rf_w * c->rf_h < c->synapses_per_column)
+        return fail(SP_EINVAL, "S larger than the receptive field");
+      return SP_OK;
+    case SP_POOL_DENSE:
+      if (c->synapses_per_column != n_in) return fail(SP_EINVAL, "dense pools need S == n_in");
+      return SP_OK;
+    default:
+      return fail(SP_EINVAL, "pool_mode %u", c->pool_mode);
+  }
+}
+
+void free_handle(sp_handle* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->own_stream) cudaStreamSynchronize(h->own_stream);
+  if (h->s_in) cudaStreamSynchronize(h->s_in);
+  if (h->s_out) cudaStreamSynchronize(h->s_out);
+  for (int i = 0; i < kSlots; ++i) {
+    if (h->ev_h2d[i]) cudaEventDestroy(h->ev_h2d[i]);
+    if (h->ev_comp[i]) cudaEventDestroy(h->ev_comp[i]);
+    if (h->ev_d2h[i]) cudaEventDestroy(h->ev_d2h[i]);
+  }
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
+  if (h->d_stage) cudaFree(h->d_stage);
+  if (h->d_mstage) cudaFree(h->d_mstage);
+  if (h->ev_switch) cudaEventDestroy(h->ev_switch);
+  if (h->ev_wait) cudaEventDestroy(h->ev_wait);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->d_block) cudaFree(h->d_block);
+  delete h;
+}
+
+// Allocate the device block, streams and events; copy idx/perm/boost.
+sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, const float* perm,
+                      const float* boost) {
+  h->cfg = *cfg;
+  h->C = cfg->num_columns;
+  h->S = cfg->synapses_per_column;
+  h->n_in = (uint64_t)cfg->input_w * cfg->input_h;
+  h->n_words = (uint32_t)((h->n_in + 31) / 32);
+  h->mask_words = (h->C + 31) / 32;
+  h->max_active = cfg->inhibition == SP_INHIBIT_GLOBAL
+                      ? (cfg->winners_set_size < h->C ? cfg->winners_set_size : h->C)
+                      : h->C;
+  h->timeout_ms = default_timeout_ms();
+  SP_CUDA(cudaGetDevice(&h->device));
+  SP_CUDA(sp::kernels_init());
+  const size_t CS = (size_t)h->C * h->S;
+  size_t off[9];
+  size_t total = 0;
+  const size_t sizes[9] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
+                           (size_t)h->n_words * 4 * 2, (size_t)h->mask_words * 4 * 2,
+                           ((size_t)h->C + 1) * 4, 4, 0};
+  for (int i = 0; i < 9; ++i) {
+    off[i] = total;
+    total += align256(sizes[i]);
+  }
+  SP_CUDA(cudaMalloc(&h->d_block, total));
+  h->device_bytes = total;
+  char* b = static_cast<char*>(h->d_block);
+  h->d_idx = reinterpret_cast<uint32_t*>(b + off[0]);
+  h->d_perm = reinterpret_cast<float*>(b + off[1]);
+  h->d_boost = reinterpret_cast<float*>(b + off[2]);
+  h->d_ov = reinterpret_cast<float*>(b + off[3]);
+  h->d_xsave[0] = reinterpret_cast<uint32_t*>(b + off[4]);
+  h->d_xsave[1] = h->d_xsave[0] + h->n_words;
+  h->d_mask[0] = reinterpret_cast<uint32_t*>(b + off[5]);
+  h->d_mask[1] = h->d_mask[0] + h->mask_words;
+  h->d_result = reinterpret_cast<uint32_t*>(b + off[6]);
+  h->d_counter = reinterpret_cast<uint32_t*>(b + off[7]);
+  SP_CUDA(cudaMallocHost(&h->h_result, ((size_t)h->C + 1) * 4));
+  SP_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+  h->stream = h->own_stream;
+  SP_CUDA(cudaEventCreateWithFlags(&h->ev_switch, cudaEventDisableTiming));
+  SP_CUDA(cudaEventCreateWithFlags(&h->ev_wait, cudaEventDisableTiming));
+  SP_CUDA(cudaMemsetAsync(h->d_block, 0, total, h->stream));
+  SP_CUDA(cudaMemcpyAsync(h->d_idx, idx, CS * 4, cudaMemcpyHostToDevice, h->stream));
+  SP_CUDA(cudaMemcpyAsync(h->d_perm, perm, CS * 4, cudaMemcpyHostToDevice, h->stream));
+  std::vector<float> ones;
+  if (!boost) {
+    ones.assign(h->C, 1.0f);
+    boost = ones.data();
+  }
+  SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
+  SP_CUDA(cudaStreamSynchronize(h->stream));
+  h->grid = sp::step_grid(h->C);
+  return SP_OK;
+}
+
+// Bounded wait for everything enqueued so far on the handle's stream.
+sp_status wait_handle(sp_handle* h) {
+  SP_CUDA(cudaEventRecord(h->ev_wait, h->stream));
+  const auto deadline =
+      std::chrono::steady_clock::now() + std::chrono::milliseconds(h->timeout_ms);
+  for (uint32_t spin = 0;; ++spin) {
+    const cudaError_t e = cudaEventQuery(h->ev_wait);
+    if (e == cudaSuccess) return SP_OK;
+    if (e != cudaErrorNotReady)
+      return fail(SP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+    if (std::chrono::steady_clock::now() > deadline)
+      return fail(SP_ETIMEOUT, "wait exceeded %u ms", h->timeout_ms);
+    if (spin < 2000)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+sp_status bounded_stream_wait(cudaStream_t s, cudaEvent_t ev, uint32_t timeout_ms) {
+  SP_CUDA(cudaEventRecord(ev, s));
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (uint32_t spin = 0;; ++spin) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return SP_OK;
+    if (e != cudaErrorNotReady)
+      return fail(SP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+    if (std::chrono::steady_clock::now() > deadline)
+      return fail(SP_ETIMEOUT, "wait exceeded %u ms", timeout_ms);
+    if (spin < 2000)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// Order the handle's work on stream s after everything enqueued before.
+sp_status use_stream(sp_handle* h, cudaStream_t s) {
+  if (!s) s = h->own_stream;
+  if (s != h->stream) {
+    SP_CUDA(cudaEventRecord(h->ev_switch, h->stream));
+    SP_CUDA(cudaStreamWaitEvent(s, h->ev_switch, 0));
+    h->stream = s;
+  }
+  return SP_OK;
+}
+
+sp::StepArgs base_args(const sp_handle* h) {
+  sp::StepArgs a{};
+  a.idx = h->d_idx;
+  a.perm = h->d_perm;
+  a.boost = h->d_boost;
+  a.ov = h->d_ov;
+  a.result = h->d_result;
+  a.counter = h->d_counter;
+  a.C = h->C;
+  a.S = h->S;
+  a.n_words = h->n_words;
+  a.mask_words = h->mask_words;
+  a.thr = h->cfg.connect_threshold;
+  a.inc = h->cfg.perm_inc;
+  a.dec = h->cfg.perm_dec;
+  a.min_overlap = h->cfg.min_overlap;
+  a.k = h->cfg.winners_set_size;
+  a.inhibition = h->cfg.inhibition;
+  a.gw = h->cfg.col_grid_w;
+  a.gh = h->cfg.col_grid_h;
+  a.radius = h->cfg.local_radius;
+  return a;
+}
+
+// Enqueue one frame: x is this frame's input (device); x_prev the previous
+// frame's (used iff learning is pending); x_save, if set, receives a copy of
+// x for the next frame's learning.
+sp_status enqueue_frame(sp_handle* h, const uint32_t* x, const uint32_t* x_prev,
+                        uint32_t* x_save, int learn, uint32_t* mask_copy) {
+  sp::StepArgs a = base_args(h);
+  const int cur = h->cur;
+  a.x = x;
+  if (h->pending) {
+    a.x_prev = x_prev;
+    a.mask_prev = h->d_mask[cur ^ 1];
+  }
+  a.x_save = x_save;
+  a.mask_out = h->d_mask[cur];
+  a.mask_copy = mask_copy;
+  SP_CUDA(sp::launch_step(a, h->grid, h->stream));
+  h->pending = learn != 0;
+  h->cur = cur ^ 1;
+  h->frames++;
+  return SP_OK;
+}
+
+// Apply pending learning now (before reading permanences).
+sp_status flush_learning(sp_handle* h) {
+  if (!h->pending) return SP_OK;
+  sp::LearnArgs l{};
+  l.idx = h->d_idx;
+  l.perm = h->d_perm;
+  l.x = h->d_xsave[h->cur ^ 1];
+  l.mask = h->d_mask[h->cur ^ 1];
+  l.C = h->C;
+  l.S = h->S;
+  l.inc = h->cfg.perm_inc;
+  l.dec = h->cfg.perm_dec;
+  SP_CUDA(sp::launch_learn(l, h->stream));
+  h->pending = false;
+  return SP_OK;
+}
+
+bool finite_nonneg(const float* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!(v[i] >= 0.0f) || std::isinf(v[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+SP_API sp_status sp_config_init(sp_config* cfg) {
+  if (!cfg) return fail(SP_EINVAL, "cfg is NULL");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->abi_version = SP_ABI_VERSION;
+  cfg->input_w = 240;
+  cfg->input_h = 134;
+  cfg->num_columns = 2048;
+  cfg->synapses_per_column = 128;
+  cfg->pool_mode = SP_POOL_UNIFORM;
+  cfg->connect_threshold = 0.2f;
+  cfg->perm_inc = 0.1f;
+  cfg->perm_dec = 0.1f;
+  cfg->perm_init_lo = 0.21f;
+  cfg->perm_init_hi = 0.21f;
+  cfg->min_overlap = 8;
+  cfg->winners_set_size = 40;
+  cfg->inhibition = SP_INHIBIT_GLOBAL;
+  cfg->seed = 1;
+  return SP_OK;
+}
+
+SP_API sp_status sp_create(const sp_config* cfg, sp_handle** out) {
+  if (!out) return fail(SP_EINVAL, "out is NULL");
+  *out = nullptr;
+  sp_status s = validate_config(cfg);
+  if (s != SP_OK) return s;
+  if ((s = validate_seeded(cfg)) != SP_OK) return s;
+  const uint32_t C = cfg->num_columns, S = cfg->synapses_per_column;
+  const uint64_t n_in = (uint64_t)cfg->input_w * cfg->input_h;
+  std::vector<uint32_t> idx((size_t)C * S);
+  std::vector<float> perm((size_t)C * S);
+  const uint64_t pool_seed = synth_derive_seed(cfg->seed, SYNTH_PURPOSE_POOL, 0);
+  const uint64_t perm_seed = synth_derive_seed(cfg->seed, SYNTH_PURPOSE_PERM, 0);
+  int rc = -1;
+  if (cfg->pool_mode == SP_POOL_UNIFORM) {
+    std::vector<uint32_t> scratch(n_in);
+    rc = synth_pool_uniform(pool_seed, C, S, (uint32_t)n_in, idx.data(), scratch.data());
+  } else if (cfg->pool_mode == SP_POOL_WINDOW) {
+    std::vector<uint32_t> scratch((size_t)cfg->rf_w * cfg->rf_h);
+    rc = synth_pool_window(pool_seed, cfg->col_grid_w, cfg->col_grid_h, cfg->input_w,
+                           cfg->input_h, cfg->rf_w, cfg->rf_h, S, idx.data(), scratch.data());
+  } else {
+    rc = synth_pool_dense(C, (uint32_t)n_in, idx.data());
+  }
+  if (rc != 0) return fail(SP_EINVAL, "pool generation rejected the configuration");
+  if (synth_perm_uniform(perm_seed, (uint64_t)C * S, cfg->perm_init_lo, cfg->perm_init_hi,
+                         perm.data()) != 0)
+    return fail(SP_EINVAL, "permanence generation rejected the configuration");
+  sp_handle* h = new (std::nothrow) sp_handle();
+  if (!h) return fail(SP_ENOMEM, "host allocation");
+  s = init_handle(h, cfg, idx.data(), perm.data(), nullptr);
+  if (s != SP_OK) {
+    free_handle(h);
+    return s;
+  }
+  *out = h;
+  return SP_OK;
+}
+
+SP_API sp_status sp_create_from_state(const sp_config* cfg, const uint32_t* idx, const float* perm,
+                                      const float* boost, sp_handle** out) {
+  if (!out) return fail(SP_EINVAL, "out is NULL");
+  *out = nullptr;
+  sp_status s = validate_config(cfg);
+  if (s != SP_OK) return s;
+  if (!idx || !perm) return fail(SP_EINVAL, "idx / perm is NULL");
+  const size_t CS = (size_t)cfg->num_columns * cfg->synapses_per_column;
+  const uint64_t n_in = (uint64_t)cfg->input_w * cfg->input_h;
+  for (size_t i = 0; i < CS; ++i) {
+    if (idx[i] >= n_in) return fail(SP_EINVAL, "idx[%zu] = %u >= n_in %llu", i, idx[i], (unsigned long long)n_in);
+    if (!(perm[i] >= 0.0f && perm[i] <= 1.0f)) return fail(SP_EINVAL, "perm[%zu] not in [0, 1]", i);
+  }
+  if (boost && !finite_nonneg(boost, cfg->num_columns))
+    return fail(SP_EINVAL, "boost must be finite and >= 0");
+  sp_handle* h = new (std::nothrow) sp_handle();
+  if (!h) return fail(SP_ENOMEM, "host allocation");
+  s = init_handle(h, cfg, idx, perm, boost);
+  if (s != SP_OK) {
+    free_handle(h);
+    return s;
+  }
+  *out = h;
+  return SP_OK;
+}
+
+SP_API void sp_destroy(sp_handle* h) { free_handle(h); }
+
+SP_API sp_status sp_get_info(const sp_handle* h, sp_info* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  out->num_columns = h->C;
+  out->synapses_per_column = h->S;
+  out->input_bits = h->n_in;
+  out->input_words = h->n_words;
+  out->mask_words = h->mask_words;
+  out->max_active = h->max_active;
+  out->device = h->device;
+  out->device_bytes = h->device_bytes;
+  out->frames = h->frames;
+  return SP_OK;
+}
+
+SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn) {
+  if (!h || !input_bits) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  sp_status s = use_stream(h, h->own_stream);
+  if (s != SP_OK) return s;
+  uint32_t* dst = h->d_xsave[h->cur];
+  SP_CUDA(cudaMemcpyAsync(dst, input_bits, (size_t)h->n_words * 4, cudaMemcpyHostToDevice,
+                          h->stream));
+  return enqueue_frame(h, dst, h->d_xsave[h->cur ^ 1], nullptr, learn, nullptr);
+}
+
+SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int learn, void* stream) {
+  if (!h || !d_bits) return fail(SP_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(d_bits) % 4u) return fail(SP_EINVAL, "d_bits not 4-byte aligned");
+  DeviceGuard g(h->device);
+  sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
+  if (s != SP_OK) return s;
+  return enqueue_frame(h, d_bits, h->d_xsave[h->cur ^ 1], learn ? h->d_xsave[h->cur] : nullptr,
+                       learn, nullptr);
+}
+
+SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames, uint32_t n_frames,
+                                          uint64_t stride, int learn, uint32_t* d_active_masks,
+                                          void* stream) {
+  if (!h || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (n_frames == 0) return SP_OK;
+  if (stride < h->n_words) return fail(SP_EINVAL, "frame stride %llu < %u words", (unsigned long long)stride, h->n_words);
+  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_active_masks) % 4u)
+    return fail(SP_EINVAL, "device pointers must be 4-byte aligned");
+  DeviceGuard g(h->device);
+  sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
+  if (s != SP_OK) return s;
+  for (uint32_t t = 0; t < n_frames; ++t) {
+    const uint32_t* x = d_frames + (uint64_t)t * stride;
+    const uint32_t* x_prev = t ? d_frames + (uint64_t)(t - 1) * stride : h->d_xsave[h->cur ^ 1];
+    uint32_t* x_save = (learn && t + 1 == n_frames) ? h->d_xsave[h->cur] : nullptr;
+    uint32_t* mc = d_active_masks ? d_active_masks + (uint64_t)t * h->mask_words : nullptr;
+    s = enqueue_frame(h, x, x_prev, x_save, learn, mc);
+    if (s != SP_OK) return s;
+  }
+  return SP_OK;
+}
+
+SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint32_t n_frames,
+                                   uint64_t stride, int learn, uint32_t* h_active_masks) {
+  if (!h || (!h_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (n_frames == 0) return SP_OK;
+  if (stride < h->n_words) return fail(SP_EINVAL, "frame stride %llu < %u words", (unsigned long long)stride, h->n_words);
+  DeviceGuard g(h->device);
+  sp_status s = use_stream(h, h->own_stream);
+  if (s != SP_OK) return s;
+  if (!h->d_stage) {
+    SP_CUDA(cudaMalloc(&h->d_stage, (size_t)kSlots * kChunkFrames * h->n_words * 4));
+    SP_CUDA(cudaMalloc(&h->d_mstage, (size_t)kSlots * kChunkFrames * h->mask_words * 4));
+    SP_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+    SP_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < kSlots; ++i) {
+      SP_CUDA(cudaEventCreateWithFlags(&h->ev_h2d[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventCreateWithFlags(&h->ev_comp[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventCreateWithFlags(&h->ev_d2h[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventRecord(h->ev_comp[i], h->stream));
+      SP_CUDA(cudaEventRecord(h->ev_d2h[i], h->stream));
+    }
+  }
+  const size_t fbytes = (size_t)h->n_words * 4;
+  const size_t mbytes = (size_t)h->mask_words * 4;
+  for (uint32_t f0 = 0, ci = 0; f0 < n_frames; f0 += kChunkFrames, ++ci) {
+    const int slot = (int)(ci % kSlots);
+    const uint32_t nf = (n_frames - f0) < kChunkFrames ? (n_frames - f0) : kChunkFrames;
+    uint32_t* dst = h->d_stage + (size_t)slot * kChunkFrames * h->n_words;
+    uint32_t* mdst = h->d_mstage + (size_t)slot * kChunkFrames * h->mask_words;
+    // H2D of this chunk once the kernels that read this slot two chunks ago are done
+    SP_CUDA(cudaStreamWaitEvent(h->s_in, h->ev_comp[slot], 0));
+    SP_CUDA(cudaMemcpy2DAsync(dst, fbytes, h_frames + (uint64_t)f0 * stride, stride * 4, fbytes,
+                              nf, cudaMemcpyHostToDevice, h->s_in));
+    SP_CUDA(cudaEventRecord(h->ev_h2d[slot], h->s_in));
+    // compute once the chunk is in and the previous masks of this slot were read
+    SP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_h2d[slot], 0));
+    SP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_d2h[slot], 0));
+    for (uint32_t t = 0; t < nf; ++t) {
+      const uint32_t* x = dst + (size_t)t * h->n_words;
+      // within a chunk the previous frame is the staged one; across chunks it
+      // is the saved copy
+      const uint32_t* x_prev = t ? x - h->n_words : h->d_xsave[h->cur ^ 1];
+      uint32_t* x_save = (learn && t + 1 == nf) ? h->d_xsave[h->cur] : nullptr;
+      s = enqueue_frame(h, x, x_prev, x_save, learn, h_active_masks ? mdst + (size_t)t * h->mask_words : nullptr);
+      if (s != SP_OK) return s;
+    }
+    SP_CUDA(cudaEventRecord(h->ev_comp[slot], h->stream));
+    if (h_active_masks) {
+      SP_CUDA(cudaStreamWaitEvent(h->s_out, h->ev_comp[slot], 0));
+      SP_CUDA(cudaMemcpyAsync(h_active_masks + (uint64_t)f0 * h->mask_words, mdst, nf * mbytes,
+                              cudaMemcpyDeviceToHost, h->s_out));
+      SP_CUDA(cudaEventRecord(h->ev_d2h[slot], h->s_out));
+    }
+  }
+  if (h_active_masks) {
+    // the handle's stream waits for the last D2H so a later sync covers it
+    SP_CUDA(cudaEventRecord(h->ev_switch, h->s_out));
+    SP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_switch, 0));
+  }
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_active_columns(sp_handle* h, uint32_t* out, uint32_t cap, uint32_t* n) {
+  if (!h || !n || (!out && cap)) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(h->h_result, h->d_result, ((size_t)h->max_active + 1) * 4,
+                          cudaMemcpyDeviceToHost, h->stream));
+  sp_status s = wait_handle(h);
+  if (s != SP_OK) return s;
+  const uint32_t cnt = h->h_result[0];
+  *n = cnt;
+  if (cnt > h->max_active) return fail(SP_ECUDA, "winner count %u exceeds bound %u", cnt, h->max_active);
+  if (cap < cnt) return fail(SP_EINVAL, "cap %u < %u active columns", cap, cnt);
+  if (cnt) std::memcpy(out, h->h_result + 1, (size_t)cnt * 4);
+  return SP_OK;
+}
+
+SP_API sp_status sp_get_overlaps(sp_handle* h, float* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(out, h->d_ov, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_get_permanences(sp_handle* h, float* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  sp_status s = flush_learning(h);
+  if (s != SP_OK) return s;
+  SP_CUDA(cudaMemcpyAsync(out, h->d_perm, (size_t)h->C * h->S * 4, cudaMemcpyDeviceToHost,
+                          h->stream));
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(out, h->d_idx, (size_t)h->C * h->S * 4, cudaMemcpyDeviceToHost,
+                          h->stream));
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_get_boost(sp_handle* h, float* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(out, h->d_boost, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_set_boost(sp_handle* h, const float* boost) {
+  if (!h || !boost) return fail(SP_EINVAL, "NULL argument");
+  if (!finite_nonneg(boost, h->C)) return fail(SP_EINVAL, "boost must be finite and >= 0");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_sync(sp_handle* h) {
+  if (!h) return fail(SP_EINVAL, "NULL handle");
+  DeviceGuard g(h->device);
+  return wait_handle(h);
+}
+
+SP_API sp_status sp_set_timeout_ms(sp_handle* h, uint32_t ms) {
+  if (!h) return fail(SP_EINVAL, "NULL handle");
+  h->timeout_ms = ms ? ms : default_timeout_ms();
+  return SP_OK;
+}
+
+SP_API uint64_t sp_kernel_launch_count(void) {
+  return sp::g_launches.load(std::memory_order_relaxed);
+}
+
+SP_API const char* sp_status_str(sp_status s) {
+  switch (s) {
+    case SP_OK: return "ok";
+    case SP_EINVAL: return "invalid argument";
+    case SP_ENOMEM: return "out of memory";
+    case SP_ECUDA: return "CUDA error";
+    case SP_ETIMEOUT: return "timed out";
+    case SP_EBUSY: return "busy";
+    case SP_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+SP_API const char* sp_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

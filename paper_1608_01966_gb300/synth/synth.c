@@ -6,7 +6,9 @@
  * permanence draw and the double Bernoulli draws round identically on every
  * host (GCC contracts a*b+c to FMA by default on aarch64).
  */
+#ifndef SP_SYNTH_HIDDEN /* linked privately into the CUDA library */
 #define SP_SYNTH_BUILD 1
+#endif
 #include "../../include/sp_synth.h"
 
 #include <string.h>

@@ -1,0 +1,95 @@
+"""Seeded SP workloads: the inputs of the tests, smoke() and the benchmark.
+
+Only input generation lives here (pools, permanences, frames via the synth
+module): no SP arithmetic.  Recipes follow the five workloads of the build:
+  small     32x32 Bernoulli(0.10) input, 256 columns x 16 uniform synapses,
+            perms U[0.1,0.3], threshold 0.2, min_overlap 4, k 10 global;
+  frame     960x540 blobbed frames (density U[5%,20%], 7x7 box blur), 1024
+            columns on a 32x32 grid of receptive-field centres, 256 synapses
+            from a 64x64 window, perms U[0.1,0.3], threshold 0.2,
+            min_overlap 4, k 40 global, inc 0.05 / dec 0.02;
+  sweep     the frame input with columns {256,1024,4096} (square grids) x
+            synapses {16,64,256} x min_overlap {2,4,8} x k {8,32,128} x
+            global / 9x9 local inhibition.
+"""
+import dataclasses
+
+import numpy as np
+
+from . import synth
+
+BASE_SEED = 0x5EED0000
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    W: int
+    H: int
+    C: int
+    S: int
+    idx: np.ndarray
+    perm: np.ndarray
+    boost: np.ndarray
+    thr: float = 0.2
+    inc: float = 0.05
+    dec: float = 0.02
+    min_overlap: int = 4
+    k: int = 10
+    inhibition: int = 0
+    gw: int = 0
+    gh: int = 0
+    radius: int = 0
+
+    @property
+    def n_in(self):
+        return self.W * self.H
+
+    @property
+    def n_words(self):
+        return (self.n_in + 31) // 32
+
+    def config(self, **extra):
+        from ._binding import sp_config_init
+        return sp_config_init(input_w=self.W, input_h=self.H, num_columns=self.C,
+                              col_grid_w=self.gw, col_grid_h=self.gh,
+                              synapses_per_column=self.S, connect_threshold=self.thr,
+                              perm_inc=self.inc, perm_dec=self.dec,
+                              min_overlap=self.min_overlap, winners_set_size=self.k,
+                              inhibition=self.inhibition, local_radius=self.radius, **extra)
+
+
+def small_case(seed=BASE_SEED + 1):
+    C, S, n = 256, 16, 1024
+    idx = synth.pool_uniform(synth.derive_seed(seed, synth.PURPOSE_POOL, 0), C, S, n)
+    perm = synth.perm_uniform(synth.derive_seed(seed, synth.PURPOSE_PERM, 0), (C, S), 0.1, 0.3)
+    return Case("small", 32, 32, C, S, idx, perm, np.ones(C, np.float32), k=10)
+
+
+def small_frames(n, seed=BASE_SEED + 1, start=0):
+    return np.stack([synth.frame_bernoulli(synth.derive_seed(seed, synth.PURPOSE_FRAME, t),
+                                           1024, 0.10) for t in range(start, start + n)])
+
+
+def grid_case(name, C, S, seed, W=960, H=540, rf=64, min_overlap=4, k=40, inhibition=0,
+              radius=4, thr=0.2, lo=0.1, hi=0.3):
+    g = int(round(C ** 0.5))
+    assert g * g == C
+    idx = synth.pool_window(synth.derive_seed(seed, synth.PURPOSE_POOL, 0), g, g, W, H, rf, rf, S)
+    perm = synth.perm_uniform(synth.derive_seed(seed, synth.PURPOSE_PERM, 0), (C, S), lo, hi)
+    return Case(name, W, H, C, S, idx, perm, np.ones(C, np.float32), thr=thr,
+                min_overlap=min_overlap, k=k, inhibition=inhibition, gw=g, gh=g,
+                radius=radius if inhibition else 0)
+
+
+def frame_case(seed=BASE_SEED + 2):
+    return grid_case("frame", 1024, 256, seed)
+
+
+def blob_frames(n, W=960, H=540, seed=BASE_SEED + 2, start=0):
+    return np.stack([synth.frame_blobbed(synth.derive_seed(seed, synth.PURPOSE_FRAME, t), W, H)
+                     for t in range(start, start + n)])
+
+
+def pack(frames):
+    return synth.pack_frames(frames)
