@@ -209,6 +209,59 @@ SP_API sp_status sp_sync(sp_handle* h);
  * the work running. */
 SP_API sp_status sp_set_timeout_ms(sp_handle* h, uint32_t ms);
 
+/* ---- Allocation-free frame (no counterpart in the paper) ------------------
+ *
+ * sp_step_noalloc runs one frame -- overlap, inhibition and, if learn != 0,
+ * learning -- on SP state that the caller keeps in its own device buffers,
+ * and allocates nothing: no cudaMalloc, no cudaFree, no pinned or managed
+ * memory, no allocating library routine.  It is for callers that cannot
+ * allocate device memory at the point where they process a frame: a real-time
+ * video pipeline stage whose per-frame callback must not block (cudaMalloc
+ * and cudaFree may synchronise the whole device), or a host that runs work
+ * against a fixed device-memory budget, or owns every allocation itself, and
+ * so cannot let the library grow its footprint.
+ *
+ * The kernel's scratch (C boosted overlaps and a ticket counter) lives in a
+ * static device array of SP_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.  Every call
+ * shares that array and it keeps the last call's contents (the counter is
+ * cleared at the start of each call), so calls whose work overlaps on a GPU
+ * -- different streams, or different threads without ordering -- race and
+ * give wrong results: order them, e.g. all on one stream.
+ *
+ * The first call on each device does a one-time set-up with that device
+ * current (it looks up the array's device address); make that first call
+ * before any stream capture on that device.
+ *
+ * Arguments (device pointers on the current device; caller-owned; the call
+ * is asynchronous on `stream`, a cudaStream_t, NULL = legacy default):
+ *   cfg            scalars of the SP (input_w * input_h bits, num_columns C
+ *                  <= SP_NOALLOC_MAX_COLUMNS, synapses_per_column S,
+ *                  connect_threshold, perm_inc, perm_dec, min_overlap,
+ *                  winners_set_size, inhibition, column grid, local_radius);
+ *                  pool_mode, rf_*, perm_init_* and seed are ignored;
+ *   d_idx          [C][S] input indices, each < input_w * input_h (not
+ *                  checked: out-of-range indices read out of bounds);
+ *   d_perm         [C][S] permanences, updated in place when learn != 0;
+ *   d_boost        [C] boosts (finite, >= 0);
+ *   d_input        ceil(n_in / 32) packed input words (this frame);
+ *   d_active_mask  out: ceil(C / 32) words, bit c = column c active;
+ *   d_active_list  out: [0] = number of active columns n, [1..n] their
+ *                  indices ascending (room for 1 + C words).
+ * d_idx and d_perm must be 16-byte aligned when S % 4 == 0, every other
+ * pointer 4-byte aligned.
+ *
+ * Results equal those of sp_compute on a handle holding the same state.
+ * Returns SP_EINVAL (nothing enqueued) for a NULL or misaligned pointer, an
+ * invalid configuration or C > SP_NOALLOC_MAX_COLUMNS; SP_ECUDA when a launch
+ * fails.  sp_last_error() explains. */
+#define SP_NOALLOC_MAX_COLUMNS 16384u
+#define SP_NOALLOC_SCRATCH_BYTES ((SP_NOALLOC_MAX_COLUMNS + 64u) * 4u)
+SP_API sp_status sp_step_noalloc(const sp_config* cfg, const uint32_t* d_idx, float* d_perm,
+                                 const float* d_boost, const uint32_t* d_input, int learn,
+                                 uint32_t* d_active_mask, uint32_t* d_active_list,
+                                 void* stream);
+
 /* Number of kernels this library has launched in the calling process. */
 SP_API uint64_t sp_kernel_launch_count(void);
 

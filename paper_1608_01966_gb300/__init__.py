@@ -10,5 +10,5 @@ from ._binding import (  # noqa: F401
     sp_compute_frames_device, sp_config_init, sp_create, sp_create_from_state, sp_destroy,
     sp_get_boost, sp_get_info, sp_get_overlaps, sp_get_permanences, sp_get_pool,
     sp_kernel_launch_count, sp_last_error, sp_set_boost, sp_set_timeout_ms, sp_status_str,
-    sp_sync,
+    sp_step_noalloc, sp_sync,
 )

@@ -83,6 +83,7 @@ def lib():
         L.sp_sync.argtypes = [vp]
         L.sp_set_timeout_ms.argtypes = [vp, ct.c_uint32]
         L.sp_status_str.argtypes = [ct.c_int]
+        L.sp_step_noalloc.argtypes = [ct.POINTER(SpConfig), vp, vp, vp, vp, ct.c_int, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -221,6 +222,15 @@ def sp_sync(h):
 
 def sp_set_timeout_ms(h, ms):
     _check(lib().sp_set_timeout_ms(h, ms), "sp_set_timeout_ms")
+
+
+def sp_step_noalloc(cfg, d_idx, d_perm, d_boost, d_input, learn, d_active_mask, d_active_list,
+                    stream=None):
+    """One frame on caller-owned device buffers, allocating nothing (see
+    include/sp.h): every buffer is a device address or a CUDA tensor."""
+    _check(lib().sp_step_noalloc(ct.byref(cfg), _addr(d_idx), _addr(d_perm), _addr(d_boost),
+                                 _addr(d_input), 1 if learn else 0, _addr(d_active_mask),
+                                 _addr(d_active_list), _addr(stream)), "sp_step_noalloc")
 
 
 def sp_kernel_launch_count():

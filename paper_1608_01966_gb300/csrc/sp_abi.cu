@@ -28,8 +28,19 @@ extern std::atomic<uint64_t> g_launches;
 }
 
 namespace {
-
 thread_local std::string t_last_error;
+}
+
+void sp::set_last_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+}
+
+namespace {
 
 sp_status fail(sp_status s, const char* fmt, ...) {
   char buf[512];

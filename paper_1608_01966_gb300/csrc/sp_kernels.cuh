@@ -59,4 +59,7 @@ int step_grid(uint32_t C);
 // One-time per-process attribute set-up (max dynamic shared memory).
 cudaError_t kernels_init();
 
+// Record the calling thread's message for sp_last_error().
+void set_last_error(const char* fmt, ...);
+
 }  // namespace sp
