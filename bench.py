@@ -231,7 +231,8 @@ def main():
     case, frames_u8, packed = build_inputs(rank, args.frames)
     n, nw = packed.shape
     mw = (case.C + 31) // 32
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)  # a dedicated stream: events and kernels share it
+    torch.cuda.set_stream(stream)
     d_frames = torch.from_numpy(packed.view(np.int32)).to(dev)
     d_masks = torch.zeros((n, mw), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)

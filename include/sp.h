@@ -158,7 +158,7 @@ SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn)
 
 /* One frame already on the device (input_words words at d_bits, 4-byte
  * aligned), enqueued on `stream` (a cudaStream_t; NULL = the handle's own
- * stream).  The handle then stays on that stream until its next call. */
+ * stream, cudaStreamLegacy = the legacy default stream).  The handle then stays on that stream until its next call. */
 SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int learn,
                                    void* stream);
 

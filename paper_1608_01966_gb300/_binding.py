@@ -93,14 +93,26 @@ def _check(rc, where):
         raise SpError(rc, where, lib().sp_last_error().decode())
 
 
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
+
+
 def _addr(x):
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
         return x.data_ptr()
-    if hasattr(x, "cuda_stream"):
-        return x.cuda_stream
     return int(x)
+
+
+def _stream(s):
+    """A cudaStream_t for the ABI.  None selects the handle's own stream; a
+    torch stream whose handle is 0 is the legacy default stream, which the
+    ABI must receive as cudaStreamLegacy (its NULL means "own stream")."""
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream or CUDA_STREAM_LEGACY
+    return int(s) or CUDA_STREAM_LEGACY
 
 
 def _np_u32(a):
@@ -156,7 +168,7 @@ def sp_compute(h, input_bits, learn):
 
 
 def sp_compute_device(h, d_bits, learn, stream=None):
-    _check(lib().sp_compute_device(h, _addr(d_bits), 1 if learn else 0, _addr(stream)),
+    _check(lib().sp_compute_device(h, _addr(d_bits), 1 if learn else 0, _stream(stream)),
            "sp_compute_device")
 
 
@@ -164,7 +176,7 @@ def sp_compute_frames_device(h, d_frames, n_frames, stride_words, learn, d_activ
                              stream=None):
     _check(lib().sp_compute_frames_device(h, _addr(d_frames), n_frames, stride_words,
                                           1 if learn else 0, _addr(d_active_masks),
-                                          _addr(stream)), "sp_compute_frames_device")
+                                          _stream(stream)), "sp_compute_frames_device")
 
 
 def sp_compute_frames(h, frames, learn, masks_out=None):
@@ -230,7 +242,7 @@ def sp_step_noalloc(cfg, d_idx, d_perm, d_boost, d_input, learn, d_active_mask, 
     include/sp.h): every buffer is a device address or a CUDA tensor."""
     _check(lib().sp_step_noalloc(ct.byref(cfg), _addr(d_idx), _addr(d_perm), _addr(d_boost),
                                  _addr(d_input), 1 if learn else 0, _addr(d_active_mask),
-                                 _addr(d_active_list), _addr(stream)), "sp_step_noalloc")
+                                 _addr(d_active_list), _stream(stream)), "sp_step_noalloc")
 
 
 def sp_kernel_launch_count():

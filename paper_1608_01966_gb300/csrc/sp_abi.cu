@@ -85,8 +85,39 @@ struct DeviceGuard {
 
 size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
 
+bool all_ones(const float* v, size_t n);
+
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
 constexpr int kSlots = 2;
+constexpr uint32_t kGraphMinFrames = 4;  // shorter sequences are launched directly
+constexpr size_t kGraphCacheSize = 8;
+
+// A recorded frame sequence is valid for exactly the buffers, sizes and
+// starting (buffer parity, pending learning) state it was recorded with.
+struct GraphKey {
+  const uint32_t* x;
+  uint64_t n, stride;
+  int learn;
+  uint32_t* masks;
+  int cur;
+  bool pending;
+  bool unit_boost;  // selects the histogram path baked into the recorded launches
+  bool operator==(const GraphKey& o) const {
+    return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
+           cur == o.cur && pending == o.pending && unit_boost == o.unit_boost;
+  }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  uint64_t last_use;
+};
+
+bool graphs_enabled() {
+  const char* s = std::getenv("SP_DISABLE_GRAPHS");
+  return !(s && s[0] == '1');
+}
 
 }  // namespace
 
@@ -105,6 +136,8 @@ struct sp_handle {
   uint32_t* d_mask[2] = {nullptr, nullptr};
   uint32_t* d_result = nullptr;
   uint32_t* d_counter = nullptr;
+  uint32_t* d_hist = nullptr;  // [S + 1], used when every boost is 1
+  bool unit_boost = true;
   uint32_t* h_result = nullptr;  // pinned [1 + C]
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;  // stream of the last call
@@ -120,6 +153,10 @@ struct sp_handle {
   uint32_t* d_mstage = nullptr;  // [kSlots][kChunkFrames][mask_words]
   cudaStream_t s_in = nullptr, s_out = nullptr;
   cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
+  // recorded frame sequences (CUDA graphs), replayed instead of n launches
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for recording
+  uint64_t graph_clock = 0;
 };
 
 namespace {
@@ -192,6 +229,9 @@ void free_handle(sp_handle* h) {
   if (h->s_out) cudaStreamDestroy(h->s_out);
   if (h->d_stage) cudaFree(h->d_stage);
   if (h->d_mstage) cudaFree(h->d_mstage);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_switch) cudaEventDestroy(h->ev_switch);
   if (h->ev_wait) cudaEventDestroy(h->ev_wait);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -220,7 +260,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   size_t total = 0;
   const size_t sizes[9] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
                            (size_t)h->n_words * 4 * 2, (size_t)h->mask_words * 4 * 2,
-                           ((size_t)h->C + 1) * 4, 4, 0};
+                           ((size_t)h->C + 1) * 4, 4, ((size_t)h->S + 1) * 4};
   for (int i = 0; i < 9; ++i) {
     off[i] = total;
     total += align256(sizes[i]);
@@ -238,6 +278,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   h->d_mask[1] = h->d_mask[0] + h->mask_words;
   h->d_result = reinterpret_cast<uint32_t*>(b + off[6]);
   h->d_counter = reinterpret_cast<uint32_t*>(b + off[7]);
+  h->d_hist = reinterpret_cast<uint32_t*>(b + off[8]);
   SP_CUDA(cudaMallocHost(&h->h_result, ((size_t)h->C + 1) * 4));
   SP_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   h->stream = h->own_stream;
@@ -251,6 +292,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
     ones.assign(h->C, 1.0f);
     boost = ones.data();
   }
+  h->unit_boost = all_ones(boost, h->C);
   SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
   SP_CUDA(cudaStreamSynchronize(h->stream));
   h->grid = sp::step_grid(h->C);
@@ -312,6 +354,7 @@ sp::StepArgs base_args(const sp_handle* h) {
   a.ov = h->d_ov;
   a.result = h->d_result;
   a.counter = h->d_counter;
+  a.hist = (h->unit_boost && h->cfg.inhibition == SP_INHIBIT_GLOBAL) ? h->d_hist : nullptr;
   a.C = h->C;
   a.S = h->S;
   a.n_words = h->n_words;
@@ -331,7 +374,7 @@ sp::StepArgs base_args(const sp_handle* h) {
 // Enqueue one frame: x is this frame's input (device); x_prev the previous
 // frame's (used iff learning is pending); x_save, if set, receives a copy of
 // x for the next frame's learning.
-sp_status enqueue_frame(sp_handle* h, const uint32_t* x, const uint32_t* x_prev,
+sp_status enqueue_frame(sp_handle* h, cudaStream_t st, const uint32_t* x, const uint32_t* x_prev,
                         uint32_t* x_save, int learn, uint32_t* mask_copy) {
   sp::StepArgs a = base_args(h);
   const int cur = h->cur;
@@ -343,7 +386,7 @@ sp_status enqueue_frame(sp_handle* h, const uint32_t* x, const uint32_t* x_prev,
   a.x_save = x_save;
   a.mask_out = h->d_mask[cur];
   a.mask_copy = mask_copy;
-  SP_CUDA(sp::launch_step(a, h->grid, h->stream));
+  SP_CUDA(sp::launch_step(a, h->grid, st));
   h->pending = learn != 0;
   h->cur = cur ^ 1;
   h->frames++;
@@ -365,6 +408,80 @@ sp_status flush_learning(sp_handle* h) {
   SP_CUDA(sp::launch_learn(l, h->stream));
   h->pending = false;
   return SP_OK;
+}
+
+// Enqueue frames x_base + t * stride (t < n) on `st`, from the handle's
+// current (parity, pending) state.  Within the call the previous frame is
+// read in place; the last frame is saved when learning, for the next call.
+sp_status enqueue_sequence(sp_handle* h, cudaStream_t st, const uint32_t* x_base, uint32_t n,
+                           uint64_t stride, int learn, uint32_t* masks) {
+  for (uint32_t t = 0; t < n; ++t) {
+    const uint32_t* x = x_base + (uint64_t)t * stride;
+    const uint32_t* x_prev = t ? x - stride : h->d_xsave[h->cur ^ 1];
+    uint32_t* x_save = (learn && t + 1 == n) ? h->d_xsave[h->cur] : nullptr;
+    uint32_t* mc = masks ? masks + (uint64_t)t * h->mask_words : nullptr;
+    sp_status s = enqueue_frame(h, st, x, x_prev, x_save, learn, mc);
+    if (s != SP_OK) return s;
+  }
+  return SP_OK;
+}
+
+// Run a frame sequence on the handle's stream: replay its recorded graph if
+// this exact sequence was seen before, else record it on the private capture
+// stream first.  Short sequences, or SP_DISABLE_GRAPHS=1, launch directly.
+sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
+                       int learn, uint32_t* masks) {
+  if (n < kGraphMinFrames || !graphs_enabled())
+    return enqueue_sequence(h, h->stream, x_base, n, stride, learn, masks);
+  const GraphKey key{x_base, n, stride, learn, masks, h->cur, h->pending, h->unit_boost};
+  GraphEntry* e = nullptr;
+  for (auto& g : h->graphs)
+    if (g.key == key) e = &g;
+  if (!e) {
+    if (!h->cap_stream) SP_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const int cur0 = h->cur;
+    const bool pending0 = h->pending;
+    const uint64_t frames0 = h->frames;
+    SP_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sp_status s = enqueue_sequence(h, h->cap_stream, x_base, n, stride, learn, masks);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    sp::g_launches.fetch_sub(n, std::memory_order_relaxed);  // recorded, not launched
+    h->cur = cur0;
+    h->pending = pending0;
+    h->frames = frames0;
+    if (s != SP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (ec != cudaSuccess) return fail(SP_ECUDA, "recording the frame sequence: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(SP_ECUDA, "instantiating the frame sequence: %s", cudaGetErrorString(ei));
+    if (h->graphs.size() >= kGraphCacheSize) {
+      size_t lru = 0;
+      for (size_t i = 1; i < h->graphs.size(); ++i)
+        if (h->graphs[i].last_use < h->graphs[lru].last_use) lru = i;
+      cudaGraphExecDestroy(h->graphs[lru].exec);
+      h->graphs.erase(h->graphs.begin() + lru);
+    }
+    h->graphs.push_back(GraphEntry{key, exec, 0});
+    e = &h->graphs.back();
+  }
+  e->last_use = ++h->graph_clock;
+  SP_CUDA(cudaGraphLaunch(e->exec, h->stream));
+  sp::g_launches.fetch_add(n, std::memory_order_relaxed);
+  h->pending = learn != 0;
+  h->cur ^= (int)(n & 1u);
+  h->frames += n;
+  return SP_OK;
+}
+
+bool all_ones(const float* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (v[i] != 1.0f) return false;
+  return true;
 }
 
 bool finite_nonneg(const float* v, size_t n) {
@@ -486,7 +603,7 @@ SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn)
   uint32_t* dst = h->d_xsave[h->cur];
   SP_CUDA(cudaMemcpyAsync(dst, input_bits, (size_t)h->n_words * 4, cudaMemcpyHostToDevice,
                           h->stream));
-  return enqueue_frame(h, dst, h->d_xsave[h->cur ^ 1], nullptr, learn, nullptr);
+  return enqueue_frame(h, h->stream, dst, h->d_xsave[h->cur ^ 1], nullptr, learn, nullptr);
 }
 
 SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int learn, void* stream) {
@@ -495,8 +612,8 @@ SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int lea
   DeviceGuard g(h->device);
   sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
   if (s != SP_OK) return s;
-  return enqueue_frame(h, d_bits, h->d_xsave[h->cur ^ 1], learn ? h->d_xsave[h->cur] : nullptr,
-                       learn, nullptr);
+  return enqueue_frame(h, h->stream, d_bits, h->d_xsave[h->cur ^ 1],
+                       learn ? h->d_xsave[h->cur] : nullptr, learn, nullptr);
 }
 
 SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames, uint32_t n_frames,
@@ -510,15 +627,7 @@ SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames
   DeviceGuard g(h->device);
   sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
   if (s != SP_OK) return s;
-  for (uint32_t t = 0; t < n_frames; ++t) {
-    const uint32_t* x = d_frames + (uint64_t)t * stride;
-    const uint32_t* x_prev = t ? d_frames + (uint64_t)(t - 1) * stride : h->d_xsave[h->cur ^ 1];
-    uint32_t* x_save = (learn && t + 1 == n_frames) ? h->d_xsave[h->cur] : nullptr;
-    uint32_t* mc = d_active_masks ? d_active_masks + (uint64_t)t * h->mask_words : nullptr;
-    s = enqueue_frame(h, x, x_prev, x_save, learn, mc);
-    if (s != SP_OK) return s;
-  }
-  return SP_OK;
+  return run_sequence(h, d_frames, n_frames, stride, learn, d_active_masks);
 }
 
 SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint32_t n_frames,
@@ -557,15 +666,8 @@ SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint3
     // compute once the chunk is in and the previous masks of this slot were read
     SP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_h2d[slot], 0));
     SP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_d2h[slot], 0));
-    for (uint32_t t = 0; t < nf; ++t) {
-      const uint32_t* x = dst + (size_t)t * h->n_words;
-      // within a chunk the previous frame is the staged one; across chunks it
-      // is the saved copy
-      const uint32_t* x_prev = t ? x - h->n_words : h->d_xsave[h->cur ^ 1];
-      uint32_t* x_save = (learn && t + 1 == nf) ? h->d_xsave[h->cur] : nullptr;
-      s = enqueue_frame(h, x, x_prev, x_save, learn, h_active_masks ? mdst + (size_t)t * h->mask_words : nullptr);
-      if (s != SP_OK) return s;
-    }
+    s = run_sequence(h, dst, nf, h->n_words, learn, h_active_masks ? mdst : nullptr);
+    if (s != SP_OK) return s;
     SP_CUDA(cudaEventRecord(h->ev_comp[slot], h->stream));
     if (h_active_masks) {
       SP_CUDA(cudaStreamWaitEvent(h->s_out, h->ev_comp[slot], 0));
@@ -634,7 +736,9 @@ SP_API sp_status sp_set_boost(sp_handle* h, const float* boost) {
   if (!finite_nonneg(boost, h->C)) return fail(SP_EINVAL, "boost must be finite and >= 0");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
-  return wait_handle(h);
+  sp_status s = wait_handle(h);
+  if (s == SP_OK) h->unit_boost = all_ones(boost, h->C);
+  return s;
 }
 
 SP_API sp_status sp_sync(sp_handle* h) {

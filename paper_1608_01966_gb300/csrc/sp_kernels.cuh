@@ -29,6 +29,9 @@ struct StepArgs {
   uint32_t* mask_copy;       // optional second copy of the mask (caller array), or nullptr
   uint32_t* result;          // [0] = number of winners, [1..] ascending winners
   uint32_t* counter;         // last-CTA ticket, 0 between launches
+  uint32_t* hist;            // [S + 1] counts of surviving raw overlaps, 0 between
+                             // launches; used (global inhibition) when every boost
+                             // is exactly 1, else nullptr (radix select instead)
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k;

@@ -9,13 +9,16 @@
 //                       (Section 1.1) on the same pass, so learning costs no
 //                       extra read of the state.
 //   phase 2 (last CTA)  Alg. 2 over all C overlaps held in shared memory:
-//                       global = radix select of the k-th largest overlap
-//                       (four 8-bit passes over the fp32 bit patterns, which
-//                       order like the values since overlaps are >= 0), then
-//                       ties at that value go to the lowest indices through
-//                       one block scan; local = rank count over the clipped
-//                       (2r+1)^2 window.  Output: ascending winner list and
-//                       winner bitmask.
+//                       global = find the k-th largest overlap, then ties at
+//                       that value go to the lowest indices through one
+//                       block scan.  With unit boosts the overlap is the raw
+//                       count itself, so phase 1 builds a histogram of the
+//                       surviving counts (global atomics) and the k-th value
+//                       is read off it in one scan; otherwise a radix select
+//                       runs four 8-bit passes over the fp32 bit patterns
+//                       (which order like the values, overlaps being >= 0).
+//                       Local = rank count over the clipped (2r+1)^2 window.
+//                       Output: ascending winner list and winner bitmask.
 //
 // The CTA that runs phase 2 is the last one to take a ticket from a counter,
 // so no CTA ever waits for another (no grid barrier, nothing to hang).
@@ -180,6 +183,32 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
     } else if (nz_tot <= a.k) {
       T = 0u;
       need = 0u;
+    } else if (a.hist) {
+      // counts are the overlaps: walk the histogram from the top.  Thread t
+      // owns bins S - t*pb ... down to S - (t+1)*pb + 1 (descending).
+      const uint32_t nb = a.S;  // bins 1..S
+      const uint32_t pb = (nb + kStepThreads - 1) / kStepThreads;
+      const uint32_t top = nb >= t * pb ? nb - t * pb : 0u;  // first bin of this thread
+      const uint32_t cnt_bins = top == 0u ? 0u : min(pb, top);
+      uint32_t mine = 0;
+      for (uint32_t b = 0; b < cnt_bins; ++b) mine += __ldcg(a.hist + (top - b));
+      uint32_t above, e1, tot, z;
+      block_scan2(mine, 0u, above, e1, tot, z, sh);
+      if (above < a.k && above + mine >= a.k) {
+        uint32_t acc = above;
+        for (uint32_t b = 0; b < cnt_bins; ++b) {
+          const uint32_t hb = __ldcg(a.hist + (top - b));
+          if (acc + hb >= a.k) {
+            s_digit = top - b;  // the k-th largest count
+            s_above = acc;
+            break;
+          }
+          acc += hb;
+        }
+      }
+      __syncthreads();
+      T = __float_as_uint(__uint2float_rn(s_digit));
+      need = a.k - s_above;
     } else {
       uint32_t prefix = 0u, pmask = 0u, kk = a.k;
       for (int shift = 24; shift >= 0; shift -= 8) {
@@ -263,6 +292,8 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
   }
   __syncthreads();
   if (t == 0u) a.result[0] = total;
+  if (a.hist)
+    for (uint32_t b = t; b <= a.S; b += kStepThreads) a.hist[b] = 0u;
   for (uint32_t i = t; i < a.mask_words; i += kStepThreads) {
     const uint32_t m = smask[i];
     a.mask_out[i] = m;
@@ -285,7 +316,9 @@ __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a)
     const bool learn_now = a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
     const uint32_t raw = column_overlap<VEC>(a, c, learn_now, lane);
     if (lane == 0) {
-      a.ov[c] = raw < a.min_overlap ? 0.0f : __fmul_rn(__uint2float_rn(raw), __ldg(a.boost + c));
+      const bool keep = raw >= a.min_overlap;
+      a.ov[c] = keep ? __fmul_rn(__uint2float_rn(raw), __ldg(a.boost + c)) : 0.0f;
+      if (a.hist && keep && raw != 0u) atomicAdd(a.hist + raw, 1u);  // unit boost: ov == raw
     }
   }
   // publish this CTA's overlaps, then take a ticket; the last CTA inhibits

@@ -308,3 +308,31 @@ def test_set_boost_changes_overlaps_exactly():
     np.testing.assert_array_equal(g["ov"], ov[-1])
     np.testing.assert_array_equal(g["perm"], perm)
     spg.sp_destroy(h)
+
+
+def test_recorded_sequences_replay_and_boost_change():
+    """Frame sequences are recorded once as CUDA graphs and replayed: three
+    passes over the same device buffers (record, record with learning
+    pending, replay), then a non-unit boost (which switches the inhibition
+    path baked into a recording) and two more passes."""
+    case = wl.frame_case(seed=wl.BASE_SEED + 14)
+    frames = wl.blob_frames(9, seed=wl.BASE_SEED + 14)
+    packed = wl.pack(frames)
+    stream = torch.cuda.current_stream()
+    d = _dev(packed)
+    dm = torch.zeros((9, 32), dtype=torch.int32, device="cuda")
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    perm = case.perm.copy()
+    boost = synth.perm_uniform(99, (case.C,), 0.5, 1.5)
+    for p in range(5):
+        if p == 3:
+            spg.sp_set_boost(h, boost)
+            case = wl.Case(case.name, case.W, case.H, case.C, case.S, case.idx, case.perm, boost,
+                           k=case.k, min_overlap=case.min_overlap)
+        act, perm, _ = oracle_run(case, frames, True, perm=perm)
+        spg.sp_compute_frames_device(h, d, 9, packed.shape[1], True, dm, stream)
+        spg.sp_sync(h)
+        got = dense(dm.cpu().numpy().view(np.uint32), case.C)
+        assert first_diff(got, act) is None, f"pass {p}"
+    np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+    spg.sp_destroy(h)
