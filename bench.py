@@ -2,24 +2,29 @@
 """Spatial Pooler benchmark: frames/s and column-updates/s at 1024 columns x
 256 synapses.
 
-Workload (one "step"): the paper-scale frame SP -- 960x540 blobbed binary
-frames (density U[5%,20%], 7x7 box blur), 1024 columns on a 32x32 grid of
-receptive-field centres, 256 potential synapses from a 64x64 window, fp32
-permanences U[0.1,0.3], threshold 0.2, min_overlap 4, k 40 global
-inhibition -- run over a 500-frame sequence with learning on (inc 0.05,
-dec 0.02).  Frames are synthetic (seeded) and packed 32 bits per word.  Each
-step is the whole hot path (overlap, inhibition, learning) for 500 frames,
-one fused kernel per frame, with the frames and SP state resident in HBM.
-L2 (129 MB, larger than state + frames) is flushed by a 256 MiB write
-between timed steps.
+Headline workload (one "step" = one batch frame): the paper-scale frame SP --
+960x540 blobbed binary frames (density U[5%,20%], 7x7 box blur), 1024
+columns on a 32x32 grid of receptive-field centres, 256 potential synapses
+from a 64x64 window, fp32 permanences U[0.1,0.3], threshold 0.2,
+min_overlap 4, k 40 global inhibition, learning on (inc 0.05, dec 0.02) --
+run as 256 independent SP instances per GPU (own pools, permanences and
+frame streams), each computing one frame per step: overlap, inhibition and
+learning for all 256 in one launch.  The 565 MB of SP state is far larger
+than the 129 MB L2, so every step streams it from HBM (no flush needed).
+Frames come from a pool of 64 seeded blobbed frames, instance i taking
+frame (7 i + t) mod 64 at step t.
 
-Under torchrun each rank runs its own independent SP instance (the path has
-no cross-instance exchange), so `value` is the sum over ranks (weak scaling).
+Secondary (`single_sp`): one such SP over a 500-frame learning sequence
+(the latency-bound serial case), L2 flushed between steps.
+
+Under torchrun every rank runs its own 256 instances (no cross-instance
+exchange), so `value` is the sum over ranks (weak scaling).
 
 `--impl reference` times the plain CPU oracle (the parity reference) on the
 host cores on a bounded sample of the same workload.
 """
 import argparse
+import concurrent.futures as cf
 import hashlib
 import json
 import os
@@ -34,19 +39,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_FRAMES = 500
-WORKLOAD = "paper-scale frame SP: 960x540 blobbed frames, 1024 col x 256 syn (64x64 RF), k=40 global, learn on, 500-frame sequence"
+INSTANCES = 256
+FRAME_POOL = 64
+SEQ_FRAMES = 500
+WORKLOAD = ("paper-scale frame SP x 256 independent instances: 960x540 blobbed frames, "
+            "1024 col x 256 syn (64x64 RF), k=40 global, learning on, one frame per instance per step")
 METRIC = "SP frames/s (1024 col x 256 syn, 960x540 input, learning on)"
-STEP_KERNEL = "sp_step_kernel"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--instances", type=int, default=INSTANCES)
+    ap.add_argument("--seq-frames", type=int, default=SEQ_FRAMES)
+    ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -57,16 +66,27 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def build_inputs(rank, n_frames):
+def make_cases(n, rank):
+    """n frame-SP instances with their own seeds (generated in parallel: the
+    generators are C code called without the GIL)."""
     from paper_1608_01966_gb300 import workloads as wl
+    seeds = [wl.BASE_SEED + 2 + 1000 * rank + 17 * i for i in range(n)]
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        return list(ex.map(lambda s: wl.frame_case(seed=s), seeds))
+
+
+def make_frame_pool(rank):
+    from paper_1608_01966_gb300 import synth, workloads as wl
     seed = wl.BASE_SEED + 2 + 1000 * rank
-    case = wl.frame_case(seed=seed)
-    frames = wl.blob_frames(n_frames, seed=seed)
-    return case, frames, wl.pack(frames)
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        fr = list(ex.map(lambda t: synth.frame_blobbed(
+            synth.derive_seed(seed, synth.PURPOSE_FRAME, t), 960, 540), range(FRAME_POOL)))
+    fr = np.stack(fr)
+    return fr, wl.pack(fr)
 
 
 def algorithmic_bytes_per_frame(case, learn=True):
-    """Bytes one frame must move at minimum in the canonical layout: the
+    """Bytes one SP frame must move at minimum in the canonical layout: the
     pools and permanences (4 B each per synapse), the packed frame, the
     overlaps written, the winner list and, when learning, the winners'
     permanence rows written back."""
@@ -77,9 +97,8 @@ def algorithmic_bytes_per_frame(case, learn=True):
 
 
 def read_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(p) as f:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     except Exception:
@@ -88,17 +107,17 @@ def read_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sp_step.cu", "sp_kernels.cuh"):
+    for f in ("sp_step.cu", "sp_kernels.cuh", "sp_device.cuh"):
         with open(os.path.join(ROOT, "paper_1608_01966_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def read_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, only if the kernel source is unchanged since the capture."""
+    """DRAM bytes per launch of the batch step kernel from the committed ncu
+    summary, only while the kernel source is unchanged since the capture."""
     try:
-        with open(os.path.join(ROOT, "profiles", "sp_step_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "sp_batch_step_traffic.json")) as f:
             d = json.load(f)
         if d.get("source_sha") == kernel_source_sha():
             return d.get("dram_bytes_per_launch")
@@ -117,7 +136,6 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = None
 
     def start(self):
         try:
@@ -159,57 +177,95 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def time_oracle(case, frames_u8, seconds):
-    """Time the oracle (as it stands, one thread) over whole passes of the
-    frame sequence until `seconds` elapse; returns (frames/s, frames done)."""
+def oracle_sample(cases, pool_u8, seconds, start_step=0):
+    """The oracle as it stands (one thread), instance by instance in the
+    headline workload's order (step t: instance i on frame (7 i + t) mod 64),
+    until `seconds` elapse.  Returns (SP frames/s, SP frames done)."""
     import oracle
-    p = oracle.params(case.C, case.S, case.n_in, case.thr, case.inc, case.dec,
-                      case.min_overlap, case.k, case.inhibition, case.gw, case.gh, case.radius)
-    perm = case.perm.copy()
+    states = {}
     done = 0
     t0 = time.perf_counter()
-    chunk = 25
+    step = start_step
     while True:
-        for i in range(0, frames_u8.shape[0], chunk):
-            oracle.run(p, case.idx, perm, case.boost, frames_u8[i:i + chunk], True)
-            done += min(chunk, frames_u8.shape[0] - i)
+        for i, c in enumerate(cases):
+            if i not in states:
+                states[i] = (oracle.params(c.C, c.S, c.n_in, c.thr, c.inc, c.dec, c.min_overlap,
+                                           c.k), c.perm.copy())
+            p, perm = states[i]
+            fr = pool_u8[(7 * i + step) % FRAME_POOL]
+            oracle.run(p, c.idx, perm, c.boost, fr[None, :], True)
+            done += 1
             if time.perf_counter() - t0 >= seconds:
                 return done / (time.perf_counter() - t0), done
+        step += 1
 
 
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    case, frames, _ = build_inputs(0, args.frames)
+    n_sample = 8  # instances per reference step (bounded sample of the 256-instance step)
+    cases = make_cases(n_sample, 0)
+    pool_u8, _ = make_frame_pool(0)
     import oracle
-    p = oracle.params(case.C, case.S, case.n_in, case.thr, case.inc, case.dec,
-                      case.min_overlap, case.k)
-    sample = 25  # frames per reference step (bounded sample of the 500-frame step)
-    perm = case.perm.copy()
+    params = [oracle.params(c.C, c.S, c.n_in, c.thr, c.inc, c.dec, c.min_overlap, c.k)
+              for c in cases]
+    perms = [c.perm.copy() for c in cases]
+
+    def step(t):
+        for i, c in enumerate(cases):
+            oracle.run(params[i], c.idx, perms[i], c.boost,
+                       pool_u8[(7 * i + t) % FRAME_POOL][None, :], True)
+
     for w in range(args.warmup):
-        oracle.run(p, case.idx, perm, case.boost, frames[:sample], True)
+        step(w)
     times = []
     for s in range(args.steps):
-        i0 = (s * sample) % (args.frames - sample + 1)
         t0 = time.perf_counter()
-        oracle.run(p, case.idx, perm, case.boost, frames[i0:i0 + sample], True)
+        step(args.warmup + s)
         times.append(time.perf_counter() - t0)
-    fps = sample * len(times) / sum(times)
-    ms = 1000.0 * sum(times) / len(times) * (args.frames / sample)
+    fps = n_sample * len(times) / sum(times)
+    ms = 1000.0 * sum(times) / len(times) * (args.instances / n_sample)
+    sample = f"{n_sample} of the {args.instances} instances per step, one frame each, one thread"
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step": args.frames},
-        "column_updates_per_s": fps * case.C,
+        "config": {"workload": WORKLOAD, "instances_per_gpu": args.instances},
+        "column_updates_per_s": fps * 1024,
         "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} frames of the 500-frame sequence per step, one thread"},
+                         "sample": sample},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_single_sp(spg, torch, case, pool_packed, n_frames, steps, dev, stream):
+    """One SP over an n_frames learning sequence (frames cycled from the
+    pool), L2 flushed between steps; returns (frames/s, us per frame)."""
+    idx = [t % FRAME_POOL for t in range(n_frames)]
+    frames = np.ascontiguousarray(pool_packed[idx])
+    d = torch.from_numpy(frames.view(np.int32)).to(dev)
+    dm = torch.zeros((n_frames, (case.C + 31) // 32), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    for _ in range(3):
+        spg.sp_compute_frames_device(h, d, n_frames, frames.shape[1], True, dm, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        flush.fill_(s)
+        ev[s][0].record(stream)
+        spg.sp_compute_frames_device(h, d, n_frames, frames.shape[1], True, dm, stream)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    spg.sp_destroy(h)
+    del flush
+    return n_frames / (ms / 1000.0), ms * 1000.0 / n_frames
 
 
 def main():
@@ -227,42 +283,51 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-
-    case, frames_u8, packed = build_inputs(rank, args.frames)
-    n, nw = packed.shape
-    mw = (case.C + 31) // 32
     stream = torch.cuda.Stream(dev)  # a dedicated stream: events and kernels share it
     torch.cuda.set_stream(stream)
-    d_frames = torch.from_numpy(packed.view(np.int32)).to(dev)
-    d_masks = torch.zeros((n, mw), dtype=torch.int32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
-    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
 
-    def step():
-        spg.sp_compute_frames_device(h, d_frames, n, nw, True, d_masks, stream)
+    n = args.instances
+    cases = make_cases(n, rank)
+    pool_u8, pool_packed = make_frame_pool(rank)
+    handles = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(handles)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    mw = info["mask_words"]
+    # every distinct batch frame a step can see: step t uses pattern t mod 64
+    nw = pool_packed.shape[1]
+    batch = np.zeros((FRAME_POOL, fw), np.uint32)
+    for t in range(FRAME_POOL):
+        for i in range(n):
+            o = int(fo[i])
+            batch[t, o:o + nw] = pool_packed[(7 * i + t) % FRAME_POOL]
+    d_batch = torch.from_numpy(batch.view(np.int32)).to(dev)
+    d_masks = torch.zeros((FRAME_POOL, mw), dtype=torch.int32, device=dev)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    spg.sp_sync(h)
+    def step(t):
+        r = t % FRAME_POOL
+        spg.sp_batch_compute_device(b, d_batch[r], 1, fw, True, d_masks[r], mw, stream)
+
+    for w in range(max(3, args.warmup)):
+        step(w)
+    spg.sp_batch_sync(b)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     launches0 = spg.sp_kernel_launch_count()
+    start.record(stream)
     for s in range(args.steps):
-        flush.fill_(s)  # L2 flush, outside the step's events
-        starts[s].record(stream)
-        step()
-        ends[s].record(stream)
+        step(max(3, args.warmup) + s)
+    end.record(stream)
     torch.cuda.synchronize()
     launches = spg.sp_kernel_launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    ms_local = sum(step_ms) / len(step_ms)
+    ms_local = start.elapsed_time(end) / args.steps
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms_local], device=dev)
@@ -273,20 +338,20 @@ def main():
         ms = ms_local
     value = world * n / (ms / 1000.0)
 
-    # end to end through the public API with host buffers (pinned frames in,
-    # active masks out), every copy inside the timed region
-    h_frames = torch.from_numpy(packed.view(np.int32)).pin_memory()
-    h_masks = torch.zeros((n, mw), dtype=torch.int32).pin_memory()
+    # end to end through the public API with host buffers: every step's batch
+    # frame copied in from pinned memory and its mask record copied back
+    e2e_steps = max(4, min(args.steps, 16))
+    h_frames = torch.from_numpy(
+        np.ascontiguousarray(batch[np.arange(e2e_steps) % FRAME_POOL]).view(np.int32)).pin_memory()
+    h_masks = torch.zeros((e2e_steps, mw), dtype=torch.int32).pin_memory()
     hf = h_frames.numpy().view(np.uint32)
     hm = h_masks.numpy().view(np.uint32)
-    spg.sp_compute_frames(h, hf, True, hm)  # warm the staging buffers
-    e2e_steps = max(1, min(args.steps, 5))
+    spg.sp_batch_compute(b, hf, True, hm)  # warm the staging buffers
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        spg.sp_compute_frames(h, hf, True, hm)
+    spg.sp_batch_compute(b, hf, True, hm)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
@@ -294,20 +359,31 @@ def main():
         e2e_s = float(t.item())
     e2e_value = world * n / e2e_s
 
-    spg.sp_destroy(h)
+    spg.sp_batch_destroy(b)
+    for h in handles:
+        spg.sp_destroy(h)
+    del d_batch, d_masks
+
+    single = None
+    if not args.no_single:
+        fps1, us1 = run_single_sp(spg, torch, cases[0], pool_packed, args.seq_frames, 5, dev,
+                                  stream)
+        single = {"workload": f"one paper-scale frame SP, {args.seq_frames}-frame learning "
+                              "sequence, state in one 16-CTA cluster's shared memory, L2 flushed "
+                              "between steps",
+                  "frames_per_s": fps1, "us_per_frame": us1}
 
     peak, peak_kind = read_peaks()
-    per_launch = algorithmic_bytes_per_frame(case, learn=True)
-    kernel_launches_per_step = n
-    avg_launch_s = (ms / 1000.0) / kernel_launches_per_step
-    achieved = per_launch / avg_launch_s / 1e9
+    per_launch = sum(algorithmic_bytes_per_frame(c) for c in cases)
+    achieved = per_launch / (ms / 1000.0) / 1e9  # one batch-step launch per step
     traffic = read_traffic()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps_cpu, done = time_oracle(case, frames_u8, args.cpu_seconds)
+        fps_cpu, done = oracle_sample(cases[:16], pool_u8, args.cpu_seconds)
         cpu = {"value": fps_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} frames of the same 500-frame learning sequence, one thread, ~{args.cpu_seconds:.0f} s"}
+               "sample": f"{done} SP frames of the same workload (first 16 instances in step "
+                         f"order), one thread, ~{args.cpu_seconds:.0f} s"}
 
     if rank == 0:
         line = {
@@ -315,22 +391,24 @@ def main():
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "columns": case.C, "synapses": case.S,
-                       "input": "960x540", "winners_set_size": case.k, "learn": True,
-                       "frames_per_step": n, "instances_per_gpu": 1,
-                       "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"{world} independent instance(s), one per GPU"},
-            "column_updates_per_s": value * case.C,
-            "us_per_frame": ms * 1000.0 / n,
-            "roofline": {"bound": "hbm", "kernel": STEP_KERNEL, "achieved": achieved,
+            "config": {"workload": WORKLOAD, "columns": 1024, "synapses": 256,
+                       "input": "960x540", "winners_set_size": 40, "learn": True,
+                       "instances_per_gpu": n, "frames_per_step_per_instance": 1,
+                       "state_bytes_per_gpu": int(sum(c.C * c.S * 8 for c in cases)),
+                       "l2": "inputs larger than L2 (SP state streamed every step), no flush",
+                       "parallelism": f"{world} GPU(s) x {n} independent instances"},
+            "column_updates_per_s": value * 1024,
+            "roofline": {"bound": "hbm", "kernel": "sp_batch_step_kernel", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_launch": per_launch,
-                         "avg_launch_us": avg_launch_s * 1e6},
+                         "avg_launch_us": ms * 1000.0},
             "e2e": {"value": e2e_value, "unit": "frames/s",
-                    "h2d_bytes_per_step": int(n * nw * 4), "d2h_bytes_per_step": int(n * mw * 4)},
+                    "h2d_bytes_per_step": int(info["frame_words"] * 4),
+                    "d2h_bytes_per_step": int(mw * 4)},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "single_sp": single,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -209,6 +209,71 @@ SP_API sp_status sp_sync(sp_handle* h);
  * the work running. */
 SP_API sp_status sp_set_timeout_ms(sp_handle* h, uint32_t ms);
 
+/* ---- Batches of SPs ------------------------------------------------------
+ *
+ * The paper's 'Multiple HTMs' setup (Section 3, "Outer Structure") runs one
+ * SP per object class; a video server runs one per stream.  A batch steps
+ * many independent SPs -- of any shapes and parameters -- with one kernel
+ * launch per frame: every member computes one frame (overlap, inhibition,
+ * learning) exactly as sp_compute would, and its results are bit-identical
+ * to running it alone.
+ *
+ * Members are existing handles on the same device.  While a handle belongs
+ * to a batch, its own compute calls and getters return SP_EBUSY; the batch
+ * advances all members in lockstep.  sp_batch_destroy hands the members back
+ * (state, overlaps, last active list and pending learning intact).
+ *
+ * Layout: one "batch frame" holds every member's packed input frame, member
+ * i at word offset frame_off[i] (16-byte aligned), frame_words words in all;
+ * one "batch mask record" holds every member's active mask, member i at word
+ * offset mask_off[i], mask_words words in all (sp_batch_offsets). */
+typedef struct sp_batch sp_batch;
+
+typedef struct {
+  uint32_t members;
+  uint32_t ctas;          /* CTAs of one batch step launch */
+  uint64_t frame_words;   /* words of one batch frame */
+  uint64_t mask_words;    /* words of one batch mask record */
+  uint64_t frames;        /* batch frames computed so far */
+} sp_batch_info;
+
+/* Group n distinct handles (none already batched, all on one device) into a
+ * batch.  Pending learning of each member is applied first.  The handles
+ * stay owned by the caller and must outlive the batch.  SP_EINVAL for a bad
+ * member list, SP_EBUSY if a member is already batched. */
+SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch** out);
+
+/* Wait (bounded) for the batch's work and release the members.  NULL-safe. */
+SP_API void sp_batch_destroy(sp_batch* b);
+
+SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out);
+
+/* Per-member word offsets inside a batch frame and a batch mask record
+ * (arrays of `members` entries; either may be NULL). */
+SP_API sp_status sp_batch_offsets(const sp_batch* b, uint64_t* frame_off, uint64_t* mask_off);
+
+/* n_frames batch frames on the device, batch frame t at
+ * d_frames + t * frame_stride_words (stride >= frame_words, d_frames 16-byte
+ * aligned); every member computes its frames in order with the same learn
+ * flag, one launch per batch frame (recorded as a CUDA graph for repeated
+ * calls).  If d_masks is not NULL, batch frame t's mask record goes to
+ * d_masks + t * mask_stride_words (stride >= mask_words).  Asynchronous on
+ * `stream` (NULL = the batch's own stream, cudaStreamLegacy = the legacy
+ * default stream). */
+SP_API sp_status sp_batch_compute_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                         uint64_t frame_stride_words, int learn, uint32_t* d_masks,
+                                         uint64_t mask_stride_words, void* stream);
+
+/* The same from host memory: batch frames copied in (pinned memory gives
+ * overlapped copies), mask records copied back to h_masks (NULL = not
+ * returned).  Synchronous: returns when the masks are in host memory. */
+SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_t n_frames,
+                                  uint64_t frame_stride_words, int learn, uint32_t* h_masks,
+                                  uint64_t mask_stride_words);
+
+/* Wait (bounded) until the batch's enqueued work has finished. */
+SP_API sp_status sp_batch_sync(sp_batch* b);
+
 /* ---- Allocation-free frame (no counterpart in the paper) ------------------
  *
  * sp_step_noalloc runs one frame -- overlap, inhibition and, if learn != 0,

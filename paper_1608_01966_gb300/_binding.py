@@ -39,6 +39,11 @@ class SpConfig(ct.Structure):
     ]
 
 
+class SpBatchInfo(ct.Structure):
+    _fields_ = [("members", ct.c_uint32), ("ctas", ct.c_uint32), ("frame_words", ct.c_uint64),
+                ("mask_words", ct.c_uint64), ("frames", ct.c_uint64)]
+
+
 class SpInfo(ct.Structure):
     _fields_ = [
         ("num_columns", ct.c_uint32), ("synapses_per_column", ct.c_uint32),
@@ -84,6 +89,16 @@ def lib():
         L.sp_set_timeout_ms.argtypes = [vp, ct.c_uint32]
         L.sp_status_str.argtypes = [ct.c_int]
         L.sp_step_noalloc.argtypes = [ct.POINTER(SpConfig), vp, vp, vp, vp, ct.c_int, vp, vp, vp]
+        L.sp_batch_create.argtypes = [ct.POINTER(vp), ct.c_uint32, ct.POINTER(vp)]
+        L.sp_batch_destroy.argtypes = [vp]
+        L.sp_batch_destroy.restype = None
+        L.sp_batch_get_info.argtypes = [vp, ct.POINTER(SpBatchInfo)]
+        L.sp_batch_offsets.argtypes = [vp, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]
+        L.sp_batch_compute_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, ct.c_int, vp,
+                                              ct.c_uint64, vp]
+        L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
+                                       ct.c_uint64]
+        L.sp_batch_sync.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -243,6 +258,58 @@ def sp_step_noalloc(cfg, d_idx, d_perm, d_boost, d_input, learn, d_active_mask, 
     _check(lib().sp_step_noalloc(ct.byref(cfg), _addr(d_idx), _addr(d_perm), _addr(d_boost),
                                  _addr(d_input), 1 if learn else 0, _addr(d_active_mask),
                                  _addr(d_active_list), _stream(stream)), "sp_step_noalloc")
+
+
+def sp_batch_create(members):
+    arr = (ct.c_void_p * len(members))(*[m.value if isinstance(m, ct.c_void_p) else m
+                                          for m in members])
+    b = ct.c_void_p()
+    _check(lib().sp_batch_create(arr, len(members), ct.byref(b)), "sp_batch_create")
+    return b
+
+
+def sp_batch_destroy(b):
+    lib().sp_batch_destroy(b)
+
+
+def sp_batch_get_info(b):
+    info = SpBatchInfo()
+    _check(lib().sp_batch_get_info(b, ct.byref(info)), "sp_batch_get_info")
+    return {f: getattr(info, f) for f, _ in SpBatchInfo._fields_}
+
+
+def sp_batch_offsets(b):
+    n = sp_batch_get_info(b)["members"]
+    fo = np.zeros(n, np.uint64)
+    mo = np.zeros(n, np.uint64)
+    _check(lib().sp_batch_offsets(b, fo.ctypes.data_as(ct.POINTER(ct.c_uint64)),
+                                  mo.ctypes.data_as(ct.POINTER(ct.c_uint64))), "sp_batch_offsets")
+    return fo, mo
+
+
+def sp_batch_compute_device(b, d_frames, n_frames, stride_words, learn, d_masks=None,
+                            mask_stride_words=0, stream=None):
+    _check(lib().sp_batch_compute_device(b, _addr(d_frames), n_frames, stride_words,
+                                         1 if learn else 0, _addr(d_masks), mask_stride_words,
+                                         _stream(stream)), "sp_batch_compute_device")
+
+
+def sp_batch_compute(b, frames, learn, masks_out=None):
+    """frames: uint32 [n][stride] host batch frames; masks_out: uint32 [n][mstride] or None."""
+    if frames.dtype != np.uint32 or frames.ndim != 2 or not frames.flags.c_contiguous:
+        raise ValueError("frames must be a C-contiguous uint32 [n][stride] array")
+    pm, ms = None, 0
+    if masks_out is not None:
+        if masks_out.dtype != np.uint32 or masks_out.ndim != 2 or not masks_out.flags.c_contiguous:
+            raise ValueError("masks_out must be a C-contiguous uint32 [n][stride] array")
+        pm, ms = masks_out.ctypes.data_as(_u32p), masks_out.shape[1]
+    _check(lib().sp_batch_compute(b, frames.ctypes.data_as(_u32p), frames.shape[0],
+                                  frames.shape[1], 1 if learn else 0, pm, ms), "sp_batch_compute")
+    return masks_out
+
+
+def sp_batch_sync(b):
+    _check(lib().sp_batch_sync(b), "sp_batch_sync")
 
 
 def sp_kernel_launch_count():

@@ -8,6 +8,7 @@
 // learning over to the next frame's kernel (deferred learning).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -90,6 +91,13 @@ bool all_ones(const float* v, size_t n);
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
 constexpr int kSlots = 2;
 constexpr uint32_t kGraphMinFrames = 4;  // shorter sequences are launched directly
+constexpr uint32_t kSeqMinFrames = 8;    // shorter sequences use the per-frame kernel
+constexpr size_t kSeqSmemLimit = 226u * 1024u;  // 227 KiB per CTA, less static shared memory
+
+bool seq_enabled() {
+  const char* s = std::getenv("SP_DISABLE_CLUSTER");
+  return !(s && s[0] == '1');
+}
 constexpr size_t kGraphCacheSize = 8;
 
 // A recorded frame sequence is valid for exactly the buffers, sizes and
@@ -102,9 +110,11 @@ struct GraphKey {
   int cur;
   bool pending;
   bool unit_boost;  // selects the histogram path baked into the recorded launches
+  uint64_t mstride; // mask stride (batches)
   bool operator==(const GraphKey& o) const {
     return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
-           cur == o.cur && pending == o.pending && unit_boost == o.unit_boost;
+           cur == o.cur && pending == o.pending && unit_boost == o.unit_boost &&
+           mstride == o.mstride;
   }
 };
 
@@ -157,6 +167,11 @@ struct sp_handle {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream used only for recording
   uint64_t graph_clock = 0;
+  sp_batch* batch = nullptr;  // set while the handle is a member of a batch
+  // persistent cluster path for frame sequences (state in shared memory)
+  bool seq_ok = false;
+  uint32_t seq_Q = 0, seq_Cq = 0, seq_band_max = 0;
+  size_t seq_smem = 0;
 };
 
 namespace {
@@ -240,6 +255,49 @@ void free_handle(sp_handle* h) {
   delete h;
 }
 
+// Decide whether whole frame sequences of this SP can run in one persistent
+// cluster launch: Q CTAs of Cq columns (a multiple of 32) must hold their
+// pools, permanences and input bands in shared memory, and the device must
+// be able to schedule such a cluster.  Failure only disables the path.
+void plan_cluster_path(sp_handle* h, const uint32_t* idx) {
+  h->seq_ok = false;
+  uint32_t Q = (h->C + 31u) / 32u;
+  if (Q > sp::kSeqMaxCluster) Q = sp::kSeqMaxCluster;
+  if (Q < 2u) Q = 2u;
+  const uint32_t Cq = (((h->C + Q - 1u) / Q) + 31u) & ~31u;
+  if (Cq > (uint32_t)sp::kSeqThreads) return;  // one column per thread in the decision
+  uint32_t band_max = 4u;
+  for (uint32_t q = 0; q < Q; ++q) {
+    const uint32_t c0 = q * Cq;
+    if (c0 >= h->C) break;
+    const uint32_t c1 = std::min(h->C, c0 + Cq);
+    uint32_t mn = 0xffffffffu, mx = 0u;
+    for (size_t e = (size_t)c0 * h->S; e < (size_t)c1 * h->S; ++e) {
+      mn = std::min(mn, idx[e]);
+      mx = std::max(mx, idx[e]);
+    }
+    const uint32_t w_lo = (mn >> 5) & ~3u;
+    const uint32_t w_hi = ((mx >> 5) + 4u) & ~3u;
+    band_max = std::max(band_max, w_hi - w_lo);
+  }
+  const size_t smem = sp::seq_smem_bytes(h->C, h->S, Cq, band_max);
+  if (smem > kSeqSmemLimit) return;
+  if (sp::seq_kernel_init(smem) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  int clusters = 0;
+  if (sp::seq_max_active_clusters(Q, smem, &clusters) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return;
+  }
+  h->seq_ok = true;
+  h->seq_Q = Q;
+  h->seq_Cq = Cq;
+  h->seq_band_max = band_max;
+  h->seq_smem = smem;
+}
+
 // Allocate the device block, streams and events; copy idx/perm/boost.
 sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, const float* perm,
                       const float* boost) {
@@ -296,6 +354,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
   SP_CUDA(cudaStreamSynchronize(h->stream));
   h->grid = sp::step_grid(h->C);
+  plan_cluster_path(h, idx);
   return SP_OK;
 }
 
@@ -431,9 +490,50 @@ sp_status enqueue_sequence(sp_handle* h, cudaStream_t st, const uint32_t* x_base
 // stream first.  Short sequences, or SP_DISABLE_GRAPHS=1, launch directly.
 sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
                        int learn, uint32_t* masks) {
+  if (h->seq_ok && n >= kSeqMinFrames && seq_enabled()) {
+    sp::SeqArgs a{};
+    a.idx = h->d_idx;
+    a.perm = h->d_perm;
+    a.boost = h->d_boost;
+    a.frames = x_base;
+    a.stride = stride;
+    a.n_frames = n;
+    a.learn = learn;
+    if (h->pending) {
+      a.pend_mask = h->d_mask[h->cur ^ 1];
+      a.pend_x = h->d_xsave[h->cur ^ 1];
+    }
+    a.masks_out = masks;
+    a.mask_last = h->d_mask[h->cur];
+    a.result = h->d_result;
+    a.ov_out = h->d_ov;
+    a.C = h->C;
+    a.S = h->S;
+    a.n_words = h->n_words;
+    a.mask_words = h->mask_words;
+    a.Cq = h->seq_Cq;
+    a.band_max = h->seq_band_max;
+    a.vec16 = (h->n_words % 4u == 0u && stride % 4u == 0u &&
+               reinterpret_cast<uintptr_t>(x_base) % 16u == 0u) ? 1u : 0u;
+    a.thr = h->cfg.connect_threshold;
+    a.inc = h->cfg.perm_inc;
+    a.dec = h->cfg.perm_dec;
+    a.min_overlap = h->cfg.min_overlap;
+    a.k = h->cfg.winners_set_size;
+    a.inhibition = h->cfg.inhibition;
+    a.gw = h->cfg.col_grid_w;
+    a.gh = h->cfg.col_grid_h;
+    a.radius = h->cfg.local_radius;
+    a.unit_boost = h->unit_boost ? 1u : 0u;
+    SP_CUDA(sp::launch_seq(a, h->seq_Q, h->seq_smem, h->stream));
+    h->pending = false;  // learning of every frame is already applied
+    h->cur ^= 1;
+    h->frames += n;
+    return SP_OK;
+  }
   if (n < kGraphMinFrames || !graphs_enabled())
     return enqueue_sequence(h, h->stream, x_base, n, stride, learn, masks);
-  const GraphKey key{x_base, n, stride, learn, masks, h->cur, h->pending, h->unit_boost};
+  const GraphKey key{x_base, n, stride, learn, masks, h->cur, h->pending, h->unit_boost, 0};
   GraphEntry* e = nullptr;
   for (auto& g : h->graphs)
     if (g.key == key) e = &g;
@@ -579,7 +679,10 @@ SP_API sp_status sp_create_from_state(const sp_config* cfg, const uint32_t* idx,
   return SP_OK;
 }
 
-SP_API void sp_destroy(sp_handle* h) { free_handle(h); }
+SP_API void sp_destroy(sp_handle* h) {
+  if (h && h->batch) return;  // still a batch member: the batch must be destroyed first
+  free_handle(h);
+}
 
 SP_API sp_status sp_get_info(const sp_handle* h, sp_info* out) {
   if (!h || !out) return fail(SP_EINVAL, "NULL argument");
@@ -597,6 +700,7 @@ SP_API sp_status sp_get_info(const sp_handle* h, sp_info* out) {
 
 SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn) {
   if (!h || !input_bits) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   sp_status s = use_stream(h, h->own_stream);
   if (s != SP_OK) return s;
@@ -608,6 +712,7 @@ SP_API sp_status sp_compute(sp_handle* h, const uint32_t* input_bits, int learn)
 
 SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int learn, void* stream) {
   if (!h || !d_bits) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   if (reinterpret_cast<uintptr_t>(d_bits) % 4u) return fail(SP_EINVAL, "d_bits not 4-byte aligned");
   DeviceGuard g(h->device);
   sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
@@ -620,6 +725,7 @@ SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames
                                           uint64_t stride, int learn, uint32_t* d_active_masks,
                                           void* stream) {
   if (!h || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   if (n_frames == 0) return SP_OK;
   if (stride < h->n_words) return fail(SP_EINVAL, "frame stride %llu < %u words", (unsigned long long)stride, h->n_words);
   if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_active_masks) % 4u)
@@ -633,6 +739,7 @@ SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames
 SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint32_t n_frames,
                                    uint64_t stride, int learn, uint32_t* h_active_masks) {
   if (!h || (!h_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   if (n_frames == 0) return SP_OK;
   if (stride < h->n_words) return fail(SP_EINVAL, "frame stride %llu < %u words", (unsigned long long)stride, h->n_words);
   DeviceGuard g(h->device);
@@ -686,6 +793,7 @@ SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint3
 
 SP_API sp_status sp_active_columns(sp_handle* h, uint32_t* out, uint32_t cap, uint32_t* n) {
   if (!h || !n || (!out && cap)) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(h->h_result, h->d_result, ((size_t)h->max_active + 1) * 4,
                           cudaMemcpyDeviceToHost, h->stream));
@@ -701,6 +809,7 @@ SP_API sp_status sp_active_columns(sp_handle* h, uint32_t* out, uint32_t cap, ui
 
 SP_API sp_status sp_get_overlaps(sp_handle* h, float* out) {
   if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(out, h->d_ov, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
   return wait_handle(h);
@@ -708,6 +817,7 @@ SP_API sp_status sp_get_overlaps(sp_handle* h, float* out) {
 
 SP_API sp_status sp_get_permanences(sp_handle* h, float* out) {
   if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   sp_status s = flush_learning(h);
   if (s != SP_OK) return s;
@@ -718,6 +828,7 @@ SP_API sp_status sp_get_permanences(sp_handle* h, float* out) {
 
 SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out) {
   if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(out, h->d_idx, (size_t)h->C * h->S * 4, cudaMemcpyDeviceToHost,
                           h->stream));
@@ -726,6 +837,7 @@ SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out) {
 
 SP_API sp_status sp_get_boost(sp_handle* h, float* out) {
   if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(out, h->d_boost, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
   return wait_handle(h);
@@ -733,6 +845,7 @@ SP_API sp_status sp_get_boost(sp_handle* h, float* out) {
 
 SP_API sp_status sp_set_boost(sp_handle* h, const float* boost) {
   if (!h || !boost) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   if (!finite_nonneg(boost, h->C)) return fail(SP_EINVAL, "boost must be finite and >= 0");
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
@@ -771,5 +884,386 @@ SP_API const char* sp_status_str(sp_status s) {
 }
 
 SP_API const char* sp_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"
+
+// ============================== batches ======================================
+
+struct sp_batch {
+  std::vector<sp_handle*> members;
+  int device = 0;
+  void* d_block = nullptr;  // descriptors + CTA map
+  sp::BatchDesc* d_desc = nullptr;
+  uint32_t* d_cta_inst = nullptr;
+  uint32_t n_ctas = 0, max_C = 0;
+  uint64_t frame_words = 0, mask_words = 0;
+  std::vector<uint64_t> frame_off, mask_off;
+  int cur = 0;
+  bool pending = false;
+  uint64_t frames = 0;
+  uint32_t timeout_ms = 10000;
+  cudaStream_t own_stream = nullptr, stream = nullptr, cap_stream = nullptr;
+  cudaEvent_t ev_switch = nullptr, ev_wait = nullptr;
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  // sp_batch_compute staging
+  uint32_t* d_stage = nullptr;
+  uint32_t* d_mstage = nullptr;
+  uint32_t stage_frames = 0;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
+};
+
+namespace {
+
+// CTAs given to one SP in a batch launch: every warp takes several columns
+// so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
+// per-CTA ticket and fence cost small).  SP_BATCH_COLS_PER_WARP overrides.
+uint32_t batch_ctas(uint32_t C, uint32_t S) {
+  uint32_t cpw = S >= 128u ? 4u : (S >= 32u ? 8u : 16u);
+  if (const char* e = std::getenv("SP_BATCH_COLS_PER_WARP")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 1 && v <= 64) cpw = (uint32_t)v;
+  }
+  const uint32_t per_cta = (uint32_t)sp::kStepWarps * cpw;
+  return (C + per_cta - 1u) / per_cta;
+}
+
+sp_status batch_wait(sp_batch* b) {
+  SP_CUDA(cudaEventRecord(b->ev_wait, b->stream));
+  const auto deadline =
+      std::chrono::steady_clock::now() + std::chrono::milliseconds(b->timeout_ms);
+  for (uint32_t spin = 0;; ++spin) {
+    const cudaError_t e = cudaEventQuery(b->ev_wait);
+    if (e == cudaSuccess) return SP_OK;
+    if (e != cudaErrorNotReady)
+      return fail(SP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+    if (std::chrono::steady_clock::now() > deadline)
+      return fail(SP_ETIMEOUT, "wait exceeded %u ms", b->timeout_ms);
+    if (spin < 2000)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+void free_batch(sp_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->s_in) cudaStreamSynchronize(b->s_in);
+  if (b->s_out) cudaStreamSynchronize(b->s_out);
+  for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);
+  for (int i = 0; i < kSlots; ++i) {
+    if (b->ev_h2d[i]) cudaEventDestroy(b->ev_h2d[i]);
+    if (b->ev_comp[i]) cudaEventDestroy(b->ev_comp[i]);
+    if (b->ev_d2h[i]) cudaEventDestroy(b->ev_d2h[i]);
+  }
+  if (b->s_in) cudaStreamDestroy(b->s_in);
+  if (b->s_out) cudaStreamDestroy(b->s_out);
+  if (b->d_stage) cudaFree(b->d_stage);
+  if (b->d_mstage) cudaFree(b->d_mstage);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->ev_switch) cudaEventDestroy(b->ev_switch);
+  if (b->ev_wait) cudaEventDestroy(b->ev_wait);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  if (b->d_block) cudaFree(b->d_block);
+  for (sp_handle* h : b->members) {
+    if (h->batch != b) continue;
+    h->cur = b->cur;  // the members' buffers follow the batch's parity
+    h->pending = b->pending;
+    h->stream = h->own_stream;
+    h->frames += b->frames;
+    h->batch = nullptr;
+  }
+  delete b;
+}
+
+sp_status batch_use_stream(sp_batch* b, cudaStream_t s) {
+  if (!s) s = b->own_stream;
+  if (s != b->stream) {
+    SP_CUDA(cudaEventRecord(b->ev_switch, b->stream));
+    SP_CUDA(cudaStreamWaitEvent(s, b->ev_switch, 0));
+    b->stream = s;
+  }
+  return SP_OK;
+}
+
+// Enqueue n batch frames on `st` from the batch's current (parity, pending).
+sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, uint32_t n,
+                        uint64_t stride, int learn, uint32_t* masks, uint64_t mstride) {
+  for (uint32_t t = 0; t < n; ++t) {
+    sp::BatchArgs a{};
+    a.desc = b->d_desc;
+    a.cta_inst = b->d_cta_inst;
+    a.frames = x_base + (uint64_t)t * stride;
+    a.prev_frames = t ? x_base + (uint64_t)(t - 1) * stride : nullptr;
+    a.masks_out = masks ? masks + (uint64_t)t * mstride : nullptr;
+    a.cur = (uint32_t)b->cur;
+    a.pending = b->pending ? 1u : 0u;
+    a.learn = learn ? 1u : 0u;
+    a.save = (t + 1 == n) ? 1u : 0u;
+    SP_CUDA(sp::launch_batch_step(a, b->n_ctas, b->max_C, st));
+    b->pending = learn != 0;
+    b->cur ^= 1;
+  }
+  return SP_OK;
+}
+
+sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t stride, int learn,
+                    uint32_t* masks, uint64_t mstride) {
+  if (n < kGraphMinFrames || !graphs_enabled()) {
+    sp_status s = batch_enqueue(b, b->stream, x_base, n, stride, learn, masks, mstride);
+    if (s == SP_OK) b->frames += n;
+    return s;
+  }
+  const GraphKey key{x_base, n, stride, learn, masks, b->cur, b->pending, false, mstride};
+  GraphEntry* e = nullptr;
+  for (auto& g : b->graphs)
+    if (g.key == key) e = &g;
+  if (!e) {
+    if (!b->cap_stream) SP_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    const int cur0 = b->cur;
+    const bool pending0 = b->pending;
+    SP_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sp_status s = batch_enqueue(b, b->cap_stream, x_base, n, stride, learn, masks, mstride);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
+    sp::g_launches.fetch_sub(n, std::memory_order_relaxed);
+    b->cur = cur0;
+    b->pending = pending0;
+    if (s != SP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (ec != cudaSuccess) return fail(SP_ECUDA, "recording the batch sequence: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(SP_ECUDA, "instantiating the batch sequence: %s", cudaGetErrorString(ei));
+    if (b->graphs.size() >= kGraphCacheSize) {
+      size_t lru = 0;
+      for (size_t i = 1; i < b->graphs.size(); ++i)
+        if (b->graphs[i].last_use < b->graphs[lru].last_use) lru = i;
+      cudaGraphExecDestroy(b->graphs[lru].exec);
+      b->graphs.erase(b->graphs.begin() + lru);
+    }
+    b->graphs.push_back(GraphEntry{key, exec, 0});
+    e = &b->graphs.back();
+  }
+  e->last_use = ++b->graph_clock;
+  SP_CUDA(cudaGraphLaunch(e->exec, b->stream));
+  sp::g_launches.fetch_add(n, std::memory_order_relaxed);
+  b->pending = learn != 0;
+  b->cur ^= (int)(n & 1u);
+  b->frames += n;
+  return SP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch** out) {
+  if (!out) return fail(SP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!members || n == 0) return fail(SP_EINVAL, "empty member list");
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!members[i]) return fail(SP_EINVAL, "member %u is NULL", i);
+    if (members[i]->batch) return fail(SP_EBUSY, "member %u is already batched", i);
+    if (members[i]->device != members[0]->device)
+      return fail(SP_EINVAL, "members live on different devices");
+    for (uint32_t j = 0; j < i; ++j)
+      if (members[j] == members[i]) return fail(SP_EINVAL, "member %u repeats member %u", i, j);
+  }
+  sp_batch* b = new (std::nothrow) sp_batch();
+  if (!b) return fail(SP_ENOMEM, "host allocation");
+  b->device = members[0]->device;
+  b->timeout_ms = default_timeout_ms();
+  DeviceGuard g(b->device);
+  // apply every member's pending learning so the batch starts with none
+  for (uint32_t i = 0; i < n; ++i) {
+    sp_handle* h = members[i];
+    sp_status s = flush_learning(h);
+    if (s == SP_OK) s = wait_handle(h);
+    if (s != SP_OK) {
+      delete b;
+      return s;
+    }
+  }
+  std::vector<sp::BatchDesc> desc(n);
+  std::vector<uint32_t> cta_inst;
+  uint64_t foff = 0, moff = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    sp_handle* h = members[i];
+    sp::BatchDesc& d = desc[i];
+    d.idx = h->d_idx;
+    d.perm = h->d_perm;
+    d.boost = h->d_boost;
+    d.ov = h->d_ov;
+    d.xsave0 = h->d_xsave[0];
+    d.xsave1 = h->d_xsave[1];
+    d.mask0 = h->d_mask[0];
+    d.mask1 = h->d_mask[1];
+    d.result = h->d_result;
+    d.counter = h->d_counter;
+    d.hist = (h->unit_boost && h->cfg.inhibition == SP_INHIBIT_GLOBAL) ? h->d_hist : nullptr;
+    d.frame_off = foff;
+    d.mask_off = moff;
+    d.C = h->C;
+    d.S = h->S;
+    d.n_words = h->n_words;
+    d.mask_words = h->mask_words;
+    d.thr = h->cfg.connect_threshold;
+    d.inc = h->cfg.perm_inc;
+    d.dec = h->cfg.perm_dec;
+    d.min_overlap = h->cfg.min_overlap;
+    d.k = h->cfg.winners_set_size;
+    d.inhibition = h->cfg.inhibition;
+    d.gw = h->cfg.col_grid_w;
+    d.gh = h->cfg.col_grid_h;
+    d.radius = h->cfg.local_radius;
+    d.cta_first = (uint32_t)cta_inst.size();
+    d.n_ctas = batch_ctas(h->C, h->S);
+    for (uint32_t c = 0; c < d.n_ctas; ++c) cta_inst.push_back(i);
+    b->frame_off.push_back(foff);
+    b->mask_off.push_back(moff);
+    foff += ((uint64_t)h->n_words + 3u) & ~uint64_t(3);  // 16-byte aligned members
+    moff += h->mask_words;
+    b->max_C = std::max(b->max_C, h->C);
+  }
+  b->frame_words = foff;
+  b->mask_words = moff;
+  b->n_ctas = (uint32_t)cta_inst.size();
+  const size_t desc_bytes = align256(sizeof(sp::BatchDesc) * n);
+  cudaError_t e = cudaMalloc(&b->d_block, desc_bytes + cta_inst.size() * 4);
+  if (e == cudaSuccess) {
+    b->d_desc = static_cast<sp::BatchDesc*>(b->d_block);
+    b->d_cta_inst = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_block) + desc_bytes);
+    e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_switch, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_wait, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    b->stream = b->own_stream;
+    e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(sp::BatchDesc) * n, cudaMemcpyHostToDevice,
+                        b->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_cta_inst, cta_inst.data(), cta_inst.size() * 4,
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return fail(e == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA, "batch set-up: %s",
+                cudaGetErrorString(e));
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    members[i]->batch = b;
+    members[i]->pending = false;
+    b->members.push_back(members[i]);
+  }
+  *out = b;
+  return SP_OK;
+}
+
+SP_API void sp_batch_destroy(sp_batch* b) { free_batch(b); }
+
+SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out) {
+  if (!b || !out) return fail(SP_EINVAL, "NULL argument");
+  out->members = (uint32_t)b->members.size();
+  out->ctas = b->n_ctas;
+  out->frame_words = b->frame_words;
+  out->mask_words = b->mask_words;
+  out->frames = b->frames;
+  return SP_OK;
+}
+
+SP_API sp_status sp_batch_offsets(const sp_batch* b, uint64_t* frame_off, uint64_t* mask_off) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    if (frame_off) frame_off[i] = b->frame_off[i];
+    if (mask_off) mask_off[i] = b->mask_off[i];
+  }
+  return SP_OK;
+}
+
+SP_API sp_status sp_batch_compute_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                         uint64_t stride, int learn, uint32_t* d_masks,
+                                         uint64_t mstride, void* stream) {
+  if (!b || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (n_frames == 0) return SP_OK;
+  if (stride < b->frame_words) return fail(SP_EINVAL, "frame stride %llu < %llu words", (unsigned long long)stride, (unsigned long long)b->frame_words);
+  if (d_masks && mstride < b->mask_words) return fail(SP_EINVAL, "mask stride %llu < %llu words", (unsigned long long)mstride, (unsigned long long)b->mask_words);
+  if (reinterpret_cast<uintptr_t>(d_frames) % 16u || reinterpret_cast<uintptr_t>(d_masks) % 4u ||
+      (n_frames > 1 && stride % 4u))
+    return fail(SP_EINVAL, "batch frames must be 16-byte aligned (stride a multiple of 4 words)");
+  DeviceGuard g(b->device);
+  sp_status s = batch_use_stream(b, static_cast<cudaStream_t>(stream));
+  if (s != SP_OK) return s;
+  return batch_run(b, d_frames, n_frames, stride, learn, d_masks, mstride);
+}
+
+SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_t n_frames,
+                                  uint64_t stride, int learn, uint32_t* h_masks, uint64_t mstride) {
+  if (!b || (!h_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (n_frames == 0) return SP_OK;
+  if (stride < b->frame_words) return fail(SP_EINVAL, "frame stride below frame_words");
+  if (h_masks && mstride < b->mask_words) return fail(SP_EINVAL, "mask stride below mask_words");
+  DeviceGuard g(b->device);
+  sp_status s = batch_use_stream(b, b->own_stream);
+  if (s != SP_OK) return s;
+  const uint64_t fw = (b->frame_words + 3u) & ~uint64_t(3);
+  if (!b->d_stage) {
+    // about 64 MiB of staged batch frames per slot
+    uint64_t per = (64ull << 20) / (fw * 4u);
+    b->stage_frames = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(per, kChunkFrames));
+    SP_CUDA(cudaMalloc(&b->d_stage, (size_t)kSlots * b->stage_frames * fw * 4));
+    SP_CUDA(cudaMalloc(&b->d_mstage, (size_t)kSlots * b->stage_frames * b->mask_words * 4));
+    SP_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
+    SP_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < kSlots; ++i) {
+      SP_CUDA(cudaEventCreateWithFlags(&b->ev_h2d[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventCreateWithFlags(&b->ev_comp[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventCreateWithFlags(&b->ev_d2h[i], cudaEventDisableTiming));
+      SP_CUDA(cudaEventRecord(b->ev_comp[i], b->stream));
+      SP_CUDA(cudaEventRecord(b->ev_d2h[i], b->stream));
+    }
+  }
+  const uint32_t cf = b->stage_frames;
+  for (uint32_t f0 = 0, ci = 0; f0 < n_frames; f0 += cf, ++ci) {
+    const int slot = (int)(ci % kSlots);
+    const uint32_t nf = std::min(cf, n_frames - f0);
+    uint32_t* dst = b->d_stage + (size_t)slot * cf * fw;
+    uint32_t* mdst = b->d_mstage + (size_t)slot * cf * b->mask_words;
+    SP_CUDA(cudaStreamWaitEvent(b->s_in, b->ev_comp[slot], 0));
+    SP_CUDA(cudaMemcpy2DAsync(dst, fw * 4, h_frames + (uint64_t)f0 * stride, stride * 4,
+                              b->frame_words * 4, nf, cudaMemcpyHostToDevice, b->s_in));
+    SP_CUDA(cudaEventRecord(b->ev_h2d[slot], b->s_in));
+    SP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_h2d[slot], 0));
+    SP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_d2h[slot], 0));
+    s = batch_run(b, dst, nf, fw, learn, h_masks ? mdst : nullptr, b->mask_words);
+    if (s != SP_OK) return s;
+    SP_CUDA(cudaEventRecord(b->ev_comp[slot], b->stream));
+    if (h_masks) {
+      SP_CUDA(cudaStreamWaitEvent(b->s_out, b->ev_comp[slot], 0));
+      SP_CUDA(cudaMemcpy2DAsync(h_masks + (uint64_t)f0 * mstride, mstride * 4, mdst,
+                                b->mask_words * 4, b->mask_words * 4, nf, cudaMemcpyDeviceToHost,
+                                b->s_out));
+      SP_CUDA(cudaEventRecord(b->ev_d2h[slot], b->s_out));
+    }
+  }
+  if (h_masks) {
+    SP_CUDA(cudaEventRecord(b->ev_switch, b->s_out));
+    SP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_switch, 0));
+  }
+  return batch_wait(b);
+}
+
+SP_API sp_status sp_batch_sync(sp_batch* b) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  DeviceGuard g(b->device);
+  return batch_wait(b);
+}
 
 }  // extern "C"

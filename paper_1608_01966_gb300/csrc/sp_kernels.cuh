@@ -39,6 +39,39 @@ struct StepArgs {
   uint32_t gw, gh, radius;   // column grid for local inhibition
 };
 
+// One SP of a batch (device-resident descriptor; pointers into its handle).
+struct BatchDesc {
+  const uint32_t* idx;
+  float* perm;
+  const float* boost;
+  float* ov;
+  uint32_t *xsave0, *xsave1, *mask0, *mask1;
+  uint32_t* result;
+  uint32_t* counter;
+  uint32_t* hist;       // nullptr unless global inhibition with unit boosts
+  uint64_t frame_off;   // words: this SP's frame inside one batch frame
+  uint64_t mask_off;    // words: this SP's mask inside one batch mask record
+  uint32_t C, S, n_words, mask_words;
+  float thr, inc, dec;
+  uint32_t min_overlap, k, inhibition, gw, gh, radius;
+  uint32_t cta_first, n_ctas;  // this SP's CTAs in the batch grid
+};
+
+// One frame for every SP of a batch.  All members share the buffer parity
+// `cur` and the pending-learning flag (they advance in lockstep).
+struct BatchArgs {
+  const BatchDesc* desc;
+  const uint32_t* cta_inst;     // [grid] SP of each CTA
+  const uint32_t* frames;       // one batch frame (members at their frame_off)
+  const uint32_t* prev_frames;  // the previous batch frame, or nullptr (saved copies)
+  uint32_t* masks_out;          // one batch mask record, or nullptr
+  uint32_t cur, pending, learn;
+  uint32_t save;                // copy each member's frame for next-call learning
+};
+
+cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
+                              cudaStream_t stream);
+
 // Learning of one frame applied on its own (used to flush pending learning).
 struct LearnArgs {
   const uint32_t* idx;
@@ -48,6 +81,39 @@ struct LearnArgs {
   uint32_t C, S;
   float inc, dec;
 };
+
+// A whole frame sequence of one SP in one persistent cluster launch
+// (sp_seq_cluster.cu): the state stays in the cluster's shared memory.
+constexpr int kSeqThreads = 512;
+constexpr uint32_t kSeqMaxCluster = 16;
+
+struct SeqArgs {
+  const uint32_t* idx;        // [C][S]
+  float* perm;                // [C][S], rows that learned are written back at the end
+  const float* boost;         // [C]
+  const uint32_t* frames;     // frame f at frames + f * stride
+  uint64_t stride;
+  uint32_t n_frames;
+  int learn;
+  const uint32_t* pend_mask;  // learning left pending by the previous call, or nullptr
+  const uint32_t* pend_x;     // ... and the frame it belongs to
+  uint32_t* masks_out;        // [n_frames][mask_words] or nullptr
+  uint32_t* mask_last;        // last frame's mask [mask_words]
+  uint32_t* result;           // last frame: [0] count, [1..] ascending winners
+  float* ov_out;              // last frame's boosted overlaps [C]
+  uint32_t C, S, n_words, mask_words;
+  uint32_t Cq;                // columns per CTA (multiple of 32)
+  uint32_t band_max;          // words of the largest per-CTA input band (multiple of 4)
+  uint32_t vec16;             // frames 16-byte aligned with stride, n_words % 4 == 0
+  float thr, inc, dec;
+  uint32_t min_overlap, k, inhibition, gw, gh, radius;
+  uint32_t unit_boost;
+};
+
+size_t seq_smem_bytes(uint32_t C, uint32_t S, uint32_t Cq, uint32_t band_max);
+cudaError_t seq_kernel_init(size_t smem_bytes);
+cudaError_t seq_max_active_clusters(uint32_t Q, size_t smem_bytes, int* out);
+cudaError_t launch_seq(const SeqArgs& a, uint32_t Q, size_t smem_bytes, cudaStream_t stream);
 
 // Dynamic shared memory of the fused kernel for C columns.
 size_t step_smem_bytes(uint32_t C);

@@ -93,3 +93,45 @@ def blob_frames(n, W=960, H=540, seed=BASE_SEED + 2, start=0):
 
 def pack(frames):
     return synth.pack_frames(frames)
+
+
+def uneven_cases(n, seed=BASE_SEED + 4, c_range=(128, 4096), s_range=(16, 256),
+                 n_in_range=(256, 16384)):
+    """Independent SPs of uneven shapes: columns, synapses per column and input
+    bits drawn uniformly (integers) from the ranges, uniform pools,
+    perms U[0.1,0.3], threshold 0.2, min_overlap 4, global inhibition with
+    k = 2% of the columns rounded half up (at least 1).  Returns (cases,
+    densities): each SP's input density is drawn from U[2%, 20%]."""
+    cases, dens = [], []
+    for i in range(n):
+        st = synth.derive_seed(seed, synth.PURPOSE_SHAPE, i)
+        r, st2 = synth.splitmix64(st, 4)
+        C = c_range[0] + r[0] % (c_range[1] - c_range[0] + 1)
+        n_in = n_in_range[0] + r[2] % (n_in_range[1] - n_in_range[0] + 1)
+        S = min(s_range[0] + r[1] % (s_range[1] - s_range[0] + 1), n_in)
+        p = 0.02 + 0.18 * ((r[3] >> 11) / float(1 << 53))
+        k = max(1, (2 * C + 50) // 100)
+        inst = synth.derive_seed(seed, synth.PURPOSE_INSTANCE, i)
+        idx = synth.pool_uniform(synth.derive_seed(inst, synth.PURPOSE_POOL, 0), C, S, n_in)
+        perm = synth.perm_uniform(synth.derive_seed(inst, synth.PURPOSE_PERM, 0), (C, S), 0.1, 0.3)
+        cases.append(Case(f"uneven{i}", n_in, 1, C, S, idx, perm, np.ones(C, np.float32), k=k,
+                          min_overlap=4))
+        dens.append(p)
+    return cases, dens
+
+
+def bernoulli_frames(case_index, n_in, p, n, seed=BASE_SEED + 4, start=0):
+    inst = synth.derive_seed(seed, synth.PURPOSE_INSTANCE, case_index)
+    return np.stack([synth.frame_bernoulli(synth.derive_seed(inst, synth.PURPOSE_FRAME, t), n_in, p)
+                     for t in range(start, start + n)])
+
+
+def batch_frames(per_member_packed, frame_off, frame_words):
+    """Assemble batch frames: per_member_packed[i] is uint32 [n][words_i];
+    returns uint32 [n][frame_words] with member i at word offset frame_off[i]."""
+    n = per_member_packed[0].shape[0]
+    out = np.zeros((n, frame_words), np.uint32)
+    for i, pk in enumerate(per_member_packed):
+        o = int(frame_off[i])
+        out[:, o:o + pk.shape[1]] = pk
+    return out

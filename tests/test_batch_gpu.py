@@ -1,0 +1,145 @@
+"""Batches of independent SPs (one launch per batch frame) against the CPU
+oracle run on each member alone, and against the members run alone on the
+GPU.  Bar: bit-exact, as for single SPs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1608_01966_gb300 as spg  # noqa: E402
+from paper_1608_01966_gb300 import synth, workloads as wl  # noqa: E402
+from helpers import dense, first_diff, oracle_run  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _member_frames(cases, dens, n):
+    return [wl.bernoulli_frames(i, c.n_in, dens[i], n) for i, c in enumerate(cases)]
+
+
+def _run_batch(cases, frames_u8, learn, calls, boosts=None):
+    """Create handles + batch, run the batch frames split into `calls` (list of
+    frame counts), return per-member active [n][C] and final perms."""
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    n = frames_u8[0].shape[0]
+    fw = (info["frame_words"] + 3) // 4 * 4
+    bf = wl.batch_frames([wl.pack(f) for f in frames_u8], fo, fw)
+    mw = info["mask_words"]
+    stream = torch.cuda.current_stream()
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    dm = torch.zeros((n, mw), dtype=torch.int32, device="cuda")
+    t0 = 0
+    for k in calls:
+        spg.sp_batch_compute_device(b, d[t0], k, fw, learn, dm[t0], mw, stream)
+        t0 += k
+    assert t0 == n
+    spg.sp_batch_sync(b)
+    masks = dm.cpu().numpy().view(np.uint32)
+    spg.sp_batch_destroy(b)
+    acts = [dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+            for i, c in enumerate(cases)]
+    perms = [spg.sp_get_permanences(h) for h in hs]
+    ovs = [spg.sp_get_overlaps(h) for h in hs]
+    for h in hs:
+        spg.sp_destroy(h)
+    return acts, perms, ovs
+
+
+def _check(cases, frames_u8, learn, acts, perms, ovs, label):
+    for i, c in enumerate(cases):
+        act, perm, ov = oracle_run(c, frames_u8[i], learn, want_ov=True)
+        assert first_diff(acts[i], act) is None, f"{label} member {i}: frame/column {first_diff(acts[i], act)}"
+        np.testing.assert_array_equal(perms[i], perm, err_msg=f"{label} member {i} perms")
+        np.testing.assert_array_equal(ovs[i], ov[-1], err_msg=f"{label} member {i} overlaps")
+
+
+def test_batch_of_identical_shapes():
+    cases = [wl.small_case(seed=wl.BASE_SEED + 100 + i) for i in range(8)]
+    frames = [wl.small_frames(24, seed=wl.BASE_SEED + 100 + i) for i in range(8)]
+    acts, perms, ovs = _run_batch(cases, frames, True, [1, 2, 5, 16])
+    _check(cases, frames, True, acts, perms, ovs, "identical")
+
+
+def test_batch_uneven_shapes_and_modes():
+    """Uneven columns / synapses / input sizes, plus members with local
+    inhibition, non-unit boosts and S not a multiple of 4."""
+    cases, dens = wl.uneven_cases(10, c_range=(128, 2048), n_in_range=(256, 4096))
+    g = wl.grid_case("local", 256, 64, 7, W=320, H=180, rf=32, k=5, inhibition=1, radius=4)
+    cases.append(g)
+    dens.append(None)
+    rag = wl.Case("ragged", 1000, 1, 300, 17, synth.pool_uniform(3, 300, 17, 1000),
+                  synth.perm_uniform(4, (300, 17), 0.1, 0.3), synth.perm_uniform(5, (300,), 0.5, 2.0),
+                  k=9, min_overlap=2)
+    cases.append(rag)
+    dens.append(0.3)
+    frames = []
+    for i, c in enumerate(cases):
+        if c.name == "local":
+            frames.append(wl.blob_frames(12, W=320, H=180, seed=11))
+        else:
+            frames.append(wl.bernoulli_frames(i, c.n_in, dens[i], 12))
+    acts, perms, ovs = _run_batch(cases, frames, True, [3, 9])
+    _check(cases, frames, True, acts, perms, ovs, "uneven")
+
+
+def test_batch_equals_members_alone_and_hands_back_state():
+    """A batch, then each member continued alone: the same as the oracle over
+    the whole sequence (pending learning handed back by the batch)."""
+    cases = [wl.frame_case(seed=wl.BASE_SEED + 200 + i) for i in range(3)]
+    frames = [wl.blob_frames(10, seed=wl.BASE_SEED + 200 + i) for i in range(3)]
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_compute(hs[0], wl.pack(frames[0][:1])[0], True)
+    assert e.value.status == 5  # SP_EBUSY while batched
+    fo, mo = spg.sp_batch_offsets(b)
+    info = spg.sp_batch_get_info(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    bf = wl.batch_frames([wl.pack(f[:6]) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    spg.sp_batch_compute_device(b, d, 6, fw, True, None, 0, torch.cuda.current_stream())
+    spg.sp_batch_destroy(b)
+    for i, (c, h) in enumerate(zip(cases, hs)):
+        act, perm, _ = oracle_run(c, frames[i], True)
+        for t in range(6, 10):
+            spg.sp_compute(h, wl.pack(frames[i][t:t + 1])[0], True)
+            np.testing.assert_array_equal(spg.sp_active_columns(h), np.flatnonzero(act[t]))
+        np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+        spg.sp_destroy(h)
+
+
+def test_batch_host_pipelined():
+    """sp_batch_compute: pinned host batch frames in, mask records out."""
+    cases, dens = wl.uneven_cases(6, c_range=(256, 1024), n_in_range=(1024, 8192))
+    frames = _member_frames(cases, dens, 9)
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, info["frame_words"])
+    pinned = torch.from_numpy(bf.view(np.int32)).pin_memory()
+    masks = np.zeros((9, info["mask_words"]), np.uint32)
+    spg.sp_batch_compute(b, pinned.numpy().view(np.uint32), True, masks)
+    spg.sp_batch_destroy(b)
+    for i, c in enumerate(cases):
+        act, perm, _ = oracle_run(c, frames[i], True)
+        got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+        assert first_diff(got, act) is None, f"member {i}"
+        np.testing.assert_array_equal(spg.sp_get_permanences(hs[i]), perm)
+        spg.sp_destroy(hs[i])
+
+
+def test_batch_rejects_bad_members():
+    c = wl.small_case()
+    h = spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost)
+    with pytest.raises(spg.SpError):
+        spg.sp_batch_create([h, h])
+    b = spg.sp_batch_create([h])
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_batch_create([h])
+    assert e.value.status == 5
+    spg.sp_batch_destroy(b)
+    spg.sp_destroy(h)

@@ -102,7 +102,7 @@ def test_small_config_inference_then_learning():
     assert act_l.sum() > 0
 
 
-def test_frame_config_full_500_frames_learning():
+def test_frame_config_full_500_frames_learning(seq_path):
     """960x540 blobbed frames, 1024 columns x 256 windowed synapses, k 40,
     500 frames with learning: the benchmark's workload, in its launch
     configuration, compared on every frame's active set and the final state."""
@@ -112,18 +112,27 @@ def test_frame_config_full_500_frames_learning():
     assert (act.sum(axis=1) == 40).mean() > 0.9  # ties at rank 40 are exercised
 
 
+@pytest.fixture(params=["cluster", "per-frame"])
+def seq_path(request, monkeypatch):
+    """Frame sequences run either in one persistent cluster launch (state in
+    shared memory, when it fits) or as one fused kernel per frame."""
+    if request.param == "per-frame":
+        monkeypatch.setenv("SP_DISABLE_CLUSTER", "1")
+    return request.param
+
+
 @pytest.mark.parametrize("C", [256, 1024, 4096])
-def test_parameter_sweep(C):
+def test_parameter_sweep(C, seq_path):
     """Columns x synapses x min_overlap x k x {global, 9x9 local} on the
-    960x540 blobbed input, 6 learning frames each."""
-    frames = wl.blob_frames(6, seed=wl.BASE_SEED + 3)
+    960x540 blobbed input, 8 learning frames each."""
+    frames = wl.blob_frames(8, seed=wl.BASE_SEED + 3)
     for S in (16, 64, 256):
         for m in (2, 4, 8):
             for k in (8, 32, 128):
                 for inh in (0, 1):
                     case = wl.grid_case("sweep", C, S, wl.BASE_SEED + 3 + C + S, min_overlap=m,
                                         k=k, inhibition=inh, radius=4)
-                    assert_same(case, frames, True, f"C{C} S{S} m{m} k{k} inh{inh}")
+                    assert_same(case, frames, True, f"C{C} S{S} m{m} k{k} inh{inh} {seq_path}")
 
 
 # ------------------------------------------------------------- edge cases ---
@@ -143,18 +152,18 @@ def _bern(n_frames, n_in, p, seed):
                      for t in range(n_frames)])
 
 
-def test_ragged_sizes_scalar_path_and_boost():
+def test_ragged_sizes_scalar_path_and_boost(seq_path):
     """C and n_in not multiples of 32, S not a multiple of 4 (scalar loads),
     non-unit boosts (fp32 products that are not integers), min_overlap 1."""
     boost = synth.perm_uniform(77, (1000,), 0.5, 2.0)
     case = _uniform_case(1000, 17, 1000, 31, boost=boost, min_overlap=1, k=7)
-    assert_same(case, _bern(30, 1000, 0.3, 5), True, "ragged")
+    assert_same(case, _bern(30, 1000, 0.3, 5), True, f"ragged {seq_path}")
 
 
 @pytest.mark.parametrize("k", [0, 1, 5000])
-def test_k_extremes(k):
+def test_k_extremes(k, seq_path):
     case = _uniform_case(2000, 32, 4096, 41, k=k, min_overlap=2)
-    act = assert_same(case, _bern(8, 4096, 0.2, 6), True, f"k={k}")
+    act = assert_same(case, _bern(12, 4096, 0.2, 6), True, f"k={k} {seq_path}")
     if k == 0:
         assert act.sum() == 0
 
@@ -178,7 +187,7 @@ def test_single_column_single_synapse():
     assert_same(case, _bern(20, 33, 0.5, 8), True, "1x1")
 
 
-def test_tie_stress_global():
+def test_tie_stress_global(seq_path):
     """Every synapse connected, Bernoulli(0.5) input: overlaps ~ Bin(16, 0.5)
     over 2048 columns, so dozens of columns tie at the k-th value; plus a
     frame where all columns tie (all-ones input)."""
@@ -188,14 +197,14 @@ def test_tie_stress_global():
     np.testing.assert_array_equal(np.flatnonzero(act[-1]), np.arange(40))
 
 
-def test_local_inhibition_non_square_grid_and_radius_zero():
+def test_local_inhibition_non_square_grid_and_radius_zero(seq_path):
     for gw, gh, r, k in ((40, 25, 3, 5), (33, 7, 0, 1), (16, 16, 20, 9)):
         C = gw * gh
         idx = synth.pool_uniform(synth.derive_seed(91, 1, r), C, 32, 3000)
         perm = synth.perm_uniform(synth.derive_seed(91, 2, r), (C, 32), 0.1, 0.3)
         case = wl.Case("local", 3000, 1, C, 32, idx, perm, np.ones(C, np.float32), k=k,
                        min_overlap=2, inhibition=1, gw=gw, gh=gh, radius=r)
-        assert_same(case, _bern(5, 3000, 0.3, 10 + r), True, f"local {gw}x{gh} r{r}")
+        assert_same(case, _bern(10, 3000, 0.3, 10 + r), True, f"local {gw}x{gh} r{r} {seq_path}")
 
 
 @pytest.mark.parametrize("inh", [0, 1])
@@ -334,5 +343,36 @@ def test_recorded_sequences_replay_and_boost_change():
         spg.sp_sync(h)
         got = dense(dm.cpu().numpy().view(np.uint32), case.C)
         assert first_diff(got, act) is None, f"pass {p}"
+    np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+    spg.sp_destroy(h)
+
+
+def test_pending_learning_hands_over_between_paths():
+    """Single frames (per-frame kernel, learning deferred to the next frame)
+    and sequences (persistent cluster launch) interleaved on one handle: the
+    learning a single frame leaves pending is applied by the next sequence."""
+    case = wl.frame_case(seed=wl.BASE_SEED + 15)
+    frames = wl.blob_frames(40, seed=wl.BASE_SEED + 15)
+    packed = wl.pack(frames)
+    plan = [(0, 3, True), (3, 23, True), (23, 25, True), (25, 35, False), (35, 36, True),
+            (36, 40, True)]
+    perm = case.perm.copy()
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    stream = torch.cuda.current_stream()
+    d = _dev(packed)
+    for a0, a1, learn in plan:
+        act, perm, _ = oracle_run(case, frames[a0:a1], learn, perm=perm)
+        if a1 - a0 < 8:
+            for t in range(a0, a1):
+                spg.sp_compute_device(h, d[t], learn, stream)
+                np.testing.assert_array_equal(spg.sp_active_columns(h),
+                                              np.flatnonzero(act[t - a0]), err_msg=f"t={t}")
+        else:
+            dm = torch.zeros((a1 - a0, 32), dtype=torch.int32, device="cuda")
+            spg.sp_compute_frames_device(h, d[a0], a1 - a0, packed.shape[1], learn, dm, stream)
+            spg.sp_sync(h)
+            got = dense(dm.cpu().numpy().view(np.uint32), case.C)
+            assert first_diff(got, act) is None, f"frames {a0}..{a1}"
+            np.testing.assert_array_equal(spg.sp_active_columns(h), np.flatnonzero(act[-1]))
     np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
     spg.sp_destroy(h)
