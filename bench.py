@@ -66,18 +66,35 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def reduce_max(x, device=None):
+    """Max over ranks of a float (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def instance_seed(rank, i):
+    """Seed of SP i on `rank`: every rank steps its own, distinct SPs."""
+    from paper_1608_01966_gb300 import workloads as wl
+    return wl.BASE_SEED + 2 + 1000003 * rank + 17 * i
+
+
 def make_cases(n, rank):
     """n frame-SP instances with their own seeds (generated in parallel: the
     generators are C code called without the GIL)."""
     from paper_1608_01966_gb300 import workloads as wl
-    seeds = [wl.BASE_SEED + 2 + 1000 * rank + 17 * i for i in range(n)]
+    seeds = [instance_seed(rank, i) for i in range(n)]
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         return list(ex.map(lambda s: wl.frame_case(seed=s), seeds))
 
 
 def make_frame_pool(rank):
     from paper_1608_01966_gb300 import synth, workloads as wl
-    seed = wl.BASE_SEED + 2 + 1000 * rank
+    seed = wl.BASE_SEED + 2 + 1000003 * rank
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         fr = list(ex.map(lambda t: synth.frame_blobbed(
             synth.derive_seed(seed, synth.PURPOSE_FRAME, t), 960, 540), range(FRAME_POOL)))
@@ -329,13 +346,9 @@ def main():
     launches = spg.sp_kernel_launch_count() - launches0
     ms_local = start.elapsed_time(end) / args.steps
     clk = clocks.stop()
+    ms = reduce_max(ms_local, dev)
     if world > 1:
-        t = torch.tensor([ms_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    else:
-        ms = ms_local
     value = world * n / (ms / 1000.0)
 
     # end to end through the public API with host buffers: every step's batch
@@ -352,11 +365,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     spg.sp_batch_compute(b, hf, True, hm)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
     e2e_value = world * n / e2e_s
 
     spg.sp_batch_destroy(b)
