@@ -15,7 +15,10 @@ Frames come from a pool of 64 seeded blobbed frames, instance i taking
 frame (7 i + t) mod 64 at step t.
 
 Secondary (`single_sp`): one such SP over a 500-frame learning sequence
-(the latency-bound serial case), L2 flushed between steps.
+(the latency-bound serial case), L2 flushed between steps.  `serve`: 32
+simulated video streams (Poisson arrivals, 30 fps each, mixed 320x180 /
+640x360 / 960x540) on the library's continuous-batching server -- frames/s
+and per-frame latency p50/p99 in ms, open loop and at saturation.
 
 Under torchrun every rank runs its own 256 instances (no cross-instance
 exchange), so `value` is the sum over ranks (weak scaling).
@@ -56,6 +59,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=INSTANCES)
     ap.add_argument("--seq-frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="open-loop serving run (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -382,6 +387,12 @@ def main():
                               "between steps",
                   "frames_per_s": fps1, "us_per_frame": us1}
 
+    serve = None
+    if args.serve_seconds > 0 and rank == 0:
+        from paper_1608_01966_gb300 import serve_sim
+        serve = serve_sim.simulate(streams=32, fps=30.0, seconds=args.serve_seconds,
+                                   saturate_seconds=3.0)
+
     peak, peak_kind = read_peaks()
     per_launch = sum(algorithmic_bytes_per_frame(c) for c in cases)
     achieved = per_launch / (ms / 1000.0) / 1e9  # one batch-step launch per step
@@ -418,6 +429,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "single_sp": single,
+            "serve": serve,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

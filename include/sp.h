@@ -72,7 +72,7 @@ extern "C" {
 #define SP_API
 #endif
 
-#define SP_ABI_VERSION 1u
+#define SP_ABI_VERSION 2u
 #define SP_MAX_COLUMNS 16384u        /* per SP instance */
 #define SP_MAX_SYNAPSES 65536u       /* per column */
 #define SP_MAX_INPUT_BITS (1u << 28) /* per frame */
@@ -110,6 +110,12 @@ typedef struct {
   uint32_t inhibition;          /* SP_INHIBIT_* */
   uint32_t local_radius;        /* r: (2r+1)^2 window for SP_INHIBIT_LOCAL */
   uint64_t seed;                /* pools / permanences for sp_create */
+  float duty_period;            /* > 0: track each column's active-duty cycle,
+                                   d <- d + (a - d) / duty_period per frame (a = 1 if
+                                   active); 0 = off.  The paper only cites the
+                                   Numenta duty-cycle rules; this moving average is
+                                   the library's own definition. */
+  uint32_t reserved;            /* must be 0 */
 } sp_config;
 
 /* Sizes of a handle's state and buffers. */
@@ -195,6 +201,9 @@ SP_API sp_status sp_get_permanences(sp_handle* h, float* out);
 /* Potential pools [C][S] (host). */
 SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out);
 
+/* Active-duty cycles [C] (host); SP_EINVAL unless duty_period > 0. */
+SP_API sp_status sp_get_duty_cycles(sp_handle* h, float* out);
+
 /* Boosts [C] (host). */
 SP_API sp_status sp_get_boost(sp_handle* h, float* out);
 
@@ -273,6 +282,85 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
 
 /* Wait (bounded) until the batch's enqueued work has finished. */
 SP_API sp_status sp_batch_sync(sp_batch* b);
+
+/* ---- Serving many video streams (continuous batching) ---------------------
+ *
+ * The paper feeds a system frame by frame (Section 2) and runs one SP per
+ * class or video (Section 3); a server does the same for many live streams.
+ * Each stream owns an SP kept on the device (pools, permanences, boosts,
+ * duty cycles) and submits frames as they arrive.  A worker thread inside
+ * the library forms a launch from every stream that has a frame waiting and
+ * no frame on the GPU -- streams that arrive while others are being computed
+ * join the next launch -- with up to two launches in flight on separate
+ * CUDA streams.  Frames of one stream are computed in submission order; each
+ * result is bit-identical to computing the stream alone with sp_compute.
+ * Streams are admitted against a device-memory budget (SP_EBUSY when full). */
+typedef struct sp_server sp_server;
+
+typedef struct {
+  uint32_t abi_version;          /* SP_ABI_VERSION */
+  uint32_t max_streams;          /* open streams at once, 1..4096 */
+  uint32_t queue_depth;          /* frames one stream may have waiting or in flight, 1..64 */
+  uint32_t max_input_words;      /* largest frame of any stream, in 32-bit words */
+  uint64_t device_budget_bytes;  /* device memory the open streams may hold in total */
+  uint32_t max_active;           /* room for one frame's active list; every stream's
+                                    upper bound (k, or C for local inhibition) must fit */
+  uint32_t reserved;             /* 0 */
+} sp_server_config;
+
+typedef struct {
+  uint64_t request_id;     /* from sp_server_submit */
+  uint64_t frame_seq;      /* frame number within its stream, from 0 */
+  uint32_t stream_id;
+  uint32_t n_active;       /* active columns of the frame */
+  uint32_t active_offset;  /* their ascending list starts here in the poll's buffer */
+  sp_status status;        /* SP_OK, or the failure of its launch */
+  double latency_us;       /* submit -> result available on the host */
+} sp_server_result;
+
+typedef struct {
+  uint64_t submitted, completed, launches, frames_in_launches;
+  uint64_t device_bytes_used;
+  uint32_t open_streams;
+  uint32_t reserved;
+  double p50_us, p99_us;   /* latency percentiles over the results since the last reset */
+} sp_server_stats;
+
+/* Create a server on the current device (starts its worker thread). */
+SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out);
+
+/* Stop the worker after the work in flight (bounded wait), free every stream. */
+SP_API void sp_server_destroy(sp_server* s);
+
+/* Open a stream with an SP drawn from cfg (as sp_create) or from caller state
+ * (as sp_create_from_state).  SP_EBUSY if no slot is free or the stream would
+ * exceed the device-memory budget (nothing is allocated then). */
+SP_API sp_status sp_server_open_stream(sp_server* s, const sp_config* cfg, uint32_t* stream_id);
+SP_API sp_status sp_server_open_stream_from_state(sp_server* s, const sp_config* cfg,
+                                                  const uint32_t* idx, const float* perm,
+                                                  const float* boost, uint32_t* stream_id);
+
+/* Close an idle stream (SP_EBUSY while it has frames waiting or in flight)
+ * and release its memory. */
+SP_API sp_status sp_server_close_stream(sp_server* s, uint32_t stream_id);
+
+/* Queue one frame (host memory, the stream's input_words words, copied before
+ * return) with its learn flag.  SP_EBUSY if the stream's queue is full. */
+SP_API sp_status sp_server_submit(sp_server* s, uint32_t stream_id, const uint32_t* frame_bits,
+                                  int learn, uint64_t* request_id);
+
+/* Take up to max_results finished frames (oldest first), their active lists
+ * copied into active[0..active_cap); waits up to wait_ms for the first one.
+ * *n_results may be 0.  Results whose lists do not fit stay queued. */
+SP_API sp_status sp_server_poll(sp_server* s, sp_server_result* results, uint32_t max_results,
+                                uint32_t* active, uint32_t active_cap, uint32_t* n_results,
+                                uint32_t wait_ms);
+
+/* Permanences [C][S] of an idle stream (bounded wait for its frames). */
+SP_API sp_status sp_server_get_permanences(sp_server* s, uint32_t stream_id, float* out);
+
+/* Counters and latency percentiles; reset != 0 restarts the latency window. */
+SP_API sp_status sp_server_get_stats(sp_server* s, sp_server_stats* out, int reset);
 
 /* ---- Allocation-free frame (no counterpart in the paper) ------------------
  *

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-SP_ABI_VERSION = 1
+SP_ABI_VERSION = 2
 SP_MAX_COLUMNS = 16384
 SP_POOL_UNIFORM, SP_POOL_WINDOW, SP_POOL_DENSE = 0, 1, 2
 SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL = 0, 1
@@ -36,12 +36,34 @@ class SpConfig(ct.Structure):
         ("perm_init_hi", ct.c_float), ("min_overlap", ct.c_uint32),
         ("winners_set_size", ct.c_uint32), ("inhibition", ct.c_uint32),
         ("local_radius", ct.c_uint32), ("seed", ct.c_uint64),
+        ("duty_period", ct.c_float), ("reserved", ct.c_uint32),
     ]
 
 
 class SpBatchInfo(ct.Structure):
     _fields_ = [("members", ct.c_uint32), ("ctas", ct.c_uint32), ("frame_words", ct.c_uint64),
                 ("mask_words", ct.c_uint64), ("frames", ct.c_uint64)]
+
+
+class SpServerConfig(ct.Structure):
+    _fields_ = [("abi_version", ct.c_uint32), ("max_streams", ct.c_uint32),
+                ("queue_depth", ct.c_uint32), ("max_input_words", ct.c_uint32),
+                ("device_budget_bytes", ct.c_uint64), ("max_active", ct.c_uint32),
+                ("reserved", ct.c_uint32)]
+
+
+class SpServerResult(ct.Structure):
+    _fields_ = [("request_id", ct.c_uint64), ("frame_seq", ct.c_uint64),
+                ("stream_id", ct.c_uint32), ("n_active", ct.c_uint32),
+                ("active_offset", ct.c_uint32), ("status", ct.c_int),
+                ("latency_us", ct.c_double)]
+
+
+class SpServerStats(ct.Structure):
+    _fields_ = [("submitted", ct.c_uint64), ("completed", ct.c_uint64),
+                ("launches", ct.c_uint64), ("frames_in_launches", ct.c_uint64),
+                ("device_bytes_used", ct.c_uint64), ("open_streams", ct.c_uint32),
+                ("reserved", ct.c_uint32), ("p50_us", ct.c_double), ("p99_us", ct.c_double)]
 
 
 class SpInfo(ct.Structure):
@@ -84,6 +106,7 @@ def lib():
         L.sp_get_permanences.argtypes = [vp, _f32p]
         L.sp_get_pool.argtypes = [vp, _u32p]
         L.sp_get_boost.argtypes = [vp, _f32p]
+        L.sp_get_duty_cycles.argtypes = [vp, _f32p]
         L.sp_set_boost.argtypes = [vp, _f32p]
         L.sp_sync.argtypes = [vp]
         L.sp_set_timeout_ms.argtypes = [vp, ct.c_uint32]
@@ -99,6 +122,19 @@ def lib():
         L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
                                        ct.c_uint64]
         L.sp_batch_sync.argtypes = [vp]
+        L.sp_server_create.argtypes = [ct.POINTER(SpServerConfig), ct.POINTER(vp)]
+        L.sp_server_destroy.argtypes = [vp]
+        L.sp_server_destroy.restype = None
+        L.sp_server_open_stream.argtypes = [vp, ct.POINTER(SpConfig), _u32p]
+        L.sp_server_open_stream_from_state.argtypes = [vp, ct.POINTER(SpConfig), _u32p, _f32p,
+                                                       _f32p, _u32p]
+        L.sp_server_close_stream.argtypes = [vp, ct.c_uint32]
+        L.sp_server_submit.argtypes = [vp, ct.c_uint32, _u32p, ct.c_int,
+                                       ct.POINTER(ct.c_uint64)]
+        L.sp_server_poll.argtypes = [vp, ct.POINTER(SpServerResult), ct.c_uint32, _u32p,
+                                     ct.c_uint32, _u32p, ct.c_uint32]
+        L.sp_server_get_permanences.argtypes = [vp, ct.c_uint32, _f32p]
+        L.sp_server_get_stats.argtypes = [vp, ct.POINTER(SpServerStats), ct.c_int]
         _lib = L
     return _lib
 
@@ -236,6 +272,7 @@ sp_get_permanences = _getter("sp_get_permanences", np.float32,
 sp_get_pool = _getter("sp_get_pool", np.uint32,
                       lambda i: (i["num_columns"], i["synapses_per_column"]))
 sp_get_boost = _getter("sp_get_boost", np.float32, lambda i: (i["num_columns"],))
+sp_get_duty_cycles = _getter("sp_get_duty_cycles", np.float32, lambda i: (i["num_columns"],))
 
 
 def sp_set_boost(h, boost):
@@ -310,6 +347,77 @@ def sp_batch_compute(b, frames, learn, masks_out=None):
 
 def sp_batch_sync(b):
     _check(lib().sp_batch_sync(b), "sp_batch_sync")
+
+
+def sp_server_create(max_streams, queue_depth, max_input_words, device_budget_bytes,
+                     max_active):
+    cfg = SpServerConfig(SP_ABI_VERSION, max_streams, queue_depth, max_input_words,
+                         device_budget_bytes, max_active, 0)
+    s = ct.c_void_p()
+    _check(lib().sp_server_create(ct.byref(cfg), ct.byref(s)), "sp_server_create")
+    return s
+
+
+def sp_server_destroy(s):
+    lib().sp_server_destroy(s)
+
+
+def sp_server_open_stream(s, cfg, state=None):
+    sid = ct.c_uint32()
+    if state is None:
+        _check(lib().sp_server_open_stream(s, ct.byref(cfg), ct.byref(sid)),
+               "sp_server_open_stream")
+    else:
+        idx, perm, boost = state
+        idx, pi = _np_u32(idx)
+        perm, pp = _np_f32(perm)
+        pb = None
+        if boost is not None:
+            boost, pb = _np_f32(boost)
+        _check(lib().sp_server_open_stream_from_state(s, ct.byref(cfg), pi, pp, pb,
+                                                      ct.byref(sid)),
+               "sp_server_open_stream_from_state")
+    return sid.value
+
+
+def sp_server_close_stream(s, sid):
+    _check(lib().sp_server_close_stream(s, sid), "sp_server_close_stream")
+
+
+def sp_server_submit(s, sid, frame_bits, learn):
+    a, p = _np_u32(frame_bits)
+    rid = ct.c_uint64()
+    _check(lib().sp_server_submit(s, sid, p, 1 if learn else 0, ct.byref(rid)),
+           "sp_server_submit")
+    return rid.value
+
+
+def sp_server_poll(s, max_results=256, active_cap=1 << 16, wait_ms=0):
+    """Returns a list of (result dict, active ndarray)."""
+    res = (SpServerResult * max_results)()
+    act = np.zeros(active_cap, np.uint32)
+    n = ct.c_uint32()
+    _check(lib().sp_server_poll(s, res, max_results, act.ctypes.data_as(_u32p), active_cap,
+                                ct.byref(n), wait_ms), "sp_server_poll")
+    out = []
+    for i in range(n.value):
+        r = res[i]
+        d = {f: getattr(r, f) for f, _ in SpServerResult._fields_}
+        out.append((d, act[r.active_offset:r.active_offset + r.n_active].copy()))
+    return out
+
+
+def sp_server_get_permanences(s, sid, shape):
+    out = np.empty(shape, np.float32)
+    _check(lib().sp_server_get_permanences(s, sid, out.ctypes.data_as(_f32p)),
+           "sp_server_get_permanences")
+    return out
+
+
+def sp_server_get_stats(s, reset=False):
+    st = SpServerStats()
+    _check(lib().sp_server_get_stats(s, ct.byref(st), 1 if reset else 0), "sp_server_get_stats")
+    return {f: getattr(st, f) for f, _ in SpServerStats._fields_}
 
 
 def sp_kernel_launch_count():

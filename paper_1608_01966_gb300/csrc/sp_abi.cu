@@ -41,138 +41,9 @@ void sp::set_last_error(const char* fmt, ...) {
   t_last_error = buf;
 }
 
-namespace {
+#include "sp_internal.h"
 
-sp_status fail(sp_status s, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  t_last_error = buf;
-  return s;
-}
-
-#define SP_CUDA(call)                                                                      \
-  do {                                                                                     \
-    cudaError_t e_ = (call);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return fail(e_ == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA, "%s: %s (%s:%d)", \
-                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
-  } while (0)
-
-uint32_t default_timeout_ms() {
-  const char* s = std::getenv("SP_TIMEOUT_MS");
-  if (s && *s) {
-    long v = std::strtol(s, nullptr, 10);
-    if (v > 0) return (uint32_t)v;
-  }
-  return 10000u;
-}
-
-// Make `dev` current for the scope and restore the caller's device after.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
-
-bool all_ones(const float* v, size_t n);
-
-constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
-constexpr int kSlots = 2;
-constexpr uint32_t kGraphMinFrames = 4;  // shorter sequences are launched directly
-constexpr uint32_t kSeqMinFrames = 8;    // shorter sequences use the per-frame kernel
-constexpr size_t kSeqSmemLimit = 226u * 1024u;  // 227 KiB per CTA, less static shared memory
-
-bool seq_enabled() {
-  const char* s = std::getenv("SP_DISABLE_CLUSTER");
-  return !(s && s[0] == '1');
-}
-constexpr size_t kGraphCacheSize = 8;
-
-// A recorded frame sequence is valid for exactly the buffers, sizes and
-// starting (buffer parity, pending learning) state it was recorded with.
-struct GraphKey {
-  const uint32_t* x;
-  uint64_t n, stride;
-  int learn;
-  uint32_t* masks;
-  int cur;
-  bool pending;
-  bool unit_boost;  // selects the histogram path baked into the recorded launches
-  uint64_t mstride; // mask stride (batches)
-  bool operator==(const GraphKey& o) const {
-    return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
-           cur == o.cur && pending == o.pending && unit_boost == o.unit_boost &&
-           mstride == o.mstride;
-  }
-};
-
-struct GraphEntry {
-  GraphKey key;
-  cudaGraphExec_t exec;
-  uint64_t last_use;
-};
-
-bool graphs_enabled() {
-  const char* s = std::getenv("SP_DISABLE_GRAPHS");
-  return !(s && s[0] == '1');
-}
-
-}  // namespace
-
-struct sp_handle {
-  sp_config cfg{};
-  int device = 0;
-  uint32_t C = 0, S = 0, n_words = 0, mask_words = 0, max_active = 0;
-  uint64_t n_in = 0;
-  void* d_block = nullptr;
-  size_t device_bytes = 0;
-  uint32_t* d_idx = nullptr;
-  float* d_perm = nullptr;
-  float* d_boost = nullptr;
-  float* d_ov = nullptr;
-  uint32_t* d_xsave[2] = {nullptr, nullptr};
-  uint32_t* d_mask[2] = {nullptr, nullptr};
-  uint32_t* d_result = nullptr;
-  uint32_t* d_counter = nullptr;
-  uint32_t* d_hist = nullptr;  // [S + 1], used when every boost is 1
-  bool unit_boost = true;
-  uint32_t* h_result = nullptr;  // pinned [1 + C]
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;  // stream of the last call
-  cudaEvent_t ev_switch = nullptr;
-  cudaEvent_t ev_wait = nullptr;
-  int cur = 0;
-  bool pending = false;  // the previous frame's learning is not applied yet
-  uint64_t frames = 0;
-  uint32_t timeout_ms = 10000;
-  int grid = 1;
-  // sp_compute_frames staging (allocated on first use)
-  uint32_t* d_stage = nullptr;   // [kSlots][kChunkFrames][n_words]
-  uint32_t* d_mstage = nullptr;  // [kSlots][kChunkFrames][mask_words]
-  cudaStream_t s_in = nullptr, s_out = nullptr;
-  cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
-  // recorded frame sequences (CUDA graphs), replayed instead of n launches
-  std::vector<GraphEntry> graphs;
-  cudaStream_t cap_stream = nullptr;  // private stream used only for recording
-  uint64_t graph_clock = 0;
-  sp_batch* batch = nullptr;  // set while the handle is a member of a batch
-  // persistent cluster path for frame sequences (state in shared memory)
-  bool seq_ok = false;
-  uint32_t seq_Q = 0, seq_Cq = 0, seq_band_max = 0;
-  size_t seq_smem = 0;
-};
+using namespace sp::rt;
 
 namespace {
 
@@ -194,6 +65,8 @@ sp_status validate_config(const sp_config* c) {
       !std::isfinite(c->perm_dec))
     return fail(SP_EINVAL, "perm_inc / perm_dec must be finite and >= 0");
   if (c->inhibition > SP_INHIBIT_LOCAL) return fail(SP_EINVAL, "inhibition %u", c->inhibition);
+  if (!(c->duty_period >= 0.0f) || std::isinf(c->duty_period) || c->reserved != 0u)
+    return fail(SP_EINVAL, "duty_period must be finite and >= 0, reserved 0");
   const bool grid = c->col_grid_w != 0 || c->col_grid_h != 0;
   if (grid && (uint64_t)c->col_grid_w * c->col_grid_h != c->num_columns)
     return fail(SP_EINVAL, "col_grid %ux%u != num_columns %u", c->col_grid_w, c->col_grid_h,
@@ -314,12 +187,13 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   SP_CUDA(cudaGetDevice(&h->device));
   SP_CUDA(sp::kernels_init());
   const size_t CS = (size_t)h->C * h->S;
-  size_t off[9];
+  size_t off[10];
   size_t total = 0;
-  const size_t sizes[9] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
-                           (size_t)h->n_words * 4 * 2, (size_t)h->mask_words * 4 * 2,
-                           ((size_t)h->C + 1) * 4, 4, ((size_t)h->S + 1) * 4};
-  for (int i = 0; i < 9; ++i) {
+  const size_t sizes[10] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
+                            (size_t)h->n_words * 4 * 2, (size_t)h->mask_words * 4 * 2,
+                            ((size_t)h->C + 1) * 4, 4, ((size_t)h->S + 1) * 4,
+                            (size_t)h->C * 4};
+  for (int i = 0; i < 10; ++i) {
     off[i] = total;
     total += align256(sizes[i]);
   }
@@ -337,6 +211,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   h->d_result = reinterpret_cast<uint32_t*>(b + off[6]);
   h->d_counter = reinterpret_cast<uint32_t*>(b + off[7]);
   h->d_hist = reinterpret_cast<uint32_t*>(b + off[8]);
+  h->d_duty = reinterpret_cast<float*>(b + off[9]);
   SP_CUDA(cudaMallocHost(&h->h_result, ((size_t)h->C + 1) * 4));
   SP_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   h->stream = h->own_stream;
@@ -414,6 +289,8 @@ sp::StepArgs base_args(const sp_handle* h) {
   a.result = h->d_result;
   a.counter = h->d_counter;
   a.hist = (h->unit_boost && h->cfg.inhibition == SP_INHIBIT_GLOBAL) ? h->d_hist : nullptr;
+  a.duty = h->cfg.duty_period > 0.0f ? h->d_duty : nullptr;
+  a.duty_period = h->cfg.duty_period;
   a.C = h->C;
   a.S = h->S;
   a.n_words = h->n_words;
@@ -525,6 +402,8 @@ sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_
     a.gh = h->cfg.col_grid_h;
     a.radius = h->cfg.local_radius;
     a.unit_boost = h->unit_boost ? 1u : 0u;
+    a.duty = h->cfg.duty_period > 0.0f ? h->d_duty : nullptr;
+    a.duty_period = h->cfg.duty_period;
     SP_CUDA(sp::launch_seq(a, h->seq_Q, h->seq_smem, h->stream));
     h->pending = false;  // learning of every frame is already applied
     h->cur ^= 1;
@@ -578,11 +457,6 @@ sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_
   return SP_OK;
 }
 
-bool all_ones(const float* v, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (v[i] != 1.0f) return false;
-  return true;
-}
 
 bool finite_nonneg(const float* v, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -591,6 +465,53 @@ bool finite_nonneg(const float* v, size_t n) {
 }
 
 }  // namespace
+
+namespace sp {
+namespace rt {
+
+bool all_ones(const float* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (v[i] != 1.0f) return false;
+  return true;
+}
+
+sp_status handle_wait(sp_handle* h) { return wait_handle(h); }
+sp_status handle_flush_learning(sp_handle* h) { return flush_learning(h); }
+
+// The descriptor of one SP inside a multi-SP launch.
+void fill_desc(const sp_handle* h, sp::BatchDesc* d) {
+  *d = sp::BatchDesc{};
+  d->idx = h->d_idx;
+  d->perm = h->d_perm;
+  d->boost = h->d_boost;
+  d->ov = h->d_ov;
+  d->xsave0 = h->d_xsave[0];
+  d->xsave1 = h->d_xsave[1];
+  d->mask0 = h->d_mask[0];
+  d->mask1 = h->d_mask[1];
+  d->result = h->d_result;
+  d->counter = h->d_counter;
+  d->hist = (h->unit_boost && h->cfg.inhibition == SP_INHIBIT_GLOBAL) ? h->d_hist : nullptr;
+  d->duty = h->cfg.duty_period > 0.0f ? h->d_duty : nullptr;
+  d->duty_period = h->cfg.duty_period;
+  d->C = h->C;
+  d->S = h->S;
+  d->n_words = h->n_words;
+  d->mask_words = h->mask_words;
+  d->thr = h->cfg.connect_threshold;
+  d->inc = h->cfg.perm_inc;
+  d->dec = h->cfg.perm_dec;
+  d->min_overlap = h->cfg.min_overlap;
+  d->k = h->cfg.winners_set_size;
+  d->inhibition = h->cfg.inhibition;
+  d->gw = h->cfg.col_grid_w;
+  d->gh = h->cfg.col_grid_h;
+  d->radius = h->cfg.local_radius;
+  d->n_ctas = batch_ctas(h->C, h->S);
+}
+
+}  // namespace rt
+}  // namespace sp
 
 extern "C" {
 
@@ -843,6 +764,15 @@ SP_API sp_status sp_get_boost(sp_handle* h, float* out) {
   return wait_handle(h);
 }
 
+SP_API sp_status sp_get_duty_cycles(sp_handle* h, float* out) {
+  if (!h || !out) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
+  if (!(h->cfg.duty_period > 0.0f)) return fail(SP_EINVAL, "duty cycles are not tracked (duty_period 0)");
+  DeviceGuard g(h->device);
+  SP_CUDA(cudaMemcpyAsync(out, h->d_duty, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
+  return wait_handle(h);
+}
+
 SP_API sp_status sp_set_boost(sp_handle* h, const float* boost) {
   if (!h || !boost) return fail(SP_EINVAL, "NULL argument");
   if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
@@ -914,7 +844,8 @@ struct sp_batch {
   cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
 };
 
-namespace {
+namespace sp {
+namespace rt {
 
 // CTAs given to one SP in a batch launch: every warp takes several columns
 // so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
@@ -928,6 +859,11 @@ uint32_t batch_ctas(uint32_t C, uint32_t S) {
   const uint32_t per_cta = (uint32_t)sp::kStepWarps * cpw;
   return (C + per_cta - 1u) / per_cta;
 }
+
+}  // namespace rt
+}  // namespace sp
+
+namespace {
 
 sp_status batch_wait(sp_batch* b) {
   SP_CUDA(cudaEventRecord(b->ev_wait, b->stream));
@@ -1097,34 +1033,10 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   for (uint32_t i = 0; i < n; ++i) {
     sp_handle* h = members[i];
     sp::BatchDesc& d = desc[i];
-    d.idx = h->d_idx;
-    d.perm = h->d_perm;
-    d.boost = h->d_boost;
-    d.ov = h->d_ov;
-    d.xsave0 = h->d_xsave[0];
-    d.xsave1 = h->d_xsave[1];
-    d.mask0 = h->d_mask[0];
-    d.mask1 = h->d_mask[1];
-    d.result = h->d_result;
-    d.counter = h->d_counter;
-    d.hist = (h->unit_boost && h->cfg.inhibition == SP_INHIBIT_GLOBAL) ? h->d_hist : nullptr;
+    fill_desc(h, &d);
     d.frame_off = foff;
     d.mask_off = moff;
-    d.C = h->C;
-    d.S = h->S;
-    d.n_words = h->n_words;
-    d.mask_words = h->mask_words;
-    d.thr = h->cfg.connect_threshold;
-    d.inc = h->cfg.perm_inc;
-    d.dec = h->cfg.perm_dec;
-    d.min_overlap = h->cfg.min_overlap;
-    d.k = h->cfg.winners_set_size;
-    d.inhibition = h->cfg.inhibition;
-    d.gw = h->cfg.col_grid_w;
-    d.gh = h->cfg.col_grid_h;
-    d.radius = h->cfg.local_radius;
     d.cta_first = (uint32_t)cta_inst.size();
-    d.n_ctas = batch_ctas(h->C, h->S);
     for (uint32_t c = 0; c < d.n_ctas; ++c) cta_inst.push_back(i);
     b->frame_off.push_back(foff);
     b->mask_off.push_back(moff);

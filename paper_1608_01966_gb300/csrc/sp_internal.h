@@ -1,0 +1,157 @@
+// Internal definitions shared by the host runtime files (not part of the ABI):
+// the handle's layout, error helpers, device guard and graph-cache keys.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "../../include/sp.h"
+#include "sp_kernels.cuh"
+
+struct sp_handle;
+struct sp_batch;
+
+namespace sp {
+namespace rt {
+
+inline sp_status fail(sp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  sp::set_last_error("%s", buf);
+  return s;
+}
+
+#define SP_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+inline uint32_t default_timeout_ms() {
+  const char* s = std::getenv("SP_TIMEOUT_MS");
+  if (s && *s) {
+    long v = std::strtol(s, nullptr, 10);
+    if (v > 0) return (uint32_t)v;
+  }
+  return 10000u;
+}
+
+// Make `dev` current for the scope and restore the caller's device after.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
+
+bool all_ones(const float* v, size_t n);
+sp_status handle_wait(sp_handle* h);
+sp_status handle_flush_learning(sp_handle* h);
+uint32_t batch_ctas(uint32_t C, uint32_t S);
+void fill_desc(const sp_handle* h, sp::BatchDesc* d);
+
+constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
+constexpr int kSlots = 2;
+constexpr uint32_t kGraphMinFrames = 4;  // shorter sequences are launched directly
+constexpr uint32_t kSeqMinFrames = 8;    // shorter sequences use the per-frame kernel
+constexpr size_t kSeqSmemLimit = 226u * 1024u;  // 227 KiB per CTA, less static shared memory
+
+inline bool seq_enabled() {
+  const char* s = std::getenv("SP_DISABLE_CLUSTER");
+  return !(s && s[0] == '1');
+}
+constexpr size_t kGraphCacheSize = 8;
+
+// A recorded frame sequence is valid for exactly the buffers, sizes and
+// starting (buffer parity, pending learning) state it was recorded with.
+struct GraphKey {
+  const uint32_t* x;
+  uint64_t n, stride;
+  int learn;
+  uint32_t* masks;
+  int cur;
+  bool pending;
+  bool unit_boost;  // selects the histogram path baked into the recorded launches
+  uint64_t mstride; // mask stride (batches)
+  bool operator==(const GraphKey& o) const {
+    return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
+           cur == o.cur && pending == o.pending && unit_boost == o.unit_boost &&
+           mstride == o.mstride;
+  }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  uint64_t last_use;
+};
+
+inline bool graphs_enabled() {
+  const char* s = std::getenv("SP_DISABLE_GRAPHS");
+  return !(s && s[0] == '1');
+}
+
+}  // namespace rt
+}  // namespace sp
+
+struct sp_handle {
+  sp_config cfg{};
+  int device = 0;
+  uint32_t C = 0, S = 0, n_words = 0, mask_words = 0, max_active = 0;
+  uint64_t n_in = 0;
+  void* d_block = nullptr;
+  size_t device_bytes = 0;
+  uint32_t* d_idx = nullptr;
+  float* d_perm = nullptr;
+  float* d_boost = nullptr;
+  float* d_ov = nullptr;
+  uint32_t* d_xsave[2] = {nullptr, nullptr};
+  uint32_t* d_mask[2] = {nullptr, nullptr};
+  uint32_t* d_result = nullptr;
+  uint32_t* d_counter = nullptr;
+  uint32_t* d_hist = nullptr;  // [S + 1], used when every boost is 1
+  float* d_duty = nullptr;     // [C] active-duty cycles (tracked when duty_period > 0)
+  bool unit_boost = true;
+  uint32_t* h_result = nullptr;  // pinned [1 + C]
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;  // stream of the last call
+  cudaEvent_t ev_switch = nullptr;
+  cudaEvent_t ev_wait = nullptr;
+  int cur = 0;
+  bool pending = false;  // the previous frame's learning is not applied yet
+  uint64_t frames = 0;
+  uint32_t timeout_ms = 10000;
+  int grid = 1;
+  // sp_compute_frames staging (allocated on first use)
+  uint32_t* d_stage = nullptr;   // [sp::rt::kSlots][kChunkFrames][n_words]
+  uint32_t* d_mstage = nullptr;  // [sp::rt::kSlots][kChunkFrames][mask_words]
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_h2d[sp::rt::kSlots] = {}, ev_comp[sp::rt::kSlots] = {}, ev_d2h[sp::rt::kSlots] = {};
+  // recorded frame sequences (CUDA graphs), replayed instead of n launches
+  std::vector<sp::rt::GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for recording
+  uint64_t graph_clock = 0;
+  sp_batch* batch = nullptr;  // set while the handle is a member of a batch
+  // persistent cluster path for frame sequences (state in shared memory)
+  bool seq_ok = false;
+  uint32_t seq_Q = 0, seq_Cq = 0, seq_band_max = 0;
+  size_t seq_smem = 0;
+};

@@ -32,6 +32,9 @@ struct StepArgs {
   uint32_t* hist;            // [S + 1] counts of surviving raw overlaps, 0 between
                              // launches; used (global inhibition) when every boost
                              // is exactly 1, else nullptr (radix select instead)
+  uint32_t* result_copy;     // optional second copy of result[0..n] (serving), or nullptr
+  float* duty;               // [C] active-duty cycles updated each frame, or nullptr
+  float duty_period;
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k;
@@ -49,6 +52,8 @@ struct BatchDesc {
   uint32_t* result;
   uint32_t* counter;
   uint32_t* hist;       // nullptr unless global inhibition with unit boosts
+  float* duty;          // nullptr unless duty cycles are tracked
+  float duty_period;
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
   uint32_t C, S, n_words, mask_words;
@@ -56,6 +61,17 @@ struct BatchDesc {
   uint32_t min_overlap, k, inhibition, gw, gh, radius;
   uint32_t cta_first, n_ctas;  // this SP's CTAs in the batch grid
 };
+
+// Per-launch entry of one SP when a launch steps a chosen subset of SPs,
+// each with its own state (serving: streams advance independently).
+struct TickMember {
+  const uint32_t* x;   // this SP's frame (device)
+  uint32_t flags;      // bit 0 parity, bit 1 learning pending, bit 2 learn, bit 3 save frame
+  uint32_t cta_first;  // this SP's first CTA in this launch
+  uint32_t out_off;    // words: its [count, list...] in results_out
+  uint32_t pad;
+};
+enum : uint32_t { kTickCur = 1u, kTickPending = 2u, kTickLearn = 4u, kTickSave = 8u };
 
 // One frame for every SP of a batch.  All members share the buffer parity
 // `cur` and the pending-learning flag (they advance in lockstep).
@@ -67,6 +83,9 @@ struct BatchArgs {
   uint32_t* masks_out;          // one batch mask record, or nullptr
   uint32_t cur, pending, learn;
   uint32_t save;                // copy each member's frame for next-call learning
+  const TickMember* tick;       // if set: per-SP frame/state (indexed like desc); the
+                                // uniform fields above are then ignored
+  uint32_t* results_out;        // with tick: per-SP [count, ascending list]
 };
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
@@ -108,6 +127,8 @@ struct SeqArgs {
   float thr, inc, dec;
   uint32_t min_overlap, k, inhibition, gw, gh, radius;
   uint32_t unit_boost;
+  float* duty;                // [C] active-duty cycles, or nullptr
+  float duty_period;
 };
 
 size_t seq_smem_bytes(uint32_t C, uint32_t S, uint32_t Cq, uint32_t band_max);

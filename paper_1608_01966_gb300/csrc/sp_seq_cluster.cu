@@ -366,6 +366,15 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
       if (q == 0u && t == 0u) a.result[0] = total;
     }
 
+    if (a.duty) {
+      for (uint32_t lc = t; lc < nc; lc += kSeqThreads) {
+        const uint32_t c = c0 + lc;
+        const float act = ((s_mask[c >> 5] >> (c & 31u)) & 1u) ? 1.0f : 0.0f;
+        const float d = a.duty[c];
+        a.duty[c] = __fadd_rn(d, __fdiv_rn(__fsub_rn(act, d), a.duty_period));
+      }
+    }
+
     // ---- learning of this CTA's winners (frame band still resident) ---------
     if (a.learn) {
       for (uint32_t lc = warp; lc < nc; lc += kSeqWarps) {

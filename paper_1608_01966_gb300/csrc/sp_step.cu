@@ -154,6 +154,19 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
     a.mask_out[i] = m;
     if (a.mask_copy) a.mask_copy[i] = m;
   }
+  if (a.duty) {
+    // duty cycle d <- d + (a - d) / period, each step one fp32 RN op
+    for (uint32_t i = t; i < C; i += kStepThreads) {
+      const float act = ((smask[i >> 5] >> (i & 31u)) & 1u) ? 1.0f : 0.0f;
+      const float d = a.duty[i];
+      a.duty[i] = __fadd_rn(d, __fdiv_rn(__fsub_rn(act, d), a.duty_period));
+    }
+  }
+  if (a.result_copy) {
+    __syncthreads();  // the list written above is visible to the whole CTA
+    for (uint32_t i = t; i <= total; i += kStepThreads)
+      a.result_copy[i] = i == 0u ? total : __ldcg(a.result + i);
+  }
 }
 
 // One frame of one SP, run by nb CTAs of which this is number bid.
@@ -212,17 +225,37 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.perm = d.perm;
   a.boost = d.boost;
   a.ov = d.ov;
-  a.x = ba.frames + d.frame_off;
-  const uint32_t cur = ba.cur;
-  a.x_prev = !ba.pending ? nullptr
-             : (ba.prev_frames ? ba.prev_frames + d.frame_off : (cur ? d.xsave0 : d.xsave1));
-  a.mask_prev = ba.pending ? (cur ? d.mask0 : d.mask1) : nullptr;
-  a.x_save = (ba.learn && ba.save) ? (cur ? d.xsave1 : d.xsave0) : nullptr;
+  uint32_t cur, pending, learn, save, cta_first;
+  a.result_copy = nullptr;
+  if (ba.tick) {
+    const TickMember& tm = ba.tick[inst];
+    a.x = tm.x;
+    cur = tm.flags & kTickCur;
+    pending = tm.flags & kTickPending;
+    learn = tm.flags & kTickLearn;
+    save = tm.flags & kTickSave;
+    cta_first = tm.cta_first;
+    a.x_prev = pending ? (cur ? d.xsave0 : d.xsave1) : nullptr;
+    a.result_copy = ba.results_out ? ba.results_out + tm.out_off : nullptr;
+  } else {
+    a.x = ba.frames + d.frame_off;
+    cur = ba.cur;
+    pending = ba.pending;
+    learn = ba.learn;
+    save = ba.save;
+    cta_first = d.cta_first;
+    a.x_prev = !pending ? nullptr
+               : (ba.prev_frames ? ba.prev_frames + d.frame_off : (cur ? d.xsave0 : d.xsave1));
+  }
+  a.mask_prev = pending ? (cur ? d.mask0 : d.mask1) : nullptr;
+  a.x_save = (learn && save) ? (cur ? d.xsave1 : d.xsave0) : nullptr;
   a.mask_out = cur ? d.mask1 : d.mask0;
-  a.mask_copy = ba.masks_out ? ba.masks_out + d.mask_off : nullptr;
+  a.mask_copy = (ba.masks_out && !ba.tick) ? ba.masks_out + d.mask_off : nullptr;
   a.result = d.result;
   a.counter = d.counter;
   a.hist = d.hist;
+  a.duty = d.duty;
+  a.duty_period = d.duty_period;
   a.C = d.C;
   a.S = d.S;
   a.n_words = d.n_words;
@@ -236,7 +269,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.gw = d.gw;
   a.gh = d.gh;
   a.radius = d.radius;
-  const uint32_t bid = blockIdx.x - d.cta_first;
+  const uint32_t bid = blockIdx.x - cta_first;
   if ((a.S & 3u) == 0u)
     step_body<4, true>(a, bid, d.n_ctas, dyn_smem);
   else

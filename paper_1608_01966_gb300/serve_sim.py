@@ -1,0 +1,193 @@
+"""Simulated video-stream serving on the library's server (sp_server_*).
+
+S streams (default 32) with Poisson frame arrivals (default mean 30 fps
+each) at round-robin resolutions 320x180, 640x360 and 960x540 (blobbed binary
+frames, cycled from a seeded pool per resolution).  Each stream owns an SP of
+1024 columns x 256 synapses from a 64x64 window, learning on, duty cycles
+tracked.  An open-loop run submits frames at their arrival times and reports
+frames/s and per-frame latency (submit -> result on the host) p50/p99; a
+closed-loop run keeps every stream's queue full to find the saturation
+throughput.
+
+    python -m paper_1608_01966_gb300.serve_sim --seconds 60
+"""
+import argparse
+import heapq
+import json
+import threading
+import time
+
+import numpy as np
+
+from . import _binding as spg
+from . import synth, workloads as wl
+
+RESOLUTIONS = [(320, 180), (640, 360), (960, 540)]
+
+
+def _frame_pools(n_per_res, seed):
+    pools = {}
+    for r, (W, H) in enumerate(RESOLUTIONS):
+        fr = [synth.frame_blobbed(synth.derive_seed(seed, synth.PURPOSE_FRAME, 1000 * r + t), W, H)
+              for t in range(n_per_res)]
+        pools[(W, H)] = wl.pack(np.stack(fr))
+    return pools
+
+
+def open_streams(srv, n, seed, duty_period=1000.0):
+    sids, res = [], []
+    for i in range(n):
+        W, H = RESOLUTIONS[i % 3]
+        cfg = spg.sp_config_init(input_w=W, input_h=H, num_columns=1024, col_grid_w=32,
+                                 col_grid_h=32, synapses_per_column=256,
+                                 pool_mode=spg.SP_POOL_WINDOW, rf_w=64, rf_h=64,
+                                 perm_init_lo=0.1, perm_init_hi=0.3, connect_threshold=0.2,
+                                 perm_inc=0.05, perm_dec=0.02, min_overlap=4,
+                                 winners_set_size=40, duty_period=duty_period,
+                                 seed=synth.derive_seed(seed, synth.PURPOSE_INSTANCE, i))
+        sids.append(spg.sp_server_open_stream(srv, cfg))
+        res.append((W, H))
+    return sids, res
+
+
+class _Collector(threading.Thread):
+    def __init__(self, srv, expected):
+        super().__init__(daemon=True)
+        self.srv, self.expected = srv, expected
+        self.lat = []
+        self.errors = 0
+        self.t_last = None
+
+    def run(self):
+        while len(self.lat) + self.errors < self.expected:
+            for r, _ in spg.sp_server_poll(self.srv, max_results=512, wait_ms=20):
+                if r["status"] != 0:
+                    self.errors += 1
+                else:
+                    self.lat.append(r["latency_us"])
+                self.t_last = time.perf_counter()
+
+
+def _submit(srv, sid, frame, learn=True):
+    while True:
+        try:
+            return spg.sp_server_submit(srv, sid, frame, learn)
+        except spg.SpError as e:
+            if e.status != 5:  # anything but a full queue
+                raise
+            time.sleep(0.0002)
+
+
+def run_open_loop(srv, sids, res, pools, seconds, fps, seed):
+    """Poisson arrivals: every stream's inter-arrival times are exponential
+    with mean 1/fps; frames are submitted at their arrival times."""
+    rng = np.random.default_rng(seed)
+    events = []
+    for i in range(len(sids)):
+        t = rng.exponential(1.0 / fps)
+        while t < seconds:
+            events.append((t, i))
+            t += rng.exponential(1.0 / fps)
+    heapq.heapify(events)
+    col = _Collector(srv, len(events))
+    col.start()
+    spg.sp_server_get_stats(srv, reset=True)
+    t0 = time.perf_counter()
+    count = [0] * len(sids)
+    while events:
+        t, i = heapq.heappop(events)
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        pool = pools[res[i]]
+        _submit(srv, sids[i], pool[count[i] % pool.shape[0]])
+        count[i] += 1
+    col.join(timeout=seconds + 30)
+    elapsed = (col.t_last or time.perf_counter()) - t0
+    lat = np.array(col.lat)
+    return {"frames": int(lat.size), "errors": col.errors, "seconds": elapsed,
+            "frames_per_s": lat.size / elapsed if elapsed > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)) / 1000 if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) / 1000 if lat.size else None}
+
+
+def run_closed_loop(srv, sids, res, pools, seconds):
+    """Every stream resubmits as soon as its queue has room (saturation)."""
+    stop = threading.Event()
+    submitted = [0]
+    lock = threading.Lock()
+
+    def producer(members):
+        k = 0
+        while not stop.is_set():
+            for i in members:
+                pool = pools[res[i]]
+                try:
+                    spg.sp_server_submit(srv, sids[i], pool[k % pool.shape[0]], True)
+                    with lock:
+                        submitted[0] += 1
+                except spg.SpError as e:
+                    if e.status != 5:
+                        raise
+            k += 1
+            time.sleep(0)
+
+    lat = []
+    threads = [threading.Thread(target=producer, args=(list(range(j, len(sids), 4)),),
+                                daemon=True) for j in range(4)]
+    spg.sp_server_get_stats(srv, reset=True)
+    t0 = time.perf_counter()
+    for th in threads:
+        th.start()
+    while time.perf_counter() - t0 < seconds:
+        for r, _ in spg.sp_server_poll(srv, max_results=1024, wait_ms=10):
+            lat.append(r["latency_us"])
+    elapsed = time.perf_counter() - t0
+    stop.set()
+    for th in threads:
+        th.join()
+    while True:  # drain
+        got = spg.sp_server_poll(srv, max_results=1024, wait_ms=100)
+        if not got:
+            break
+    lat = np.array(lat)
+    return {"frames": int(lat.size), "seconds": elapsed, "frames_per_s": lat.size / elapsed,
+            "p50_ms": float(np.percentile(lat, 50)) / 1000 if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) / 1000 if lat.size else None}
+
+
+def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=5.0, seed=0x5EED0005,
+             budget_bytes=8 << 30):
+    pools = _frame_pools(16, seed)
+    words = max(p.shape[1] for p in pools.values())
+    srv = spg.sp_server_create(max_streams=streams, queue_depth=4, max_input_words=words,
+                               device_budget_bytes=budget_bytes, max_active=64)
+    try:
+        sids, res = open_streams(srv, streams, seed)
+        out = {"streams": streams, "fps_per_stream": fps,
+               "resolutions": "round-robin 320x180 / 640x360 / 960x540",
+               "open_loop": run_open_loop(srv, sids, res, pools, seconds, fps, seed)}
+        if saturate_seconds > 0:
+            out["closed_loop"] = run_closed_loop(srv, sids, res, pools, saturate_seconds)
+        st = spg.sp_server_get_stats(srv)
+        out["launches"] = st["launches"]
+        out["frames_per_launch"] = st["frames_in_launches"] / max(1, st["launches"])
+        for sid in sids:
+            spg.sp_server_close_stream(srv, sid)
+    finally:
+        spg.sp_server_destroy(srv)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--streams", type=int, default=32)
+    ap.add_argument("--fps", type=float, default=30.0)
+    ap.add_argument("--seconds", type=float, default=60.0)
+    ap.add_argument("--saturate-seconds", type=float, default=5.0)
+    a = ap.parse_args()
+    print(json.dumps(simulate(a.streams, a.fps, a.seconds, a.saturate_seconds)))
+
+
+if __name__ == "__main__":
+    main()
