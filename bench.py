@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=INSTANCES)
     ap.add_argument("--seq-frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core run")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="open-loop serving run (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -290,6 +291,62 @@ def run_single_sp(spg, torch, case, pool_packed, n_frames, steps, dev, stream):
     return n_frames / (ms / 1000.0), ms * 1000.0 / n_frames
 
 
+def read_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_dense_tc(spg, torch, dev, stream, members=16, frames=256, steps=5):
+    """16 SPs with dense pools (1024 inputs x 1024 columns, k = 20) inferring
+    256 frames each: one tensor-core launch for all overlaps (16 x 256 x 1024 x
+    1024 multiply-adds of {0,1} bf16 operands) plus one Alg. 2 launch."""
+    from paper_1608_01966_gb300 import synth, workloads as wl
+    n_in, C = 1024, 1024
+    cases, packed = [], []
+    for i in range(members):
+        sd = synth.derive_seed(wl.BASE_SEED + 4, synth.PURPOSE_INSTANCE, 1000 + i)
+        idx = synth.pool_dense(C, n_in)
+        perm = synth.perm_uniform(synth.derive_seed(sd, synth.PURPOSE_PERM, 0), (C, n_in), 0.1, 0.3)
+        cases.append(wl.Case("dense", n_in, 1, C, n_in, idx, perm, np.ones(C, np.float32), k=20))
+        p = 0.02 + 0.18 * i / max(1, members - 1)
+        fr = np.stack([synth.frame_bernoulli(synth.derive_seed(sd, synth.PURPOSE_FRAME, t), n_in, p)
+                       for t in range(frames)])
+        packed.append(wl.pack(fr))
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, _ = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    d = torch.from_numpy(wl.batch_frames(packed, fo, fw).view(np.int32)).to(dev)
+    mw = info["mask_words"]
+    dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        spg.sp_batch_infer_device(b, d, frames, fw, dm, mw, stream)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(steps):
+        spg.sp_batch_infer_device(b, d, frames, fw, dm, mw, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / steps
+    spg.sp_batch_destroy(b)
+    for h in hs:
+        spg.sp_destroy(h)
+    flops = 2.0 * members * frames * C * n_in
+    peak, kind = read_bf16_peak()
+    tf = flops / (ms / 1000.0) / 1e12
+    return {"workload": f"{members} dense SPs (1024 inputs x 1024 columns) x {frames} frames, "
+                        "inference, tensor cores (tcgen05 kind::f16, bf16 {0,1}, fp32 accumulate)",
+            "ms_per_run": ms, "frames_per_s": members * frames / (ms / 1000.0),
+            "tensor": {"achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                       "peak_kind": kind}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -387,6 +444,10 @@ def main():
                               "between steps",
                   "frames_per_s": fps1, "us_per_frame": us1}
 
+    dense_tc = None
+    if not args.no_dense:
+        dense_tc = run_dense_tc(spg, torch, dev, stream)
+
     serve = None
     if args.serve_seconds > 0 and rank == 0:
         from paper_1608_01966_gb300 import serve_sim
@@ -429,6 +490,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "single_sp": single,
+            "dense_tc": dense_tc,
             "serve": serve,
             "cpu_baseline": cpu,
         }

@@ -122,6 +122,7 @@ def lib():
         L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
                                        ct.c_uint64]
         L.sp_batch_sync.argtypes = [vp]
+        L.sp_batch_infer_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_server_create.argtypes = [ct.POINTER(SpServerConfig), ct.POINTER(vp)]
         L.sp_server_destroy.argtypes = [vp]
         L.sp_server_destroy.restype = None
@@ -343,6 +344,13 @@ def sp_batch_compute(b, frames, learn, masks_out=None):
     _check(lib().sp_batch_compute(b, frames.ctypes.data_as(_u32p), frames.shape[0],
                                   frames.shape[1], 1 if learn else 0, pm, ms), "sp_batch_compute")
     return masks_out
+
+
+def sp_batch_infer_device(b, d_frames, n_frames, stride_words, d_masks=None,
+                          mask_stride_words=0, stream=None):
+    _check(lib().sp_batch_infer_device(b, _addr(d_frames), n_frames, stride_words,
+                                       _addr(d_masks), mask_stride_words, _stream(stream)),
+           "sp_batch_infer_device")
 
 
 def sp_batch_sync(b):

@@ -92,8 +92,8 @@ def build_sp(force=False, jobs=None):
             list(ex.map(_run, jobs_list))
     if force or jobs_list or _newer(SP_LIB, objs):
         tmp = SP_LIB + f".tmp{os.getpid()}"
-        _run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt",
-                                                               "-lpthread", "-ldl"])
+        _run([NVCC] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
+             + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"])
         os.replace(tmp, SP_LIB)
     return SP_LIB
 

@@ -117,6 +117,9 @@ void free_handle(sp_handle* h) {
   if (h->s_out) cudaStreamDestroy(h->s_out);
   if (h->d_stage) cudaFree(h->d_stage);
   if (h->d_mstage) cudaFree(h->d_mstage);
+  if (h->d_run_ov) cudaFree(h->d_run_ov);
+  if (h->d_run_masks) cudaFree(h->d_run_masks);
+  if (h->d_conn) cudaFree(h->d_conn);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -124,6 +127,7 @@ void free_handle(sp_handle* h) {
   if (h->ev_wait) cudaEventDestroy(h->ev_wait);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->h_err) cudaFreeHost(h->h_err);
   if (h->d_block) cudaFree(h->d_block);
   delete h;
 }
@@ -186,14 +190,16 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   h->timeout_ms = default_timeout_ms();
   SP_CUDA(cudaGetDevice(&h->device));
   SP_CUDA(sp::kernels_init());
+  SP_CUDA(sp::dense_init());
+  SP_CUDA(sp::frame_inhibit_init());
   const size_t CS = (size_t)h->C * h->S;
-  size_t off[10];
+  size_t off[11];
   size_t total = 0;
-  const size_t sizes[10] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
+  const size_t sizes[11] = {CS * 4, CS * 4, (size_t)h->C * 4, (size_t)h->C * 4,
                             (size_t)h->n_words * 4 * 2, (size_t)h->mask_words * 4 * 2,
                             ((size_t)h->C + 1) * 4, 4, ((size_t)h->S + 1) * 4,
-                            (size_t)h->C * 4};
-  for (int i = 0; i < 10; ++i) {
+                            (size_t)h->C * 4, 4};
+  for (int i = 0; i < 11; ++i) {
     off[i] = total;
     total += align256(sizes[i]);
   }
@@ -212,7 +218,10 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   h->d_counter = reinterpret_cast<uint32_t*>(b + off[7]);
   h->d_hist = reinterpret_cast<uint32_t*>(b + off[8]);
   h->d_duty = reinterpret_cast<float*>(b + off[9]);
+  h->d_err = reinterpret_cast<uint32_t*>(b + off[10]);
   SP_CUDA(cudaMallocHost(&h->h_result, ((size_t)h->C + 1) * 4));
+  SP_CUDA(cudaMallocHost(&h->h_err, 4));
+  *h->h_err = 0u;
   SP_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   h->stream = h->own_stream;
   SP_CUDA(cudaEventCreateWithFlags(&h->ev_switch, cudaEventDisableTiming));
@@ -226,6 +235,8 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
     boost = ones.data();
   }
   h->unit_boost = all_ones(boost, h->C);
+  h->dense = h->S == h->n_in;
+  for (size_t e = 0; h->dense && e < CS; ++e) h->dense = idx[e] == (uint32_t)(e % h->S);
   SP_CUDA(cudaMemcpyAsync(h->d_boost, boost, (size_t)h->C * 4, cudaMemcpyHostToDevice, h->stream));
   SP_CUDA(cudaStreamSynchronize(h->stream));
   h->grid = sp::step_grid(h->C);
@@ -235,12 +246,20 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
 
 // Bounded wait for everything enqueued so far on the handle's stream.
 sp_status wait_handle(sp_handle* h) {
+  if (h->dense_used) {
+    // a tensor-core run reports an expired bounded wait through d_err
+    SP_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
+  }
   SP_CUDA(cudaEventRecord(h->ev_wait, h->stream));
   const auto deadline =
       std::chrono::steady_clock::now() + std::chrono::milliseconds(h->timeout_ms);
   for (uint32_t spin = 0;; ++spin) {
     const cudaError_t e = cudaEventQuery(h->ev_wait);
-    if (e == cudaSuccess) return SP_OK;
+    if (e == cudaSuccess) {
+      if (h->dense_used && *h->h_err != 0u)
+        return fail(SP_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+      return SP_OK;
+    }
     if (e != cudaErrorNotReady)
       return fail(SP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
     if (std::chrono::steady_clock::now() > deadline)
@@ -365,8 +384,85 @@ sp_status enqueue_sequence(sp_handle* h, cudaStream_t st, const uint32_t* x_base
 // Run a frame sequence on the handle's stream: replay its recorded graph if
 // this exact sequence was seen before, else record it on the private capture
 // stream first.  Short sequences, or SP_DISABLE_GRAPHS=1, launch directly.
+// Scratch of a dense inference run of n frames: overlaps, masks, connected bits.
+sp_status ensure_dense_buffers(sp_handle* h, uint32_t n) {
+  if (n > h->run_cap) {
+    if (h->d_run_ov) cudaFree(h->d_run_ov);
+    if (h->d_run_masks) cudaFree(h->d_run_masks);
+    h->d_run_ov = nullptr;
+    h->d_run_masks = nullptr;
+    h->run_cap = 0;
+    SP_CUDA(cudaMalloc(&h->d_run_ov, (size_t)n * h->C * 4));
+    SP_CUDA(cudaMalloc(&h->d_run_masks, (size_t)n * h->mask_words * 4));
+    h->run_cap = n;
+  }
+  if (!h->d_conn) {
+    h->conn_words = 2u * ((h->S + 63u) / 64u);
+    SP_CUDA(cudaMalloc(&h->d_conn, (size_t)h->C * h->conn_words * 4));
+  }
+  return SP_OK;
+}
+
+// Inference run of a dense-pool SP on the tensor cores: all overlaps of the
+// run as one matrix product, then Alg. 2 per frame, then duty cycles in
+// frame order.
+sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
+                    uint32_t* masks) {
+  sp_status s = flush_learning(h);
+  if (s != SP_OK) return s;
+  if ((s = ensure_dense_buffers(h, n)) != SP_OK) return s;
+  sp::DenseArgs d{};
+  d.perm = h->d_perm;
+  d.conn = h->d_conn;
+  d.conn_words = h->conn_words;
+  d.boost = h->d_boost;
+  d.frames = x_base;
+  d.stride = stride;
+  d.n_frames = n;
+  d.C = h->C;
+  d.K = h->S;
+  d.n_words = h->n_words;
+  d.thr = h->cfg.connect_threshold;
+  d.min_overlap = h->cfg.min_overlap;
+  d.ov = h->d_run_ov;
+  d.err = h->d_err;
+  SP_CUDA(sp::launch_conn_pack_one(d, h->stream));
+  SP_CUDA(sp::launch_dense_overlap(d, h->stream));
+  h->dense_used = true;
+  const bool duty = h->cfg.duty_period > 0.0f;
+  sp::FrameInhibitArgs f{};
+  f.ov = h->d_run_ov;
+  f.n_frames = n;
+  f.C = h->C;
+  f.mask_words = h->mask_words;
+  f.k = h->cfg.winners_set_size;
+  f.inhibition = h->cfg.inhibition;
+  f.gw = h->cfg.col_grid_w;
+  f.gh = h->cfg.col_grid_h;
+  f.radius = h->cfg.local_radius;
+  f.unit_S = h->unit_boost ? h->S : 0u;
+  if (sp::frame_inhibit_smem(h->C, f.unit_S) > sp::frame_inhibit_smem_limit()) f.unit_S = 0u;
+  if (sp::frame_inhibit_smem(h->C, 0u) > sp::frame_inhibit_smem_limit())
+    return fail(SP_ENOTSUP, "too many columns for the per-frame inhibition kernel");
+  f.masks_out = masks ? masks : (duty ? h->d_run_masks : nullptr);
+  f.masks_stride = h->mask_words;
+  f.mask_last = h->d_mask[h->cur];
+  f.result = h->d_result;
+  f.ov_last = h->d_ov;
+  SP_CUDA(sp::launch_frame_inhibit(f, h->stream));
+  if (duty)
+    SP_CUDA(sp::launch_duty_run(f.masks_out, n, h->mask_words, h->C, h->d_duty,
+                                h->cfg.duty_period, h->stream));
+  h->pending = false;
+  h->cur ^= 1;
+  h->frames += n;
+  return SP_OK;
+}
+
 sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
                        int learn, uint32_t* masks) {
+  if (!learn && h->dense && n >= kDenseMinFrames && dense_enabled())
+    return run_dense(h, x_base, n, stride, masks);
   if (h->seq_ok && n >= kSeqMinFrames && seq_enabled()) {
     sp::SeqArgs a{};
     a.idx = h->d_idx;
@@ -836,6 +932,8 @@ struct sp_batch {
   cudaEvent_t ev_switch = nullptr, ev_wait = nullptr;
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
+  // sp_batch_infer_device: per-member kernel arguments on the device
+  void* d_infer_args = nullptr;
   // sp_batch_compute staging
   uint32_t* d_stage = nullptr;
   uint32_t* d_mstage = nullptr;
@@ -904,6 +1002,7 @@ void free_batch(sp_batch* b) {
   if (b->ev_wait) cudaEventDestroy(b->ev_wait);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   if (b->d_block) cudaFree(b->d_block);
+  if (b->d_infer_args) cudaFree(b->d_infer_args);
   for (sp_handle* h : b->members) {
     if (h->batch != b) continue;
     h->cur = b->cur;  // the members' buffers follow the batch's parity
@@ -1170,6 +1269,108 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
     SP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_switch, 0));
   }
   return batch_wait(b);
+}
+
+SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                       uint64_t stride, uint32_t* d_masks, uint64_t mstride,
+                                       void* stream) {
+  if (!b || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
+  if (n_frames == 0) return SP_OK;
+  if (stride < b->frame_words) return fail(SP_EINVAL, "frame stride below frame_words");
+  if (d_masks && mstride < b->mask_words) return fail(SP_EINVAL, "mask stride below mask_words");
+  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_masks) % 4u)
+    return fail(SP_EINVAL, "device pointers must be 4-byte aligned");
+  for (sp_handle* h : b->members)
+    if (!h->dense) return fail(SP_ENOTSUP, "every member needs dense pools (S = n_in)");
+  DeviceGuard g(b->device);
+  sp_status st = batch_use_stream(b, static_cast<cudaStream_t>(stream));
+  if (st != SP_OK) return st;
+  const uint32_t n = (uint32_t)b->members.size();
+  // learning left pending by the last batch step is applied first
+  if (b->pending) {
+    for (sp_handle* h : b->members) {
+      sp::LearnArgs l{};
+      l.idx = h->d_idx;
+      l.perm = h->d_perm;
+      l.x = h->d_xsave[b->cur ^ 1];
+      l.mask = h->d_mask[b->cur ^ 1];
+      l.C = h->C;
+      l.S = h->S;
+      l.inc = h->cfg.perm_inc;
+      l.dec = h->cfg.perm_dec;
+      SP_CUDA(sp::launch_learn(l, b->stream));
+    }
+    b->pending = false;
+  }
+  std::vector<sp::DenseArgs> dargs(n);
+  std::vector<sp::FrameInhibitArgs> fargs(n);
+  uint32_t max_C = 0, max_S = 0, max_cw = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    sp_handle* h = b->members[i];
+    if ((st = ensure_dense_buffers(h, n_frames)) != SP_OK) return st;
+    sp::DenseArgs& d = dargs[i];
+    d.perm = h->d_perm;
+    d.conn = h->d_conn;
+    d.conn_words = h->conn_words;
+    max_cw = std::max(max_cw, h->conn_words);
+    d.boost = h->d_boost;
+    d.frames = d_frames + b->frame_off[i];
+    d.stride = stride;
+    d.n_frames = n_frames;
+    d.C = h->C;
+    d.K = h->S;
+    d.n_words = h->n_words;
+    d.thr = h->cfg.connect_threshold;
+    d.min_overlap = h->cfg.min_overlap;
+    d.ov = h->d_run_ov;
+    d.err = h->d_err;
+    h->dense_used = true;
+    sp::FrameInhibitArgs& f = fargs[i];
+    f.ov = h->d_run_ov;
+    f.n_frames = n_frames;
+    f.C = h->C;
+    f.mask_words = h->mask_words;
+    f.k = h->cfg.winners_set_size;
+    f.inhibition = h->cfg.inhibition;
+    f.gw = h->cfg.col_grid_w;
+    f.gh = h->cfg.col_grid_h;
+    f.radius = h->cfg.local_radius;
+    f.unit_S = h->unit_boost ? h->S : 0u;
+    if (sp::frame_inhibit_smem(h->C, f.unit_S) > sp::frame_inhibit_smem_limit()) f.unit_S = 0u;
+    const bool duty = h->cfg.duty_period > 0.0f;
+    f.masks_out = d_masks ? d_masks + b->mask_off[i] : (duty ? h->d_run_masks : nullptr);
+    f.masks_stride = d_masks ? mstride : h->mask_words;
+    f.mask_last = h->d_mask[b->cur];
+    f.result = h->d_result;
+    f.ov_last = h->d_ov;
+    max_C = std::max(max_C, h->C);
+    max_S = std::max(max_S, f.unit_S);
+  }
+  if (sp::frame_inhibit_smem(max_C, max_S) > sp::frame_inhibit_smem_limit())
+    return fail(SP_ENOTSUP, "members too large for one per-frame inhibition launch");
+  if (!b->d_infer_args)
+    SP_CUDA(cudaMalloc(&b->d_infer_args, (sizeof(sp::DenseArgs) + sizeof(sp::FrameInhibitArgs)) * n));
+  sp::DenseArgs* d_dargs = static_cast<sp::DenseArgs*>(b->d_infer_args);
+  sp::FrameInhibitArgs* d_fargs = reinterpret_cast<sp::FrameInhibitArgs*>(d_dargs + n);
+  // the argument arrays go through the stream so earlier launches keep theirs
+  SP_CUDA(cudaMemcpyAsync(d_dargs, dargs.data(), sizeof(sp::DenseArgs) * n,
+                          cudaMemcpyHostToDevice, b->stream));
+  SP_CUDA(cudaMemcpyAsync(d_fargs, fargs.data(), sizeof(sp::FrameInhibitArgs) * n,
+                          cudaMemcpyHostToDevice, b->stream));
+  SP_CUDA(sp::launch_conn_pack(d_dargs, n, max_C, max_cw, b->stream));
+  SP_CUDA(sp::launch_dense_overlap_many(d_dargs, n, max_C, n_frames, b->stream));
+  SP_CUDA(sp::launch_frame_inhibit_many(d_fargs, n, max_C, max_S, n_frames, b->stream));
+  for (uint32_t i = 0; i < n; ++i) {
+    sp_handle* h = b->members[i];
+    if (h->cfg.duty_period > 0.0f)
+      SP_CUDA(sp::launch_duty_run(fargs[i].masks_out, n_frames, (uint32_t)fargs[i].masks_stride,
+                                  h->C, h->d_duty, h->cfg.duty_period, b->stream));
+  }
+  // host copies of the argument arrays must outlive the asynchronous copies
+  SP_CUDA(cudaStreamSynchronize(b->stream));
+  b->cur ^= 1;
+  b->frames += n_frames;
+  return SP_OK;
 }
 
 SP_API sp_status sp_batch_sync(sp_batch* b) {

@@ -104,6 +104,13 @@ struct GraphEntry {
   uint64_t last_use;
 };
 
+constexpr uint32_t kDenseMinFrames = 16;  // shorter inference runs use the per-frame kernel
+
+inline bool dense_enabled() {
+  const char* s = std::getenv("SP_DISABLE_TENSOR_CORES");
+  return !(s && s[0] == '1');
+}
+
 inline bool graphs_enabled() {
   const char* s = std::getenv("SP_DISABLE_GRAPHS");
   return !(s && s[0] == '1');
@@ -129,6 +136,17 @@ struct sp_handle {
   uint32_t* d_counter = nullptr;
   uint32_t* d_hist = nullptr;  // [S + 1], used when every boost is 1
   float* d_duty = nullptr;     // [C] active-duty cycles (tracked when duty_period > 0)
+  uint32_t* d_err = nullptr;   // set by a kernel whose bounded wait expired
+  uint32_t* h_err = nullptr;   // pinned copy of d_err
+  // dense pools (every column sees the whole input): inference runs of frames
+  // go through the tensor cores
+  bool dense = false;
+  bool dense_used = false;
+  float* d_run_ov = nullptr;        // [run_cap][C] overlaps of a run
+  uint32_t* d_run_masks = nullptr;  // [run_cap][mask_words]
+  uint32_t run_cap = 0;
+  uint32_t* d_conn = nullptr;       // [C][conn_words] connected bits of a dense run
+  uint32_t conn_words = 0;
   bool unit_boost = true;
   uint32_t* h_result = nullptr;  // pinned [1 + C]
   cudaStream_t own_stream = nullptr;

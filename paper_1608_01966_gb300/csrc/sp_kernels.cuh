@@ -136,6 +136,56 @@ cudaError_t seq_kernel_init(size_t smem_bytes);
 cudaError_t seq_max_active_clusters(uint32_t Q, size_t smem_bytes, int* out);
 cudaError_t launch_seq(const SeqArgs& a, uint32_t Q, size_t smem_bytes, cudaStream_t stream);
 
+// Dense pools on the tensor cores (sp_dense_tc.cu): the raw overlaps of a run
+// of frames without learning as one {0,1} matrix product.
+struct DenseArgs {
+  const float* perm;        // [C][K]
+  const uint32_t* conn;     // [C][conn_words] connected bits (perm >= thr), LSB first
+  uint32_t conn_words;      // words per column row (even)
+  const float* boost;       // [C]
+  const uint32_t* frames;   // frame f at frames + f * stride
+  uint64_t stride;
+  uint32_t n_frames, C, K, n_words;
+  float thr;
+  uint32_t min_overlap;
+  float* ov;                // [n_frames][C] boosted overlaps (out)
+  uint32_t* err;            // set to 1 if a bounded wait expired
+};
+
+// Alg. 2 for every frame of a run whose overlaps are rows of ov.
+struct FrameInhibitArgs {
+  const float* ov;          // [n_frames][C]
+  uint32_t n_frames, C, mask_words, k, inhibition, gw, gh, radius;
+  uint32_t unit_S;          // S when every boost is 1 (histogram select), else 0
+  uint32_t* masks_out;      // frame f's mask at masks_out + f * masks_stride, or nullptr
+  uint64_t masks_stride;    // words between consecutive frames' masks
+  uint32_t* mask_last;      // the last frame's mask
+  uint32_t* result;         // the last frame's [count, list...]
+  float* ov_last;           // the last frame's overlaps [C]
+};
+
+size_t dense_smem_bytes();
+cudaError_t dense_init();
+cudaError_t launch_dense_overlap(const DenseArgs& a, cudaStream_t stream);
+// Pack the connected bits of every dense SP of a launch (conn written in place
+// of the args' conn pointers; one thread per 32 synapses).
+cudaError_t launch_conn_pack(const DenseArgs* args, uint32_t n, uint32_t max_C,
+                             uint32_t max_conn_words, cudaStream_t stream);
+cudaError_t launch_conn_pack_one(const DenseArgs& a, cudaStream_t stream);
+// Several SPs in one launch: args is a device array of n entries; every SP
+// covers at most max_C columns and max_frames frames.
+cudaError_t launch_dense_overlap_many(const DenseArgs* args, uint32_t n, uint32_t max_C,
+                                      uint32_t max_frames, cudaStream_t stream);
+cudaError_t frame_inhibit_init();
+size_t frame_inhibit_smem(uint32_t C, uint32_t unit_S);
+size_t frame_inhibit_smem_limit();
+cudaError_t launch_frame_inhibit(const FrameInhibitArgs& a, cudaStream_t stream);
+cudaError_t launch_frame_inhibit_many(const FrameInhibitArgs* args, uint32_t n, uint32_t max_C,
+                                      uint32_t max_unit_S, uint32_t max_frames,
+                                      cudaStream_t stream);
+cudaError_t launch_duty_run(const uint32_t* masks, uint32_t n_frames, uint32_t mask_words,
+                            uint32_t C, float* duty, float period, cudaStream_t stream);
+
 // Dynamic shared memory of the fused kernel for C columns.
 size_t step_smem_bytes(uint32_t C);
 

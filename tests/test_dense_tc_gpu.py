@@ -1,0 +1,146 @@
+"""Dense potential pools (every column sees the whole input) computed without
+learning on the tensor cores (tcgen05, bf16 {0,1} operands, fp32
+accumulation: exact), against the CPU oracle and against the per-frame
+kernel.  Bar: bit-exact."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1608_01966_gb300 as spg  # noqa: E402
+from paper_1608_01966_gb300 import synth, workloads as wl  # noqa: E402
+from helpers import dense, first_diff, oracle_run  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dense_case(C, n_in, seed, k=20, m=4, boost=None, lo=0.1, hi=0.3, **kw):
+    idx = synth.pool_dense(C, n_in)
+    perm = synth.perm_uniform(synth.derive_seed(seed, 2, 0), (C, n_in), lo, hi)
+    b = np.ones(C, np.float32) if boost is None else boost
+    return wl.Case("dense", n_in, 1, C, n_in, idx, perm, b, k=k, min_overlap=m, **kw)
+
+
+def _frames(F, n_in, p, seed):
+    return np.stack([synth.frame_bernoulli(synth.derive_seed(seed, 3, t), n_in, p)
+                     for t in range(F)])
+
+
+def _run(case, frames, cfg_extra=None):
+    packed = wl.pack(frames)
+    F = packed.shape[0]
+    cfg = case.config(**(cfg_extra or {}))
+    h = spg.sp_create_from_state(cfg, case.idx, case.perm, case.boost)
+    d = torch.from_numpy(packed.view(np.int32)).cuda()
+    dm = torch.zeros((F, (case.C + 31) // 32), dtype=torch.int32, device="cuda")
+    before = spg.sp_kernel_launch_count()
+    spg.sp_compute_frames_device(h, d, F, packed.shape[1], False, dm, torch.cuda.current_stream())
+    spg.sp_sync(h)
+    launches = spg.sp_kernel_launch_count() - before
+    out = dense(dm.cpu().numpy().view(np.uint32), case.C)
+    ov = spg.sp_get_overlaps(h)
+    lst = spg.sp_active_columns(h)
+    duty = spg.sp_get_duty_cycles(h) if (cfg_extra or {}).get("duty_period") else None
+    spg.sp_destroy(h)
+    return out, ov, lst, launches, duty
+
+
+def test_dense_pools_on_tensor_cores_match_oracle():
+    """1024 inputs x 1024 columns over 256 frames: two 128-frame tiles x four
+    256-column tiles, sixteen 64-input slices."""
+    case = _dense_case(1024, 1024, 41, k=40)
+    frames = _frames(256, 1024, 0.2, 42)
+    act, _, ov = oracle_run(case, frames, False, want_ov=True)
+    got, gov, lst, launches, _ = _run(case, frames)
+    assert launches <= 4  # pack, GEMM, per-frame inhibition: not 256 launches
+    assert first_diff(got, act) is None
+    np.testing.assert_array_equal(gov, ov[-1])
+    np.testing.assert_array_equal(lst, np.flatnonzero(act[-1]))
+
+
+def test_dense_ragged_tiles_and_boosts():
+    """Columns, inputs and frames that fill no tile exactly; non-unit boosts
+    (radix select); input bits beyond n_in in the last word are ignored."""
+    boost = synth.perm_uniform(7, (300,), 0.5, 2.0)
+    case = _dense_case(300, 1000, 43, k=9, m=1, boost=boost, lo=0.15, hi=0.25)
+    frames = _frames(130, 1000, 0.4, 44)
+    act, _, ov = oracle_run(case, frames, False, want_ov=True)
+    packed = wl.pack(frames)
+    packed[:, -1] |= np.uint32(0xFF000000)  # garbage in the unused high bits
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    d = torch.from_numpy(packed.view(np.int32)).cuda()
+    dm = torch.zeros((130, 10), dtype=torch.int32, device="cuda")
+    spg.sp_compute_frames_device(h, d, 130, packed.shape[1], False, dm, torch.cuda.current_stream())
+    spg.sp_sync(h)
+    assert first_diff(dense(dm.cpu().numpy().view(np.uint32), 300), act) is None
+    np.testing.assert_array_equal(spg.sp_get_overlaps(h), ov[-1])
+    spg.sp_destroy(h)
+
+
+def test_dense_local_inhibition_and_duty(monkeypatch):
+    case = _dense_case(256, 512, 45, k=3, m=2, inhibition=1, gw=16, gh=16, radius=2)
+    frames = _frames(40, 512, 0.3, 46)
+    act, _, _ = oracle_run(case, frames, False)
+    got, _, _, _, duty = _run(case, frames, {"duty_period": 10.0})
+    assert first_diff(got, act) is None
+    import oracle
+    d = np.zeros(256, np.float32)
+    for t in range(40):
+        oracle.duty_update(d, act[t], 10.0)
+    np.testing.assert_array_equal(duty, d)
+    # the per-frame kernel gives the same
+    monkeypatch.setenv("SP_DISABLE_TENSOR_CORES", "1")
+    got2, _, _, launches, _ = _run(case, frames)
+    assert launches >= 40 or launches == 1  # per-frame kernels (or one recorded graph)
+    np.testing.assert_array_equal(got2, got)
+
+
+def test_dense_run_after_learning_uses_learned_state():
+    """Learning frames (per-frame kernel) then an inference run on the tensor
+    cores: the run sees the learned permanences."""
+    case = _dense_case(512, 512, 47, k=10, m=2)
+    frames = _frames(40, 512, 0.3, 48)
+    act_l, perm, _ = oracle_run(case, frames[:8], True)
+    act_i, _, _ = oracle_run(case, frames[8:], False, perm=perm)
+    packed = wl.pack(frames)
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    for t in range(8):
+        spg.sp_compute(h, packed[t], True)
+    d = torch.from_numpy(packed[8:].view(np.int32)).cuda()
+    dm = torch.zeros((32, 16), dtype=torch.int32, device="cuda")
+    spg.sp_compute_frames_device(h, d, 32, packed.shape[1], False, dm, torch.cuda.current_stream())
+    spg.sp_sync(h)
+    assert first_diff(dense(dm.cpu().numpy().view(np.uint32), 512), act_i) is None
+    np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+    spg.sp_destroy(h)
+
+
+def test_batch_of_dense_sps_infers_in_two_launches():
+    """Dense SPs of different shapes in one batch: all overlaps in one
+    tensor-core launch, Alg. 2 for every frame and SP in one more."""
+    shapes = [(1024, 1024), (300, 500), (700, 2048), (1024, 1024)]
+    cases = [_dense_case(C, n, 50 + i, k=max(1, (2 * C + 50) // 100))
+             for i, (C, n) in enumerate(shapes)]
+    F = 130
+    frames = [_frames(F, c.n_in, 0.02 + 0.05 * i, 60 + i) for i, c in enumerate(cases)]
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    dm = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    before = spg.sp_kernel_launch_count()
+    spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
+    spg.sp_batch_sync(b)
+    assert spg.sp_kernel_launch_count() - before == 3  # pack, GEMM, inhibition
+    masks = dm.cpu().numpy().view(np.uint32)
+    spg.sp_batch_destroy(b)
+    for i, c in enumerate(cases):
+        act, _, ov = oracle_run(c, frames[i], False, want_ov=True)
+        got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+        assert first_diff(got, act) is None, f"member {i}"
+        np.testing.assert_array_equal(spg.sp_get_overlaps(hs[i]), ov[-1])
+        spg.sp_destroy(hs[i])
