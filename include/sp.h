@@ -90,7 +90,11 @@ typedef enum {
 } sp_status;
 
 enum { SP_POOL_UNIFORM = 0, SP_POOL_WINDOW = 1, SP_POOL_DENSE = 2 };
-enum { SP_INHIBIT_GLOBAL = 0, SP_INHIBIT_LOCAL = 1 };
+/* SP_INHIBIT_PAPER_LITERAL: Alg. 2 word for word over the whole SP, for
+ * comparison with the rank count: a column is active iff its overlap exceeds
+ * both 1 and the k-th largest overlap among the other columns (ties at the
+ * boundary all lose, so fewer than k columns may win). */
+enum { SP_INHIBIT_GLOBAL = 0, SP_INHIBIT_LOCAL = 1, SP_INHIBIT_PAPER_LITERAL = 2 };
 
 /* Configuration of one SP (Table 2 names the paper's defaults). */
 typedef struct {
@@ -203,6 +207,15 @@ SP_API sp_status sp_get_pool(sp_handle* h, uint32_t* out);
 
 /* Active-duty cycles [C] (host); SP_EINVAL unless duty_period > 0. */
 SP_API sp_status sp_get_duty_cycles(sp_handle* h, float* out);
+
+/* Checkpoint: write the SP (configuration, pools, permanences with all
+ * learning so far applied, boosts, duty cycles, frame count) to a file.
+ * Bounded wait for the handle's work.  SP_EINVAL on I/O errors. */
+SP_API sp_status sp_save(sp_handle* h, const char* path);
+
+/* Create an SP on the current device from a file written by sp_save;
+ * continuing it gives the results of never having stopped. */
+SP_API sp_status sp_load(const char* path, sp_handle** out);
 
 /* Boosts [C] (host). */
 SP_API sp_status sp_get_boost(sp_handle* h, float* out);

@@ -147,6 +147,8 @@ int orc_step(const orc_params* p, const uint32_t* idx, float* perm, const float*
   int rc;
   if (p->inhibition == 0) {
     rc = orc_inhibit_global(p->C, o, p->winners_set_size, active);
+  } else if (p->inhibition == 2) {
+    rc = orc_inhibit_paper_literal(p->C, o, p->winners_set_size, active);
   } else {
     if ((uint64_t)p->col_grid_w * p->col_grid_h != p->C) return -1;
     rc = orc_inhibit_local(p->col_grid_w, p->col_grid_h, o, p->winners_set_size,

@@ -59,7 +59,8 @@ typedef struct {
   float perm_inc, perm_dec;
   uint32_t min_overlap;
   uint32_t winners_set_size;
-  uint32_t inhibition;    /* 0 global, 1 local window on the column grid */
+  uint32_t inhibition;    /* 0 global, 1 local window on the column grid,
+                             2 the paper-literal reading of Alg. 2 (global) */
   uint32_t col_grid_w, col_grid_h; /* C = w * h when inhibition == 1 */
   uint32_t local_radius;  /* window (2r+1) x (2r+1), clipped at the edges */
 } orc_params;

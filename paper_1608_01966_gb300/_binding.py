@@ -15,7 +15,7 @@ import numpy as np
 SP_ABI_VERSION = 2
 SP_MAX_COLUMNS = 16384
 SP_POOL_UNIFORM, SP_POOL_WINDOW, SP_POOL_DENSE = 0, 1, 2
-SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL = 0, 1
+SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL, SP_INHIBIT_PAPER_LITERAL = 0, 1, 2
 STATUS = {0: "SP_OK", 1: "SP_EINVAL", 2: "SP_ENOMEM", 3: "SP_ECUDA", 4: "SP_ETIMEOUT",
           5: "SP_EBUSY", 6: "SP_ENOTSUP"}
 
@@ -107,6 +107,8 @@ def lib():
         L.sp_get_pool.argtypes = [vp, _u32p]
         L.sp_get_boost.argtypes = [vp, _f32p]
         L.sp_get_duty_cycles.argtypes = [vp, _f32p]
+        L.sp_save.argtypes = [vp, ct.c_char_p]
+        L.sp_load.argtypes = [ct.c_char_p, ct.POINTER(vp)]
         L.sp_set_boost.argtypes = [vp, _f32p]
         L.sp_sync.argtypes = [vp]
         L.sp_set_timeout_ms.argtypes = [vp, ct.c_uint32]
@@ -274,6 +276,16 @@ sp_get_pool = _getter("sp_get_pool", np.uint32,
                       lambda i: (i["num_columns"], i["synapses_per_column"]))
 sp_get_boost = _getter("sp_get_boost", np.float32, lambda i: (i["num_columns"],))
 sp_get_duty_cycles = _getter("sp_get_duty_cycles", np.float32, lambda i: (i["num_columns"],))
+
+
+def sp_save(h, path):
+    _check(lib().sp_save(h, os.fsencode(path)), "sp_save")
+
+
+def sp_load(path):
+    h = ct.c_void_p()
+    _check(lib().sp_load(os.fsencode(path), ct.byref(h)), "sp_load")
+    return h
 
 
 def sp_set_boost(h, boost):

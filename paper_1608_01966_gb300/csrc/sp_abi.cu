@@ -64,7 +64,7 @@ sp_status validate_config(const sp_config* c) {
   if (!(c->perm_inc >= 0.0f) || !(c->perm_dec >= 0.0f) || !std::isfinite(c->perm_inc) ||
       !std::isfinite(c->perm_dec))
     return fail(SP_EINVAL, "perm_inc / perm_dec must be finite and >= 0");
-  if (c->inhibition > SP_INHIBIT_LOCAL) return fail(SP_EINVAL, "inhibition %u", c->inhibition);
+  if (c->inhibition > SP_INHIBIT_PAPER_LITERAL) return fail(SP_EINVAL, "inhibition %u", c->inhibition);
   if (!(c->duty_period >= 0.0f) || std::isinf(c->duty_period) || c->reserved != 0u)
     return fail(SP_EINVAL, "duty_period must be finite and >= 0, reserved 0");
   const bool grid = c->col_grid_w != 0 || c->col_grid_h != 0;
@@ -138,6 +138,7 @@ void free_handle(sp_handle* h) {
 // be able to schedule such a cluster.  Failure only disables the path.
 void plan_cluster_path(sp_handle* h, const uint32_t* idx) {
   h->seq_ok = false;
+  if (h->cfg.inhibition == SP_INHIBIT_PAPER_LITERAL) return;  // per-frame kernel only
   uint32_t Q = (h->C + 31u) / 32u;
   if (Q > sp::kSeqMaxCluster) Q = sp::kSeqMaxCluster;
   if (Q < 2u) Q = 2u;
@@ -184,9 +185,11 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
   h->n_in = (uint64_t)cfg->input_w * cfg->input_h;
   h->n_words = (uint32_t)((h->n_in + 31) / 32);
   h->mask_words = (h->C + 31) / 32;
-  h->max_active = cfg->inhibition == SP_INHIBIT_GLOBAL
-                      ? (cfg->winners_set_size < h->C ? cfg->winners_set_size : h->C)
-                      : h->C;
+  h->max_active = cfg->inhibition == SP_INHIBIT_LOCAL
+                      ? h->C
+                      : (cfg->winners_set_size < h->C ? cfg->winners_set_size : h->C);
+  if (cfg->inhibition == SP_INHIBIT_PAPER_LITERAL && cfg->winners_set_size >= h->C)
+    h->max_active = h->C;  // no k-th largest among the others: the floor alone decides
   h->timeout_ms = default_timeout_ms();
   SP_CUDA(cudaGetDevice(&h->device));
   SP_CUDA(sp::kernels_init());
@@ -203,7 +206,7 @@ sp_status init_handle(sp_handle* h, const sp_config* cfg, const uint32_t* idx, c
     off[i] = total;
     total += align256(sizes[i]);
   }
-  SP_CUDA(cudaMalloc(&h->d_block, total));
+  SP_CUDA(device_malloc((void**)&h->d_block, total));
   h->device_bytes = total;
   char* b = static_cast<char*>(h->d_block);
   h->d_idx = reinterpret_cast<uint32_t*>(b + off[0]);
@@ -392,13 +395,13 @@ sp_status ensure_dense_buffers(sp_handle* h, uint32_t n) {
     h->d_run_ov = nullptr;
     h->d_run_masks = nullptr;
     h->run_cap = 0;
-    SP_CUDA(cudaMalloc(&h->d_run_ov, (size_t)n * h->C * 4));
-    SP_CUDA(cudaMalloc(&h->d_run_masks, (size_t)n * h->mask_words * 4));
+    SP_CUDA(device_malloc((void**)&h->d_run_ov, (size_t)n * h->C * 4));
+    SP_CUDA(device_malloc((void**)&h->d_run_masks, (size_t)n * h->mask_words * 4));
     h->run_cap = n;
   }
   if (!h->d_conn) {
     h->conn_words = 2u * ((h->S + 63u) / 64u);
-    SP_CUDA(cudaMalloc(&h->d_conn, (size_t)h->C * h->conn_words * 4));
+    SP_CUDA(device_malloc((void**)&h->d_conn, (size_t)h->C * h->conn_words * 4));
   }
   return SP_OK;
 }
@@ -763,8 +766,8 @@ SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint3
   sp_status s = use_stream(h, h->own_stream);
   if (s != SP_OK) return s;
   if (!h->d_stage) {
-    SP_CUDA(cudaMalloc(&h->d_stage, (size_t)kSlots * kChunkFrames * h->n_words * 4));
-    SP_CUDA(cudaMalloc(&h->d_mstage, (size_t)kSlots * kChunkFrames * h->mask_words * 4));
+    SP_CUDA(device_malloc((void**)&h->d_stage, (size_t)kSlots * kChunkFrames * h->n_words * 4));
+    SP_CUDA(device_malloc((void**)&h->d_mstage, (size_t)kSlots * kChunkFrames * h->mask_words * 4));
     SP_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
     SP_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
     for (int i = 0; i < kSlots; ++i) {
@@ -867,6 +870,90 @@ SP_API sp_status sp_get_duty_cycles(sp_handle* h, float* out) {
   DeviceGuard g(h->device);
   SP_CUDA(cudaMemcpyAsync(out, h->d_duty, (size_t)h->C * 4, cudaMemcpyDeviceToHost, h->stream));
   return wait_handle(h);
+}
+
+namespace {
+constexpr char kCkptMagic[8] = {'S', 'P', 'G', 'B', '3', '0', '0', '\0'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t config_bytes;
+  sp_config cfg;
+  uint32_t C, S;
+  uint64_t frames;
+};
+}  // namespace
+
+SP_API sp_status sp_save(sp_handle* h, const char* path) {
+  if (!h || !path) return fail(SP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
+  DeviceGuard g(h->device);
+  const size_t CS = (size_t)h->C * h->S;
+  std::vector<uint32_t> idx(CS);
+  std::vector<float> perm(CS), boost(h->C), duty(h->C, 0.0f);
+  sp_status s = flush_learning(h);
+  if (s != SP_OK) return s;
+  SP_CUDA(cudaMemcpyAsync(idx.data(), h->d_idx, CS * 4, cudaMemcpyDeviceToHost, h->stream));
+  SP_CUDA(cudaMemcpyAsync(perm.data(), h->d_perm, CS * 4, cudaMemcpyDeviceToHost, h->stream));
+  SP_CUDA(cudaMemcpyAsync(boost.data(), h->d_boost, (size_t)h->C * 4, cudaMemcpyDeviceToHost,
+                          h->stream));
+  SP_CUDA(cudaMemcpyAsync(duty.data(), h->d_duty, (size_t)h->C * 4, cudaMemcpyDeviceToHost,
+                          h->stream));
+  if ((s = wait_handle(h)) != SP_OK) return s;
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, sizeof(kCkptMagic));
+  hd.version = kCkptVersion;
+  hd.config_bytes = (uint32_t)sizeof(sp_config);
+  hd.cfg = h->cfg;
+  hd.C = h->C;
+  hd.S = h->S;
+  hd.frames = h->frames;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(SP_EINVAL, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+            std::fwrite(idx.data(), 4, CS, f) == CS && std::fwrite(perm.data(), 4, CS, f) == CS &&
+            std::fwrite(boost.data(), 4, h->C, f) == h->C &&
+            std::fwrite(duty.data(), 4, h->C, f) == h->C;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SP_OK : fail(SP_EINVAL, "writing %s failed", path);
+}
+
+SP_API sp_status sp_load(const char* path, sp_handle** out) {
+  if (!path || !out) return fail(SP_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(SP_EINVAL, "cannot open %s", path);
+  CkptHeader hd{};
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 &&
+            std::memcmp(hd.magic, kCkptMagic, sizeof(kCkptMagic)) == 0 &&
+            hd.version == kCkptVersion && hd.config_bytes == sizeof(sp_config) &&
+            hd.C == hd.cfg.num_columns && hd.S == hd.cfg.synapses_per_column &&
+            hd.C <= SP_MAX_COLUMNS && hd.S <= SP_MAX_SYNAPSES;
+  const size_t CS = ok ? (size_t)hd.C * hd.S : 0;
+  std::vector<uint32_t> idx(CS);
+  std::vector<float> perm(CS), boost(ok ? hd.C : 0), duty(ok ? hd.C : 0);
+  ok = ok && std::fread(idx.data(), 4, CS, f) == CS && std::fread(perm.data(), 4, CS, f) == CS &&
+       std::fread(boost.data(), 4, hd.C, f) == hd.C && std::fread(duty.data(), 4, hd.C, f) == hd.C;
+  std::fclose(f);
+  if (!ok) return fail(SP_EINVAL, "%s is not a readable SP checkpoint", path);
+  sp_handle* h = nullptr;
+  sp_status s = sp_create_from_state(&hd.cfg, idx.data(), perm.data(), boost.data(), &h);
+  if (s != SP_OK) return s;
+  h->frames = hd.frames;
+  {
+    DeviceGuard g(h->device);
+    const cudaError_t e = cudaMemcpyAsync(h->d_duty, duty.data(), (size_t)h->C * 4,
+                                          cudaMemcpyHostToDevice, h->stream);
+    s = e == cudaSuccess ? wait_handle(h) : fail(SP_ECUDA, "restoring duty cycles failed");
+  }
+  if (s != SP_OK) {
+    sp_destroy(h);
+    return s;
+  }
+  *out = h;
+  return SP_OK;
 }
 
 SP_API sp_status sp_set_boost(sp_handle* h, const float* boost) {
@@ -1147,7 +1234,7 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   b->mask_words = moff;
   b->n_ctas = (uint32_t)cta_inst.size();
   const size_t desc_bytes = align256(sizeof(sp::BatchDesc) * n);
-  cudaError_t e = cudaMalloc(&b->d_block, desc_bytes + cta_inst.size() * 4);
+  cudaError_t e = device_malloc((void**)&b->d_block, desc_bytes + cta_inst.size() * 4);
   if (e == cudaSuccess) {
     b->d_desc = static_cast<sp::BatchDesc*>(b->d_block);
     b->d_cta_inst = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_block) + desc_bytes);
@@ -1229,8 +1316,8 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
     // about 64 MiB of staged batch frames per slot
     uint64_t per = (64ull << 20) / (fw * 4u);
     b->stage_frames = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(per, kChunkFrames));
-    SP_CUDA(cudaMalloc(&b->d_stage, (size_t)kSlots * b->stage_frames * fw * 4));
-    SP_CUDA(cudaMalloc(&b->d_mstage, (size_t)kSlots * b->stage_frames * b->mask_words * 4));
+    SP_CUDA(device_malloc((void**)&b->d_stage, (size_t)kSlots * b->stage_frames * fw * 4));
+    SP_CUDA(device_malloc((void**)&b->d_mstage, (size_t)kSlots * b->stage_frames * b->mask_words * 4));
     SP_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
     SP_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
     for (int i = 0; i < kSlots; ++i) {
@@ -1349,7 +1436,7 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
   if (sp::frame_inhibit_smem(max_C, max_S) > sp::frame_inhibit_smem_limit())
     return fail(SP_ENOTSUP, "members too large for one per-frame inhibition launch");
   if (!b->d_infer_args)
-    SP_CUDA(cudaMalloc(&b->d_infer_args, (sizeof(sp::DenseArgs) + sizeof(sp::FrameInhibitArgs)) * n));
+    SP_CUDA(device_malloc((void**)&b->d_infer_args, (sizeof(sp::DenseArgs) + sizeof(sp::FrameInhibitArgs)) * n));
   sp::DenseArgs* d_dargs = static_cast<sp::DenseArgs*>(b->d_infer_args);
   sp::FrameInhibitArgs* d_fargs = reinterpret_cast<sp::FrameInhibitArgs*>(d_dargs + n);
   // the argument arrays go through the stream so earlier launches keep theirs

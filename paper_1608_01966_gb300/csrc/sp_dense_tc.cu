@@ -355,9 +355,12 @@ __global__ void __launch_bounds__(kStepThreads) sp_frame_inhibit_kernel(const In
     dev::select_threshold<kStepThreads>(sv, a.C, a.k, nz_tot, nullptr, unit_S ? unit_S : 0u,
                                         shist, sh, s2, T, need);
     total = dev::mark_global<kStepThreads>(sv, a.C, T, need, smask, list, sh);
-  } else {
+  } else if (a.inhibition == 1u) {
     __syncthreads();
     total = dev::mark_local<kStepThreads>(sv, 0u, a.C, a.gw, a.gh, a.radius, a.k, smask, list, sh);
+  } else {
+    __syncthreads();
+    total = dev::mark_paper_literal<kStepThreads>(sv, a.C, a.k, smask, list, shist, sh, s2);
   }
   __syncthreads();
   for (uint32_t i = t; i < a.mask_words; i += kStepThreads) {

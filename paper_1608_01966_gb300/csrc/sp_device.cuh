@@ -189,6 +189,94 @@ __device__ void select_threshold(const uint32_t* sv, uint32_t C, uint32_t k, uin
   need = kk;   // how many columns equal to T still win
 }
 
+// The k-th largest of the C overlap patterns in sv, repeats and zeros
+// included (0 when k is 0 or larger than C): radix select over all values.
+// shist holds 256 words; sh 2 * NW; s2 2.  Every thread must call it.
+template <int NTHREADS>
+__device__ uint32_t kth_largest(const uint32_t* sv, uint32_t C, uint32_t k, uint32_t* shist,
+                                uint32_t* s2) {
+  const uint32_t t = threadIdx.x;
+  if (k == 0u || k > C) return 0u;
+  uint32_t prefix = 0u, pmask = 0u, kk = k;
+  const uint32_t rounds = (C + NTHREADS - 1) / NTHREADS;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (uint32_t i = t; i < 256u; i += NTHREADS) shist[i] = 0u;
+    __syncthreads();
+    for (uint32_t r = 0; r < rounds; ++r) {
+      const uint32_t i = r * NTHREADS + t;
+      const uint32_t v = i < C ? sv[i] : 0u;
+      warp_hist_add(shist, (v >> shift) & 255u, i < C && (v & pmask) == prefix);
+    }
+    __syncthreads();
+    if (t < 32u) {
+      uint32_t loc[8], sum = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        loc[j] = shist[255u - 8u * t - j];
+        sum += loc[j];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if ((int)t >= o) incl += y;
+      }
+      uint32_t above = incl - sum;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (above < kk && above + loc[j] >= kk) {
+          s2[0] = 255u - 8u * t - j;
+          s2[1] = above;
+        }
+        above += loc[j];
+      }
+    }
+    __syncthreads();
+    prefix |= s2[0] << shift;
+    pmask |= 0xffu << shift;
+    kk -= s2[1];
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// Alg. 2 taken word for word (the paper-literal variant, for comparison):
+// column c is active iff ov > max(n-th largest overlap of the other columns,
+// 1), n = k.  With w_j the j-th largest of all overlaps, the n-th largest of
+// the others is w_{k+1} when ov >= w_k and w_k otherwise (0 when fewer than
+// k others exist), so c is active iff ov > 1 and, when k < C, ov >= w_k and
+// ov > w_{k+1}.  Sets smask bits; writes the ascending list if list is set.
+template <int NTHREADS>
+__device__ uint32_t mark_paper_literal(const uint32_t* sv, uint32_t C, uint32_t k,
+                                       uint32_t* smask, uint32_t* list, uint32_t* shist,
+                                       uint32_t* sh, uint32_t* s2) {
+  constexpr int NW = NTHREADS / 32;
+  const uint32_t wk = kth_largest<NTHREADS>(sv, C, k, shist, s2);
+  const uint32_t wk1 = kth_largest<NTHREADS>(sv, C, k + 1u, shist, s2);
+  const uint32_t one = __float_as_uint(1.0f);
+  const uint32_t t = threadIdx.x;
+  const uint32_t per = (C + NTHREADS - 1) / NTHREADS;
+  const uint32_t lo = min(C, t * per), hi = min(C, lo + per);
+  uint32_t wins = 0;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t v = sv[i];
+    // k = 0 or k >= C: no n-th largest among the others, the floor 1 decides
+    const bool w = v > one && ((k == 0u || k >= C) || (v >= wk && v > wk1));
+    if (w) {
+      ++wins;
+      atomicOr(smask + (i >> 5), 1u << (i & 31u));
+    }
+  }
+  uint32_t ex, e1, tot, z;
+  block_scan2<NW>(wins, 0u, ex, e1, tot, z, sh);
+  if (list) {
+    uint32_t pos = ex;
+    for (uint32_t i = lo; i < hi; ++i)
+      if ((smask[i >> 5] >> (i & 31u)) & 1u) list[pos++] = i;
+  }
+  return tot;
+}
+
 // Winner flags of global inhibition for all C columns, given (T, need):
 // sets bits of smask (zeroed by the caller) and, if list != nullptr, writes
 // the ascending winner list there.  Returns the number of winners.

@@ -111,6 +111,18 @@ inline bool dense_enabled() {
   return !(s && s[0] == '1');
 }
 
+// Device allocation used by the whole runtime.  SP_INJECT_ALLOC_FAILURE=1
+// makes it fail as an out-of-memory device would (host-side fault injection
+// for tests: nothing reaches the GPU).
+inline cudaError_t device_malloc(void** p, size_t bytes) {
+  const char* s = std::getenv("SP_INJECT_ALLOC_FAILURE");
+  if (s && s[0] == '1') {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 inline bool graphs_enabled() {
   const char* s = std::getenv("SP_DISABLE_GRAPHS");
   return !(s && s[0] == '1');

@@ -83,7 +83,7 @@ SP_API sp_status sp_step_noalloc(const sp_config* cfg, const uint32_t* d_idx, fl
   if (!std::isfinite(cfg->connect_threshold) || !(cfg->perm_inc >= 0.0f) ||
       !(cfg->perm_dec >= 0.0f) || !std::isfinite(cfg->perm_inc) || !std::isfinite(cfg->perm_dec))
     return noalloc_fail(SP_EINVAL, "threshold / perm_inc / perm_dec invalid");
-  if (cfg->inhibition > SP_INHIBIT_LOCAL) return noalloc_fail(SP_EINVAL, "inhibition mode");
+  if (cfg->inhibition > SP_INHIBIT_PAPER_LITERAL) return noalloc_fail(SP_EINVAL, "inhibition mode");
   if (cfg->inhibition == SP_INHIBIT_LOCAL &&
       ((uint64_t)cfg->col_grid_w * cfg->col_grid_h != C || cfg->col_grid_w == 0))
     return noalloc_fail(SP_EINVAL, "local inhibition needs col_grid_w * col_grid_h == num_columns");

@@ -301,7 +301,7 @@ sp_status admit(sp_server* s, sp_handle* h, uint32_t* stream_id) {
   S.n_ctas = d.n_ctas;
   const size_t ring_bytes = (size_t)s->cfg.queue_depth * info.input_words * 4;
   cudaError_t e = cudaMallocHost(&S.h_ring, ring_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&S.d_ring, ring_bytes);
+  if (e == cudaSuccess) e = device_malloc((void**)&S.d_ring, ring_bytes);
   S.ev_h2d.assign(s->cfg.queue_depth, nullptr);
   for (uint32_t i = 0; e == cudaSuccess && i < s->cfg.queue_depth; ++i)
     e = cudaEventCreateWithFlags(&S.ev_h2d[i], cudaEventDisableTiming);
@@ -379,7 +379,7 @@ SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out) 
   s->max_ctas = cfg->max_streams * batch_ctas(SP_MAX_COLUMNS, 128u);  // the largest share
   const uint32_t row = 1u + cfg->max_active;
   cudaError_t e = sp::kernels_init();
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_desc, sizeof(sp::BatchDesc) * cfg->max_streams);
+  if (e == cudaSuccess) e = device_malloc((void**)&s->d_desc, sizeof(sp::BatchDesc) * cfg->max_streams);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   for (auto& L : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
@@ -387,9 +387,9 @@ SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out) 
     if (e == cudaSuccess) e = cudaMallocHost(&L.h_table, sizeof(sp::TickMember) * cfg->max_streams);
     if (e == cudaSuccess) e = cudaMallocHost(&L.h_cta, (size_t)s->max_ctas * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&L.h_results, (size_t)cfg->max_streams * row * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_table, sizeof(sp::TickMember) * cfg->max_streams);
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_cta, (size_t)s->max_ctas * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_results, (size_t)cfg->max_streams * row * 4);
+    if (e == cudaSuccess) e = device_malloc((void**)&L.d_table, sizeof(sp::TickMember) * cfg->max_streams);
+    if (e == cudaSuccess) e = device_malloc((void**)&L.d_cta, (size_t)s->max_ctas * 4);
+    if (e == cudaSuccess) e = device_malloc((void**)&L.d_results, (size_t)cfg->max_streams * row * 4);
   }
   if (e != cudaSuccess) {
     free_server(s);

@@ -140,10 +140,14 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
     dev::select_threshold<kStepThreads>(sv, C, a.k, nz_tot, a.hist, a.hist ? a.S : 0u, shist,
                                         sh, s2, T, need);
     total = dev::mark_global<kStepThreads>(sv, C, T, need, smask, a.result + 1, sh);
-  } else {
+  } else if (a.inhibition == 1u) {
     __syncthreads();
     total = dev::mark_local<kStepThreads>(sv, 0u, C, a.gw, a.gh, a.radius, a.k, smask,
                                           a.result + 1, sh);
+  } else {
+    __syncthreads();
+    total = dev::mark_paper_literal<kStepThreads>(sv, C, a.k, smask, a.result + 1, shist, sh,
+                                                  s2);
   }
   __syncthreads();
   if (t == 0u) a.result[0] = total;

@@ -369,3 +369,13 @@ def test_duty_cycle_closed_forms():
     ref = 1 - (1 - 1 / P) ** n
     assert abs(float(d[0]) - ref) < n * 2 ** -23
     assert d[1] == 0 and d[0] == d[2]
+
+
+def test_step_dispatches_the_paper_literal_reading():
+    """orc_step with inhibition 2 applies the word-for-word Alg. 2."""
+    idx, perm = _random_sp(30, 80, 16, 256, 0.2, 0.2)
+    x = synth.frame_bernoulli(31, 256, 0.5)
+    p = oracle.params(80, 16, 256, 0.2, 0.05, 0.02, 1, 7, inhibition=2)
+    _, ov = oracle.overlap(idx, perm, np.ones(80, F32), x, 0.2, 1)
+    act = oracle.run(p, idx, perm.copy(), np.ones(80, F32), x[None, :], False)[0]
+    np.testing.assert_array_equal(act, oracle.inhibit_paper_literal(ov, 7))

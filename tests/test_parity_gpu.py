@@ -376,3 +376,24 @@ def test_pending_learning_hands_over_between_paths():
             np.testing.assert_array_equal(spg.sp_active_columns(h), np.flatnonzero(act[-1]))
     np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
     spg.sp_destroy(h)
+
+
+@pytest.mark.parametrize("k", [1, 7, 40, 299, 300, 400])
+def test_paper_literal_inhibition(k):
+    """The word-for-word reading of Alg. 2 (strict '>' against the k-th
+    largest overlap of the other columns, floor 1) on the per-frame kernel:
+    heavy ties at the boundary, k up to and beyond C, boosts that push some
+    overlaps to 1 or below."""
+    boost = np.where(np.arange(300) % 5 == 0, np.float32(0.25), np.float32(1.0)).astype(np.float32)
+    case = _uniform_case(300, 12, 512, 131, k=k, min_overlap=1, lo=0.2, hi=0.2, boost=boost,
+                         inhibition=2)
+    frames = _bern(6, 512, 0.35, 14)
+    act, perm, ov = oracle_run(case, frames, True, want_ov=True)
+    assert act.sum() > 0
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    for t in range(6):
+        spg.sp_compute(h, synth.pack_bits(frames[t]), True)
+        np.testing.assert_array_equal(spg.sp_active_columns(h), np.flatnonzero(act[t]),
+                                      err_msg=f"frame {t}")
+    np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+    spg.sp_destroy(h)
