@@ -66,6 +66,7 @@ bool all_ones(const float* v, size_t n);
 sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
 uint32_t batch_ctas(uint32_t C, uint32_t S);
+uint32_t batch_stage_cap(uint32_t need);
 void fill_desc(const sp_handle* h, sp::BatchDesc* d);
 
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames

@@ -86,10 +86,14 @@ struct BatchArgs {
   const TickMember* tick;       // if set: per-SP frame/state (indexed like desc); the
                                 // uniform fields above are then ignored
   uint32_t* results_out;        // with tick: per-SP [count, ascending list]
+  uint32_t stage_cap;           // bytes of dynamic shared memory for staging state (0: none)
+  uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
 };
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream);
+// Shared memory a batch CTA needs to stage its columns' pools and permanences.
+uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas);
 
 // Learning of one frame applied on its own (used to flush pending learning).
 struct LearnArgs {

@@ -53,6 +53,7 @@ struct Stream {
   bool pending = false;
   uint64_t next_seq = 0;
   uint32_t n_ctas = 0, max_active = 0, input_words = 0;
+  uint32_t stage_bytes = 0;    // shared memory to stage its CTAs' state
 };
 
 struct Done {
@@ -70,6 +71,8 @@ struct LaunchSlot {
   sp::TickMember* d_table = nullptr;
   uint32_t* d_cta = nullptr;
   uint32_t* d_results = nullptr;
+  uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
+  uint32_t* d_err = nullptr;
   std::vector<std::pair<uint32_t, Request>> members;  // (slot, request)
 };
 
@@ -175,8 +178,13 @@ sp_status start_launch(sp_server* s, LaunchSlot& L) {
   a.cta_inst = L.d_cta;
   a.tick = L.d_table;
   a.results_out = L.d_results;
-  uint32_t max_C = 1;
-  for (auto& m : L.members) max_C = std::max(max_C, s->streams[m.first].h->C);
+  uint32_t max_C = 1, stage = 0;
+  for (auto& m : L.members) {
+    max_C = std::max(max_C, s->streams[m.first].h->C);
+    stage = std::max(stage, s->streams[m.first].stage_bytes);
+  }
+  a.stage_cap = batch_stage_cap(stage);
+  a.err = L.d_err;
   SP_CUDA(sp::launch_batch_step(a, ctas, max_C, L.st));
   SP_CUDA(cudaMemcpyAsync(L.h_results, L.d_results, (size_t)count * row * 4,
                           cudaMemcpyDeviceToHost, L.st));
@@ -197,7 +205,12 @@ void worker_main(sp_server* s) {
       if (!L.busy) continue;
       const cudaError_t e = cudaEventQuery(L.done);
       if (e == cudaErrorNotReady) continue;
-      finish_launch(s, L, e == cudaSuccess ? SP_OK : SP_ECUDA);
+      sp_status st = e == cudaSuccess ? SP_OK : SP_ECUDA;
+      if (st == SP_OK && *reinterpret_cast<volatile uint32_t*>(L.h_err)) {
+        *L.h_err = 0u;
+        st = SP_ETIMEOUT;
+      }
+      finish_launch(s, L, st);
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
@@ -260,6 +273,7 @@ void free_server(sp_server* s) {
     if (L.h_table) cudaFreeHost(L.h_table);
     if (L.h_cta) cudaFreeHost(L.h_cta);
     if (L.h_results) cudaFreeHost(L.h_results);
+    if (L.h_err) cudaFreeHost(L.h_err);
     if (L.d_table) cudaFree(L.d_table);
     if (L.d_cta) cudaFree(L.d_cta);
     if (L.d_results) cudaFree(L.d_results);
@@ -299,6 +313,7 @@ sp_status admit(sp_server* s, sp_handle* h, uint32_t* stream_id) {
   sp::BatchDesc d;
   fill_desc(h, &d);
   S.n_ctas = d.n_ctas;
+  S.stage_bytes = sp::batch_stage_bytes(h->C, h->S, d.n_ctas);
   const size_t ring_bytes = (size_t)s->cfg.queue_depth * info.input_words * 4;
   cudaError_t e = cudaMallocHost(&S.h_ring, ring_bytes);
   if (e == cudaSuccess) e = device_malloc((void**)&S.d_ring, ring_bytes);
@@ -390,6 +405,11 @@ SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out) 
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_table, sizeof(sp::TickMember) * cfg->max_streams);
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_cta, (size_t)s->max_ctas * 4);
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_results, (size_t)cfg->max_streams * row * 4);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&L.h_err, 4, cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      *L.h_err = 0u;
+      e = cudaHostGetDevicePointer((void**)&L.d_err, L.h_err, 0);
+    }
   }
   if (e != cudaSuccess) {
     free_server(s);

@@ -28,6 +28,7 @@
 // built with -fmad=false); comparisons are exact.
 #include "sp_kernels.cuh"
 
+#include <algorithm>
 #include <atomic>
 
 #include "sp_device.cuh"
@@ -173,10 +174,129 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
   }
 }
 
-// One frame of one SP, run by nb CTAs of which this is number bid.
-template <int VEC, bool STREAM>
+// Two columns by one warp with all four 16-byte vectors of each lane in
+// flight before the first gather (S <= 256, S % 4 == 0): twice the bytes in
+// flight of column_overlap.  has1 = false leaves the second column out.
+template <bool STREAM>
+__device__ __forceinline__ void column_overlap_pair(const StepArgs& a, uint32_t c0, uint32_t c1,
+                                                    bool has1, bool learn0, bool learn1,
+                                                    int lane, uint32_t& raw0, uint32_t& raw1) {
+  const uint32_t n4 = a.S >> 2;  // <= 64
+  const uint32_t ja = lane, jb = 32u + lane;
+  const bool va = ja < n4, vb = jb < n4;
+  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  const float4 f4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const uint4* i0 = reinterpret_cast<const uint4*>(a.idx + (uint64_t)c0 * a.S);
+  const uint4* i1 = reinterpret_cast<const uint4*>(a.idx + (uint64_t)c1 * a.S);
+  float4* q0 = reinterpret_cast<float4*>(a.perm + (uint64_t)c0 * a.S);
+  float4* q1 = reinterpret_cast<float4*>(a.perm + (uint64_t)c1 * a.S);
+  const uint4 ida0 = va ? ld_state<STREAM>(i0 + ja) : z4;
+  const uint4 idb0 = vb ? ld_state<STREAM>(i0 + jb) : z4;
+  float4 pa0 = va ? ld_state<STREAM>(q0 + ja) : f4;
+  float4 pb0 = vb ? ld_state<STREAM>(q0 + jb) : f4;
+  const uint4 ida1 = (has1 && va) ? ld_state<STREAM>(i1 + ja) : z4;
+  const uint4 idb1 = (has1 && vb) ? ld_state<STREAM>(i1 + jb) : z4;
+  float4 pa1 = (has1 && va) ? ld_state<STREAM>(q1 + ja) : f4;
+  float4 pb1 = (has1 && vb) ? ld_state<STREAM>(q1 + jb) : f4;
+  if (learn0) {
+    if (va) {
+      learn4(pa0, ida0, a);
+      q0[ja] = pa0;
+    }
+    if (vb) {
+      learn4(pb0, idb0, a);
+      q0[jb] = pb0;
+    }
+  }
+  if (has1 && learn1) {
+    if (va) {
+      learn4(pa1, ida1, a);
+      q1[ja] = pa1;
+    }
+    if (vb) {
+      learn4(pb1, idb1, a);
+      q1[jb] = pb1;
+    }
+  }
+  uint32_t n0 = 0, n1 = 0;
+  if (va) n0 += count4(pa0, ida0, a.thr, a.x);
+  if (vb) n0 += count4(pb0, idb0, a.thr, a.x);
+  if (has1 && va) n1 += count4(pa1, ida1, a.thr, a.x);
+  if (has1 && vb) n1 += count4(pb1, idb1, a.thr, a.x);
+  raw0 = __reduce_add_sync(kFull, n0);
+  raw1 = __reduce_add_sync(kFull, n1);
+}
+
+// Columns of one SP given to CTA bid of nb: a contiguous range when
+// SP_CONTIG_COLUMNS (neighbouring receptive fields share cached input
+// words), else every nb-th group of kStepWarps columns.
+#ifndef SP_CONTIG_COLUMNS
+#define SP_CONTIG_COLUMNS 1
+#endif
+#ifndef SP_PAIR_COLUMNS
+#define SP_PAIR_COLUMNS 0
+#endif
+
+constexpr uint32_t kStageWaitLimit = 1u << 26;  // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Copy one contiguous block of global memory into shared memory with the
+// bulk-copy engine, completing on mbar (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < kStageWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Raw overlap of column c from its pool and permanences staged in shared
+// memory (rows ri/rp); the learning of the previous frame, if due, updates
+// the staged row and the global row.
+__device__ __forceinline__ uint32_t staged_overlap(const StepArgs& a, uint32_t c,
+                                                   const uint32_t* ri, float* rp, bool learn_now,
+                                                   int lane) {
+  uint32_t cnt = 0;
+  const uint32_t n4 = a.S >> 2;
+  const uint4* id4 = reinterpret_cast<const uint4*>(ri);
+  float4* p4 = reinterpret_cast<float4*>(rp);
+  float4* g4 = reinterpret_cast<float4*>(a.perm + (uint64_t)c * a.S);
+  for (uint32_t j = lane; j < n4; j += 32) {
+    const uint4 id = id4[j];
+    float4 p = p4[j];
+    if (learn_now) {
+      learn4(p, id, a);
+      g4[j] = p;
+    }
+    cnt += count4(p, id, a.thr, a.x);
+  }
+  return __reduce_add_sync(kFull, cnt);
+}
+
+// One frame of one SP, run by nb CTAs of which this is number bid.  With
+// STAGE, a CTA whose columns' state fits in stage_cap bytes of dynamic
+// shared memory stages it there by bulk copy first.
+template <int VEC, bool STREAM, bool STAGE = false>
 __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint32_t nb,
-                                          uint32_t* dyn_smem) {
+                                          uint32_t* dyn_smem, uint32_t stage_cap = 0u,
+                                          uint32_t* err = nullptr) {
   __shared__ uint32_t s_ticket;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -185,14 +305,82 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
       a.x_save[i] = __ldg(a.x + i);
   }
   bool wrote = false;
-  for (uint32_t c = bid * kStepWarps + warp; c < a.C; c += nb * kStepWarps) {
-    const bool learn_now = a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
-    const uint32_t raw = column_overlap<VEC, STREAM>(a, c, learn_now, lane);
-    if (lane == 0) {
-      a.ov[c] = dev::boosted(raw, a.min_overlap, __ldg(a.boost + c));
-      // unit boosts: the overlap is the count, histogrammed for the select
-      if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
-      wrote = true;
+  uint32_t c_first, c_end, c_step;
+  if (SP_CONTIG_COLUMNS) {
+    const uint32_t per = (a.C + nb - 1u) / nb;
+    c_first = min(a.C, bid * per) + warp;
+    c_end = min(a.C, (bid + 1u) * per);
+    c_step = kStepWarps;
+  } else {
+    c_first = bid * kStepWarps + warp;
+    c_end = a.C;
+    c_step = nb * kStepWarps;
+  }
+  auto publish = [&](uint32_t c, uint32_t raw) {
+    a.ov[c] = dev::boosted(raw, a.min_overlap, __ldg(a.boost + c));
+    // unit boosts: the overlap is the count, histogrammed for the select
+    if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
+    wrote = true;
+  };
+  auto learning = [&](uint32_t c) {
+    return a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
+  };
+  const uint32_t n_cols = c_end > c_first - warp ? c_end - (c_first - warp) : 0u;
+  const uint32_t stage = n_cols * a.S * 4u;  // bytes of pools (and of permanences)
+  if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && n_cols > 0u && 2u * stage <= stage_cap) {
+    // the CTA's columns are contiguous: two bulk copies bring all their
+    // pools and permanences into shared memory at once
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_fail;
+    const uint32_t c_lo = c_first - warp;
+    uint32_t* s_idx = dyn_smem;
+    float* s_perm = reinterpret_cast<float*>(dyn_smem + n_cols * a.S);
+    if (threadIdx.x == 0) {
+      s_fail = 0u;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&s_mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                       smem_addr(&s_mbar)),
+                   "r"(2u * stage)
+                   : "memory");
+      bulk_g2s(s_idx, a.idx + (uint64_t)c_lo * a.S, stage, &s_mbar);
+      bulk_g2s(s_perm, a.perm + (uint64_t)c_lo * a.S, stage, &s_mbar);
+    }
+    if (!stage_wait(&s_mbar, 0u)) s_fail = 1u;
+    __syncthreads();
+    if (s_fail) {
+      stage_wait(&s_mbar, 0u);  // bounded: let the copies land before leaving
+      if (threadIdx.x == 0 && err) atomicExch(err, 1u);
+      for (uint32_t c = c_first; c < c_end; c += c_step)
+        if (lane == 0) publish(c, 0u);
+    } else {
+      for (uint32_t c = c_first; c < c_end; c += c_step) {
+        const uint32_t r = c - c_lo;
+        const uint32_t raw =
+            staged_overlap(a, c, s_idx + r * a.S, s_perm + r * a.S, learning(c), lane);
+        if (lane == 0) publish(c, raw);
+      }
+    }
+    __syncthreads();  // the staging area becomes the last CTA's working memory
+  } else if (SP_PAIR_COLUMNS && VEC == 4 && STREAM && a.S <= 256u) {
+    for (uint32_t c = c_first; c < c_end; c += 2u * c_step) {
+      const uint32_t c1 = c + c_step;
+      const bool has1 = c1 < c_end;
+      uint32_t raw0, raw1;
+      column_overlap_pair<STREAM>(a, c, has1 ? c1 : c, has1, learning(c), has1 && learning(c1),
+                                  lane, raw0, raw1);
+      if (lane == 0) {
+        publish(c, raw0);
+        if (has1) publish(c1, raw1);
+      }
+    }
+  } else {
+    for (uint32_t c = c_first; c < c_end; c += c_step) {
+      const uint32_t raw = column_overlap<VEC, STREAM>(a, c, learning(c), lane);
+      if (lane == 0) publish(c, raw);
     }
   }
   // publish this CTA's overlaps (only their writers need the fence; the
@@ -210,7 +398,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
 
 template <int VEC>
 __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a) {
-  extern __shared__ uint32_t dyn_smem[];
+  extern __shared__ __align__(128) uint32_t dyn_smem[];
   step_body<VEC, false>(a, blockIdx.x, gridDim.x, dyn_smem);
 }
 
@@ -221,7 +409,7 @@ __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a)
 
 // One frame for every SP of a batch: CTA b works on SP cta_inst[b].
 __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_step_kernel(const BatchArgs ba) {
-  extern __shared__ uint32_t dyn_smem[];
+  extern __shared__ __align__(128) uint32_t dyn_smem[];
   const uint32_t inst = __ldg(ba.cta_inst + blockIdx.x);
   const BatchDesc& d = ba.desc[inst];
   StepArgs a;
@@ -275,7 +463,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.radius = d.radius;
   const uint32_t bid = blockIdx.x - cta_first;
   if ((a.S & 3u) == 0u)
-    step_body<4, true>(a, bid, d.n_ctas, dyn_smem);
+    step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, ba.stage_cap, ba.err);
   else
     step_body<1, true>(a, bid, d.n_ctas, dyn_smem);
 }
@@ -310,9 +498,16 @@ cudaError_t kernels_init() {
                               bytes);
 }
 
+uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas) {
+  if (S % 4u) return 0u;
+  const uint32_t per = (C + n_ctas - 1u) / n_ctas;
+  return per * S * 8u;
+}
+
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream) {
-  sp_batch_step_kernel<<<n_ctas, kStepThreads, step_smem_bytes(max_C), stream>>>(a);
+  const size_t smem = std::max<size_t>(step_smem_bytes(max_C), a.stage_cap);
+  sp_batch_step_kernel<<<n_ctas, kStepThreads, smem, stream>>>(a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

@@ -85,6 +85,22 @@ def test_batch_uneven_shapes_and_modes():
     _check(cases, frames, True, acts, perms, ovs, "uneven")
 
 
+@pytest.mark.parametrize("cpw", ["1", "4", "8"])
+def test_batch_staged_state(monkeypatch, cpw):
+    """The opt-in form that brings each CTA's pools and permanences into
+    shared memory by bulk copy, over uneven members (those with S not a
+    multiple of 4 or whose block exceeds the cap take the streamed form)."""
+    monkeypatch.setenv("SP_BATCH_STAGE_KB", "64")
+    monkeypatch.setenv("SP_BATCH_COLS_PER_WARP", cpw)
+    cases, dens = wl.uneven_cases(8, c_range=(64, 1500), n_in_range=(256, 4096))
+    cases.append(wl.frame_case(seed=wl.BASE_SEED + 300))
+    dens.append(None)
+    frames = [wl.blob_frames(8, seed=wl.BASE_SEED + 300) if d is None
+              else wl.bernoulli_frames(i, c.n_in, d, 8) for i, (c, d) in enumerate(zip(cases, dens))]
+    acts, perms, ovs = _run_batch(cases, frames, True, [1, 7])
+    _check(cases, frames, True, acts, perms, ovs, f"staged cpw={cpw}")
+
+
 def test_batch_equals_members_alone_and_hands_back_state():
     """A batch, then each member continued alone: the same as the oracle over
     the whole sequence (pending learning handed back by the batch)."""
