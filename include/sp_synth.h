@@ -102,6 +102,19 @@ SYNTH_API int synth_frame_blobbed(uint64_t seed, uint32_t W, uint32_t H, double 
                                   double p_hi, uint8_t* out_bits, uint8_t* scratch,
                                   double* out_p);
 
+/* Colour video-like frame of W x H pixels, 3 bytes (R, G, B) per pixel,
+ * row-major: blobs under an illumination ramp, for the frame encoder.
+ *   1. p = 0.05 + 0.15 u; per-channel gains g_c = 96 + (r mod 160); a ramp
+ *      direction from the low 2 bits of one draw;
+ *   2. field = (v * 255 + 24) / 49 with v the 7x7 box sum (clipped at the
+ *      borders) of Bernoulli(p) noise, as in synth_frame_blobbed;
+ *   3. light = 64 + 191 (x' + y') / (W + H - 2), x'/y' mirrored by the
+ *      direction bits;
+ *   4. channel c = (min(255, (field g_c + 32) / 64) * light + 127) / 255.
+ * scratch must hold 2 * W * H bytes. */
+SYNTH_API int synth_frame_rgb(uint64_t seed, uint32_t W, uint32_t H, uint8_t* out_rgb,
+                              uint8_t* scratch);
+
 /* Pack n one-byte bits (nonzero = 1) into ceil(n/32) LSB-first words; the
  * unused high bits of the last word are zero. */
 SYNTH_API int synth_pack_bits(const uint8_t* bits, uint64_t n, uint32_t* out_words);

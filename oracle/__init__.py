@@ -133,3 +133,18 @@ def duty_update(duty, active, period):
     _check(lib().orc_duty_update(ct.c_uint32(duty.size), _p(duty, ct.c_float),
                                  _p(active, ct.c_uint8), ct.c_float(period)), "duty_update")
     return duty
+
+
+def encode(src, reduce=1, block=11, offset=2):
+    """Frame encoder: src uint8 [H, W] (gray) or [H, W, 3] (R, G, B).
+    Returns the binary image uint8 [H // reduce, W // reduce] (0/1)."""
+    src = np.ascontiguousarray(src, dtype=np.uint8)
+    H, W = src.shape[:2]
+    ch = 1 if src.ndim == 2 else src.shape[2]
+    if reduce < 1:
+        raise ValueError("oracle encode: invalid argument")
+    out = np.zeros((H // reduce, W // reduce), np.uint8)
+    _check(lib().orc_encode(_p(src, ct.c_uint8), ct.c_uint32(W), ct.c_uint32(H),
+                            ct.c_uint32(ch), ct.c_uint32(reduce), ct.c_uint32(block),
+                            ct.c_int32(offset), _p(out, ct.c_uint8)), "encode")
+    return out

@@ -185,4 +185,59 @@ int orc_duty_update(uint32_t C, float* duty, const uint8_t* active, float period
   return 0;
 }
 
+int orc_encode(const uint8_t* src, uint32_t W, uint32_t H, uint32_t channels, uint32_t reduce,
+               uint32_t block, int32_t offset, uint8_t* out_bits) {
+  if (!src || !out_bits || W == 0 || H == 0) return -1;
+  if (channels != 1 && channels != 3) return -1;
+  if (reduce == 0 || block < 3 || block > 13 || block % 2 == 0) return -1;
+  const uint32_t Wr = W / reduce, Hr = H / reduce;
+  if (Wr == 0 || Hr == 0) return -1;
+  // 1 + 2. reduction of each channel, then the luma of the reduced pixel
+  std::vector<int64_t> gray((size_t)Wr * Hr);
+  const uint64_t area = (uint64_t)reduce * reduce;
+  for (uint32_t y = 0; y < Hr; ++y) {
+    for (uint32_t x = 0; x < Wr; ++x) {
+      uint64_t sum[3] = {0, 0, 0};
+      for (uint32_t dy = 0; dy < reduce; ++dy)
+        for (uint32_t dx = 0; dx < reduce; ++dx) {
+          const uint64_t sx = (uint64_t)x * reduce + dx, sy = (uint64_t)y * reduce + dy;
+          const uint8_t* px = src + (sy * W + sx) * channels;
+          for (uint32_t c = 0; c < channels; ++c) sum[c] += px[c];
+        }
+      uint64_t mean[3];
+      for (uint32_t c = 0; c < channels; ++c) mean[c] = (sum[c] + area / 2) / area;
+      gray[(size_t)y * Wr + x] =
+          channels == 1 ? (int64_t)mean[0]
+                        : (int64_t)((77 * mean[0] + 150 * mean[1] + 29 * mean[2] + 128) >> 8);
+    }
+  }
+  // 3. binomial weights: row B-1 of Pascal's triangle, built by additions
+  std::vector<int64_t> w(1, 1);
+  for (uint32_t n = 1; n < block; ++n) {
+    std::vector<int64_t> next(n + 1);
+    for (uint32_t i = 0; i <= n; ++i)
+      next[i] = (i > 0 ? w[i - 1] : 0) + (i < n ? w[i] : 0);
+    w = next;
+  }
+  const int64_t half = (int64_t)(block / 2);
+  const uint32_t shift = 2 * (block - 1);
+  for (uint32_t y = 0; y < Hr; ++y) {
+    for (uint32_t x = 0; x < Wr; ++x) {
+      int64_t acc = 0;
+      for (int64_t dy = -half; dy <= half; ++dy) {
+        int64_t yy = (int64_t)y + dy;
+        yy = yy < 0 ? 0 : (yy >= (int64_t)Hr ? (int64_t)Hr - 1 : yy);
+        for (int64_t dx = -half; dx <= half; ++dx) {
+          int64_t xx = (int64_t)x + dx;
+          xx = xx < 0 ? 0 : (xx >= (int64_t)Wr ? (int64_t)Wr - 1 : xx);
+          acc += w[(size_t)(dy + half)] * w[(size_t)(dx + half)] * gray[(size_t)yy * Wr + xx];
+        }
+      }
+      const int64_t mean = (acc + ((int64_t)1 << (shift - 1))) >> shift;
+      out_bits[(size_t)y * Wr + x] = (uint8_t)(gray[(size_t)y * Wr + x] > mean - offset);
+    }
+  }
+  return 0;
+}
+
 }  // extern "C"

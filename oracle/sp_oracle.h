@@ -107,6 +107,26 @@ int orc_run(const orc_params* p, const uint32_t* idx, float* perm, const float* 
  * the column's activity this frame (fp32, each step rounded). */
 int orc_duty_update(uint32_t C, float* duty, const uint8_t* active, float period);
 
+/* Frame encoder (Section 2, and "Adaptive Video Encoder" in Section 3.1):
+ * a colour frame becomes a binary image in three steps.
+ *   1. Reduction by an integer factor f (optional, f = 1 keeps the size):
+ *      the output is floor(W/f) x floor(H/f); each channel of an output pixel
+ *      is the mean of its f x f source block, rounded half up:
+ *      (sum + f*f/2) / (f*f).
+ *   2. Grayscale: g = (77 R + 150 G + 29 B + 128) >> 8 (8-bit fixed-point
+ *      luma weights summing to 256); a one-channel source is its own gray.
+ *   3. Adaptive Gaussian threshold over a B x B window (B odd, 3..13): the
+ *      Gaussian weights are the binomial coefficients w_i = C(B-1, i), the
+ *      window weight of (dx, dy) is w_dx w_dy, coordinates outside the image
+ *      take the nearest edge pixel; the local mean is
+ *      m = (sum + 2^(2B-3)) >> (2B-2) (the weighted sum divided by the total
+ *      weight 4^(B-1), rounded half up), and the bit is g > m - offset.
+ * src is [H][W][channels] bytes (channels 1 or 3, R, G, B order); out_bits
+ * receives floor(H/f) * floor(W/f) bytes (0/1), row-major.  Every step is
+ * integer arithmetic, so the result is exact. */
+int orc_encode(const uint8_t* src, uint32_t W, uint32_t H, uint32_t channels, uint32_t reduce,
+               uint32_t block, int32_t offset, uint8_t* out_bits);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,15 @@ def frame_blobbed(seed, W, H, p_lo=0.05, p_hi=0.20, return_p=False):
     return (out, p.value) if return_p else out
 
 
+def frame_rgb(seed, W, H):
+    """Colour frame [H, W, 3] uint8 (R, G, B): blobs under an illumination ramp."""
+    out = np.empty((H, W, 3), np.uint8)
+    scratch = np.empty(2 * W * H, np.uint8)
+    _ok(lib().synth_frame_rgb(ct.c_uint64(seed), ct.c_uint32(W), ct.c_uint32(H),
+                              _p(out, ct.c_uint8), _p(scratch, ct.c_uint8)), "frame_rgb")
+    return out
+
+
 def pack_bits(bits):
     bits = np.ascontiguousarray(bits, dtype=np.uint8).ravel()
     out = np.empty((bits.size + 31) // 32, np.uint32)

@@ -182,6 +182,53 @@ int synth_frame_blobbed(uint64_t seed, uint32_t W, uint32_t H, double p_lo, doub
   return 0;
 }
 
+int synth_frame_rgb(uint64_t seed, uint32_t W, uint32_t H, uint8_t* out_rgb, uint8_t* scratch) {
+  if (!out_rgb || !scratch || W == 0 || H == 0) return -1;
+  const uint64_t N = (uint64_t)W * H;
+  uint64_t st = seed;
+  double u0 = (double)(synth_splitmix64(&st) >> 11) * (1.0 / 9007199254740992.0);
+  double p = 0.05 + 0.15 * u0;
+  uint32_t gain[3];
+  for (int c = 0; c < 3; ++c) gain[c] = 96u + (uint32_t)(synth_splitmix64(&st) % 160u);
+  const uint32_t dir = (uint32_t)(synth_splitmix64(&st) & 3u);
+  uint8_t* noise = scratch;
+  uint8_t* hsum = scratch + N;
+  for (uint64_t i = 0; i < N; ++i) {
+    double u = (double)(synth_splitmix64(&st) >> 11) * (1.0 / 9007199254740992.0);
+    noise[i] = (uint8_t)(u < p);
+  }
+  for (uint32_t y = 0; y < H; ++y) {
+    const uint8_t* row = noise + (uint64_t)y * W;
+    for (uint32_t x = 0; x < W; ++x) {
+      uint32_t xa = x >= 3 ? x - 3 : 0;
+      uint32_t xb = x + 3 < W ? x + 3 : W - 1;
+      uint32_t v = 0;
+      for (uint32_t xx = xa; xx <= xb; ++xx) v += row[xx];
+      hsum[(uint64_t)y * W + x] = (uint8_t)v;
+    }
+  }
+  const uint32_t span = W + H > 2u ? W + H - 2u : 1u;
+  for (uint32_t y = 0; y < H; ++y) {
+    uint32_t ya = y >= 3 ? y - 3 : 0;
+    uint32_t yb = y + 3 < H ? y + 3 : H - 1;
+    for (uint32_t x = 0; x < W; ++x) {
+      uint32_t v = 0;
+      for (uint32_t yy = ya; yy <= yb; ++yy) v += hsum[(uint64_t)yy * W + x];
+      const uint32_t field = (v * 255u + 24u) / 49u;
+      const uint32_t xs = (dir & 1u) ? W - 1u - x : x;
+      const uint32_t ys = (dir & 2u) ? H - 1u - y : y;
+      const uint32_t light = 64u + (191u * (xs + ys)) / span;
+      uint8_t* px = out_rgb + ((uint64_t)y * W + x) * 3u;
+      for (int c = 0; c < 3; ++c) {
+        uint32_t lit = (field * gain[c] + 32u) / 64u;
+        if (lit > 255u) lit = 255u;
+        px[c] = (uint8_t)((lit * light + 127u) / 255u);
+      }
+    }
+  }
+  return 0;
+}
+
 int synth_pack_bits(const uint8_t* bits, uint64_t n, uint32_t* out_words) {
   if (!bits || !out_words || n == 0) return -1;
   uint64_t nw = (n + 31) / 32;
