@@ -50,6 +50,9 @@ WORKLOAD = ("paper-scale frame SP x 256 independent instances: 960x540 blobbed f
 METRIC = "SP frames/s (1024 col x 256 syn, 960x540 input, learning on)"
 
 
+ALU_TOPS = 152 * 128 * 2.07e9 / 1e12  # int32 lane operations per second, in T
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,6 +63,7 @@ def parse():
     ap.add_argument("--seq-frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core run")
+    ap.add_argument("--no-encoder", action="store_true", help="skip the frame-encoder runs")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="open-loop serving run (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -347,6 +351,83 @@ def run_dense_tc(spg, torch, dev, stream, members=16, frames=256, steps=5):
                        "peak_kind": kind}}
 
 
+def run_encoder(spg, torch, dev, stream, n_frames=128, steps=5, reduce=1):
+    """Frame encoder over n_frames 960x540 colour frames in one call (inputs
+    larger than L2), then the encoder feeding one frame-shaped SP (learning
+    on) from device frames and from pinned host frames."""
+    from paper_1608_01966_gb300 import synth, workloads as wl
+    uniq = wl.rgb_frames(16, 960, 540, seed=wl.BASE_SEED + 6)
+    frames = np.ascontiguousarray(uniq[np.arange(n_frames) % 16].reshape(n_frames, -1))
+    e = spg.sp_encoder_create(spg.sp_encoder_config_init(reduce=reduce))
+    info = spg.sp_encoder_get_info(e)
+    fb, words = info["src_bytes"], info["out_words"]
+    d_src = torch.from_numpy(frames).to(dev)
+    d_bits = torch.zeros((n_frames, words), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        spg.sp_encode_device(e, d_src, n_frames, fb, d_bits, words, stream)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(steps):
+        spg.sp_encode_device(e, d_src, n_frames, fb, d_bits, words, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms_enc = s0.elapsed_time(s1) / steps
+    out = {"workload": f"{n_frames} colour frames 960x540 (RGB, 1.56 MB each) per call, "
+                       f"reduce {reduce} -> {info['out_w']}x{info['out_h']}, 11x11 binomial "
+                       "window, offset 2",
+           "frames_per_s": n_frames / (ms_enc / 1000.0), "us_per_frame": ms_enc * 1000.0 / n_frames}
+    peak, kind = read_peaks()
+    gbs = n_frames * (fb + words * 4) / (ms_enc / 1000.0) / 1e9
+    # integer operations per output pixel: block sums (3 per source pixel),
+    # luma (3), two 11-tap binomial passes (22), rounding and compare (3)
+    ops_px = 3 * reduce * reduce + 3 + 22 + 3
+    tops = n_frames * info["out_bits"] * ops_px / (ms_enc / 1000.0) / 1e12
+    t_hbm = (fb + words * 4) / (peak * 1e9)
+    t_alu = info["out_bits"] * ops_px / (ALU_TOPS * 1e12)
+    if t_alu > t_hbm:
+        out["roofline"] = {"bound": "alu", "kernel": "sp_encode_kernel", "achieved": tops,
+                           "peak": ALU_TOPS, "unit": "Tops/s", "frac": tops / ALU_TOPS,
+                           "peak_kind": "derived: 152 SMs x 128 int32 lanes x 2.07 GHz",
+                           "int_ops_per_output_pixel": ops_px, "hbm_gbs": gbs}
+    else:
+        out["roofline"] = {"bound": "hbm", "kernel": "sp_encode_kernel", "achieved": gbs,
+                           "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
+                           "algorithmic_bytes_per_frame": int(fb + words * 4)}
+    if reduce == 1:
+        case = wl.frame_case()
+        h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+        mw = spg.sp_get_info(h)["mask_words"]
+        d_masks = torch.zeros((n_frames, mw), dtype=torch.int32, device=dev)
+        for _ in range(2):
+            spg.sp_encode_compute_device(e, h, d_src, n_frames, fb, True, d_masks, stream)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(steps):
+            spg.sp_encode_compute_device(e, h, d_src, n_frames, fb, True, d_masks, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / steps
+        out["with_sp"] = {"frames_per_s": n_frames / (ms / 1000.0),
+                          "us_per_frame": ms * 1000.0 / n_frames,
+                          "workload": "encoder + one paper-scale frame SP (1024 x 256, k 40, "
+                                      "learning) on device frames"}
+        pinned = torch.from_numpy(frames).pin_memory().numpy()
+        masks = np.zeros((n_frames, mw), np.uint32)
+        spg.sp_encode_compute(e, h, pinned, True, masks)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            spg.sp_encode_compute(e, h, pinned, True, masks)
+        dt = (time.perf_counter() - t0) / steps
+        out["with_sp"]["e2e"] = {"frames_per_s": n_frames / dt, "h2d_bytes_per_frame": int(fb),
+                                 "d2h_bytes_per_frame": int(mw * 4),
+                                 "note": "pinned host colour frames in, active-column masks out"}
+        spg.sp_destroy(h)
+    spg.sp_encoder_destroy(e)
+    del d_src, d_bits
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -448,6 +529,11 @@ def main():
     if not args.no_dense:
         dense_tc = run_dense_tc(spg, torch, dev, stream)
 
+    encoder = None
+    if not args.no_encoder:
+        encoder = [run_encoder(spg, torch, dev, stream, reduce=1),
+                   run_encoder(spg, torch, dev, stream, reduce=4)]
+
     serve = None
     if args.serve_seconds > 0 and rank == 0:
         from paper_1608_01966_gb300 import serve_sim
@@ -491,6 +577,7 @@ def main():
             "clocks": clk,
             "single_sp": single,
             "dense_tc": dense_tc,
+            "encoder": encoder,
             "serve": serve,
             "cpu_baseline": cpu,
         }

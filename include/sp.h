@@ -388,6 +388,81 @@ SP_API sp_status sp_server_get_permanences(sp_server* s, uint32_t stream_id, flo
 /* Counters and latency percentiles; reset != 0 restarts the latency window. */
 SP_API sp_status sp_server_get_stats(sp_server* s, sp_server_stats* out, int reset);
 
+/* ---- Frame encoder (Section 2; "Adaptive Video Encoder", Section 3.1) -----
+ *
+ * Turns colour (or gray) 8-bit frames into the SP's packed binary input on
+ * the GPU, so raw frames rather than bits cross the host link:
+ *   1. reduction by an integer factor f: the output is floor(src_w / f) x
+ *      floor(src_h / f) pixels, each channel the mean of its f x f source
+ *      block rounded half up, (sum + f*f/2) / (f*f);
+ *   2. grayscale: g = (77 R + 150 G + 29 B + 128) >> 8 (one-channel frames
+ *      are their own gray);
+ *   3. adaptive Gaussian threshold (the paper uses OpenCV's
+ *      ADAPTIVE_THRESH_GAUSSIAN_C; this is its exact integer form): over a
+ *      block x block window with binomial weights C(block-1, i) per axis and
+ *      edge pixels replicated outside the image, the local mean is the
+ *      weighted sum divided by 4^(block-1), rounded half up; the bit of a
+ *      pixel is g > mean - offset;
+ *   4. packing: output pixel p = y * out_w + x is bit p & 31 of word p >> 5
+ *      (LSB first); the unused high bits of the last word are zero.
+ * All of it is integer arithmetic, so results are exact.
+ *
+ * Source frames are [src_h][src_w][channels] bytes, row-major, channels 1 or
+ * 3 (R, G, B interleaved). */
+typedef struct {
+  uint32_t src_w, src_h;  /* source frame size in pixels (1..65535) */
+  uint32_t channels;      /* 1 or 3 */
+  uint32_t reduce;        /* f, 1..8; the output must be at least 1 x 1 */
+  uint32_t block;         /* window size: odd, 3..13 */
+  int32_t offset;         /* subtracted from the local mean */
+  uint32_t reserved[2];   /* zero */
+} sp_encoder_config;
+
+typedef struct {
+  uint32_t out_w, out_h;  /* floor(src / reduce) */
+  uint64_t out_bits;      /* out_w * out_h: the SP's input_w * input_h */
+  uint32_t out_words;     /* ceil(out_bits / 32) words per encoded frame */
+  uint64_t src_bytes;     /* src_w * src_h * channels bytes per source frame */
+} sp_encoder_info;
+
+typedef struct sp_encoder sp_encoder;
+
+/* Defaults: 960 x 540 RGB, reduce 1, block 11, offset 2. */
+SP_API sp_status sp_encoder_config_init(sp_encoder_config* cfg);
+
+/* Validates cfg and creates an encoder on the current device (it owns a
+ * stream and, once used, staging buffers).  SP_EINVAL for an invalid cfg. */
+SP_API sp_status sp_encoder_create(const sp_encoder_config* cfg, sp_encoder** out);
+SP_API void sp_encoder_destroy(sp_encoder* e);  /* NULL-safe; waits for its work */
+SP_API sp_status sp_encoder_get_info(const sp_encoder* e, sp_encoder_info* out);
+
+/* Encodes n_frames device frames (frame t at d_src + t * src_stride bytes,
+ * src_stride >= src_bytes) into d_bits (frame t at d_bits + t * bits_stride
+ * words, bits_stride >= out_words, 4-byte aligned).  Asynchronous on
+ * `stream` (a cudaStream_t; NULL = the encoder's own stream, cudaStreamLegacy
+ * = the legacy default stream).  SP_EINVAL on NULL or
+ * misaligned pointers or short strides (nothing enqueued). */
+SP_API sp_status sp_encode_device(sp_encoder* e, const uint8_t* d_src, uint32_t n_frames,
+                                  uint64_t src_stride, uint32_t* d_bits, uint64_t bits_stride,
+                                  void* stream);
+
+/* Encoder then SP, frame by frame in order, as sp_compute_frames_device
+ * would on the encoded bits (learning, masks and the handle's state
+ * included): d_active_masks (nullable) receives ceil(C / 32) words per frame.
+ * The SP's input must be out_w x out_h bits (SP_EINVAL otherwise).  The
+ * encoded bits go through the encoder's own device buffer (up to 32 frames
+ * at a time).  Asynchronous on `stream`. */
+SP_API sp_status sp_encode_compute_device(sp_encoder* e, sp_handle* h, const uint8_t* d_src,
+                                          uint32_t n_frames, uint64_t src_stride, int learn,
+                                          uint32_t* d_active_masks, void* stream);
+
+/* The same from host frames (n_frames x src_bytes contiguous; pinned memory
+ * lets the copies overlap the kernels): copies in, encoding, SP and the copy
+ * out of h_active_masks (nullable; ceil(C / 32) words per frame) are
+ * pipelined in chunks; returns after all of it finished (bounded wait). */
+SP_API sp_status sp_encode_compute(sp_encoder* e, sp_handle* h, const uint8_t* h_src,
+                                   uint32_t n_frames, int learn, uint32_t* h_active_masks);
+
 /* ---- Allocation-free frame (no counterpart in the paper) ------------------
  *
  * sp_step_noalloc runs one frame -- overlap, inhibition and, if learn != 0,

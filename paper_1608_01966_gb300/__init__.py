@@ -14,4 +14,6 @@ from ._binding import (  # noqa: F401
     sp_server_close_stream, sp_server_create, sp_server_destroy, sp_server_get_permanences,
     sp_server_get_stats, sp_server_open_stream, sp_server_poll, sp_server_submit,
     sp_step_noalloc, sp_sync,
+    SpEncoderConfig, sp_encode_compute, sp_encode_compute_device, sp_encode_device,
+    sp_encoder_config_init, sp_encoder_create, sp_encoder_destroy, sp_encoder_get_info,
 )

@@ -75,6 +75,21 @@ class SpInfo(ct.Structure):
     ]
 
 
+class SpEncoderConfig(ct.Structure):
+    _fields_ = [
+        ("src_w", ct.c_uint32), ("src_h", ct.c_uint32), ("channels", ct.c_uint32),
+        ("reduce", ct.c_uint32), ("block", ct.c_uint32), ("offset", ct.c_int32),
+        ("reserved", ct.c_uint32 * 2),
+    ]
+
+
+class SpEncoderInfo(ct.Structure):
+    _fields_ = [
+        ("out_w", ct.c_uint32), ("out_h", ct.c_uint32), ("out_bits", ct.c_uint64),
+        ("out_words", ct.c_uint32), ("src_bytes", ct.c_uint64),
+    ]
+
+
 _lib = None
 _u32p = ct.POINTER(ct.c_uint32)
 _f32p = ct.POINTER(ct.c_float)
@@ -138,6 +153,16 @@ def lib():
                                      ct.c_uint32, _u32p, ct.c_uint32]
         L.sp_server_get_permanences.argtypes = [vp, ct.c_uint32, _f32p]
         L.sp_server_get_stats.argtypes = [vp, ct.POINTER(SpServerStats), ct.c_int]
+        L.sp_encoder_config_init.argtypes = [ct.POINTER(SpEncoderConfig)]
+        L.sp_encoder_create.argtypes = [ct.POINTER(SpEncoderConfig), ct.POINTER(vp)]
+        L.sp_encoder_destroy.argtypes = [vp]
+        L.sp_encoder_destroy.restype = None
+        L.sp_encoder_get_info.argtypes = [vp, ct.POINTER(SpEncoderInfo)]
+        L.sp_encode_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
+        L.sp_encode_compute_device.argtypes = [vp, vp, vp, ct.c_uint32, ct.c_uint64, ct.c_int,
+                                               vp, vp]
+        L.sp_encode_compute.argtypes = [vp, vp, ct.POINTER(ct.c_uint8), ct.c_uint32, ct.c_int,
+                                        _u32p]
         _lib = L
     return _lib
 
@@ -488,3 +513,58 @@ class SpatialPooler:
             self.close()
         except Exception:
             pass
+
+
+# ---- frame encoder ----------------------------------------------------------
+
+def sp_encoder_config_init(**kw):
+    cfg = SpEncoderConfig()
+    _check(lib().sp_encoder_config_init(ct.byref(cfg)), "sp_encoder_config_init")
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def sp_encoder_create(cfg):
+    e = ct.c_void_p()
+    _check(lib().sp_encoder_create(ct.byref(cfg), ct.byref(e)), "sp_encoder_create")
+    return e
+
+
+def sp_encoder_destroy(e):
+    lib().sp_encoder_destroy(e)
+
+
+def sp_encoder_get_info(e):
+    info = SpEncoderInfo()
+    _check(lib().sp_encoder_get_info(e, ct.byref(info)), "sp_encoder_get_info")
+    return {f: getattr(info, f) for f, _ in SpEncoderInfo._fields_}
+
+
+def sp_encode_device(e, d_src, n_frames, src_stride, d_bits, bits_stride, stream=None):
+    _check(lib().sp_encode_device(e, _addr(d_src), n_frames, src_stride, _addr(d_bits),
+                                  bits_stride, _stream(stream)), "sp_encode_device")
+
+
+def sp_encode_compute_device(e, h, d_src, n_frames, src_stride, learn, d_active_masks=None,
+                             stream=None):
+    _check(lib().sp_encode_compute_device(e, h, _addr(d_src), n_frames, src_stride,
+                                          1 if learn else 0, _addr(d_active_masks),
+                                          _stream(stream)), "sp_encode_compute_device")
+
+
+def sp_encode_compute(e, h, frames, learn, masks_out=None):
+    """frames: uint8 [n, H, W(, 3)] host array, C-contiguous (pinned memory
+    overlaps the copies); masks_out: uint32 [n][mask_words] or None."""
+    if frames.dtype != np.uint8 or not frames.flags.c_contiguous:
+        raise ValueError("frames must be a C-contiguous uint8 array")
+    pm = None
+    if masks_out is not None:
+        if masks_out.dtype != np.uint32 or not masks_out.flags.c_contiguous:
+            raise ValueError("masks_out must be a C-contiguous uint32 array")
+        pm = masks_out.ctypes.data_as(_u32p)
+    _check(lib().sp_encode_compute(e, h, frames.ctypes.data_as(ct.POINTER(ct.c_uint8)),
+                                   frames.shape[0], 1 if learn else 0, pm), "sp_encode_compute")
+    return masks_out

@@ -10,7 +10,9 @@ module): no SP arithmetic.  Recipes follow the five workloads of the build:
             min_overlap 4, k 40 global, inc 0.05 / dec 0.02;
   sweep     the frame input with columns {256,1024,4096} (square grids) x
             synapses {16,64,256} x min_overlap {2,4,8} x k {8,32,128} x
-            global / 9x9 local inhibition.
+            global / 9x9 local inhibition;
+  video     960x540 colour frames (blobs under an illumination ramp) for
+            the frame encoder, whose output feeds a frame-shaped SP.
 """
 import dataclasses
 
@@ -88,6 +90,12 @@ def frame_case(seed=BASE_SEED + 2):
 
 def blob_frames(n, W=960, H=540, seed=BASE_SEED + 2, start=0):
     return np.stack([synth.frame_blobbed(synth.derive_seed(seed, synth.PURPOSE_FRAME, t), W, H)
+                     for t in range(start, start + n)])
+
+
+def rgb_frames(n, W=960, H=540, seed=BASE_SEED + 6, start=0):
+    """Colour frames uint8 [n, H, W, 3] (R, G, B)."""
+    return np.stack([synth.frame_rgb(synth.derive_seed(seed, synth.PURPOSE_FRAME, t), W, H)
                      for t in range(start, start + n)])
 
 

@@ -91,10 +91,30 @@ def test_create_from_state_rejects_bad_state_on_host():
         spg.sp_create_from_state(cfg, idx, perm, np.array([1.0, -1.0], np.float32))
 
 
+def test_encoder_defaults():
+    cfg = spg.sp_encoder_config_init()
+    assert (cfg.src_w, cfg.src_h, cfg.channels, cfg.reduce, cfg.block, cfg.offset) == \
+        (960, 540, 3, 1, 11, 2)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(block=4), dict(block=1), dict(block=15), dict(channels=2), dict(reduce=0),
+    dict(reduce=9), dict(src_w=0), dict(src_h=70000), dict(src_w=7, reduce=8),
+    dict(src_w=65535, src_h=65535),                # 2^32 output bits
+    dict(src_w=20000, src_h=4),                    # too wide for one CTA's rows
+])
+def test_encoder_rejects_bad_config_on_host(bad):
+    cfg = spg.sp_encoder_config_init(**bad)
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_encoder_create(cfg)
+    assert e.value.status == 1  # SP_EINVAL, raised before any CUDA call
+
+
 def test_status_strings_and_null_safety():
     assert spg.sp_status_str(0) == "ok"
     assert spg.sp_status_str(4) == "timed out"
     spg.sp_destroy(None)  # NULL-safe
+    spg.sp_encoder_destroy(None)
     assert spg.sp_kernel_launch_count() >= 0
 
 
