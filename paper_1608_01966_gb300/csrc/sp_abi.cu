@@ -120,6 +120,7 @@ void free_handle(sp_handle* h) {
   if (h->d_run_ov) cudaFree(h->d_run_ov);
   if (h->d_run_masks) cudaFree(h->d_run_masks);
   if (h->d_conn) cudaFree(h->d_conn);
+  if (h->d_xspan) cudaFree(h->d_xspan);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -578,7 +579,33 @@ sp_status handle_wait(sp_handle* h) { return wait_handle(h); }
 sp_status handle_flush_learning(sp_handle* h) { return flush_learning(h); }
 
 // The descriptor of one SP inside a multi-SP launch.
-void fill_desc(const sp_handle* h, sp::BatchDesc* d) {
+// The input-word span of each of the handle's batch CTAs (computed once per
+// CTA split, since pools never change); nullptr if it cannot be had, which
+// only turns the staging of input words off.
+const uint32_t* handle_xspan(sp_handle* h, uint32_t n_ctas) {
+  if (h->d_xspan && h->xspan_ctas == n_ctas) return h->d_xspan;
+  if (h->d_xspan) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_xspan);
+    h->d_xspan = nullptr;
+    h->xspan_ctas = 0;
+  }
+  DeviceGuard g(h->device);
+  if (device_malloc((void**)&h->d_xspan, (size_t)n_ctas * 8) != cudaSuccess) {
+    h->d_xspan = nullptr;
+    return nullptr;
+  }
+  if (sp::launch_xspan(h->d_idx, h->C, h->S, n_ctas, h->d_xspan, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaFree(h->d_xspan);
+    h->d_xspan = nullptr;
+    return nullptr;
+  }
+  h->xspan_ctas = n_ctas;
+  return h->d_xspan;
+}
+
+void fill_desc(sp_handle* h, sp::BatchDesc* d) {
   *d = sp::BatchDesc{};
   d->idx = h->d_idx;
   d->perm = h->d_perm;
@@ -607,6 +634,7 @@ void fill_desc(const sp_handle* h, sp::BatchDesc* d) {
   d->gh = h->cfg.col_grid_h;
   d->radius = h->cfg.local_radius;
   d->n_ctas = batch_ctas(h->C, h->S);
+  d->xspan = handle_xspan(h, d->n_ctas);
 }
 
 }  // namespace rt
@@ -1010,6 +1038,7 @@ struct sp_batch {
   uint32_t* d_cta_inst = nullptr;
   uint32_t n_ctas = 0, max_C = 0;
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
+  uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
   uint32_t* d_err = nullptr;
   uint64_t frame_words = 0, mask_words = 0;
@@ -1054,6 +1083,20 @@ uint32_t batch_ctas(uint32_t C, uint32_t S) {
 // on 256 SPs of 1024x256 the staged form measured 0.29-0.47 of HBM peak
 // against 0.63 for the streamed one, since a CTA waits for all of its state
 // before its first gather and fewer CTAs fit on an SM.
+// Shared memory a batch launch offers each CTA for the input words its
+// columns index, copied in once so the bit gathers read shared memory.  Off
+// unless SP_BATCH_XSPAN_KB (1..48) allows it: on 256 SPs of 1024x256 it
+// measured 0.53-0.61 of HBM peak against 0.63 without, the copy adding two
+// dependent memory latencies to every CTA's start.
+uint32_t batch_xspan_cap() {
+  uint32_t kb = 0u;
+  if (const char* e = std::getenv("SP_BATCH_XSPAN_KB")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 0 && v <= 48) kb = (uint32_t)v;
+  }
+  return kb << 10;
+}
+
 uint32_t batch_stage_cap(uint32_t need) {
   uint32_t limit = 0u;
   if (const char* e = std::getenv("SP_BATCH_STAGE_KB")) {
@@ -1151,6 +1194,7 @@ sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, ui
     a.learn = learn ? 1u : 0u;
     a.save = (t + 1 == n) ? 1u : 0u;
     a.stage_cap = b->stage_cap;
+    a.xspan_cap = b->xspan_cap;
     a.err = b->d_err;
     SP_CUDA(sp::launch_batch_step(a, b->n_ctas, b->max_C, st));
     b->pending = learn != 0;
@@ -1259,6 +1303,7 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
     b->stage_cap = std::max(b->stage_cap, sp::batch_stage_bytes(h->C, h->S, d.n_ctas));
   }
   b->stage_cap = batch_stage_cap(b->stage_cap);
+  b->xspan_cap = batch_xspan_cap();
   b->frame_words = foff;
   b->mask_words = moff;
   b->n_ctas = (uint32_t)cta_inst.size();

@@ -67,7 +67,8 @@ sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
 uint32_t batch_ctas(uint32_t C, uint32_t S);
 uint32_t batch_stage_cap(uint32_t need);
-void fill_desc(const sp_handle* h, sp::BatchDesc* d);
+void fill_desc(sp_handle* h, sp::BatchDesc* d);
+uint32_t batch_xspan_cap();
 
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
 constexpr int kSlots = 2;
@@ -158,6 +159,8 @@ struct sp_handle {
   float* d_run_ov = nullptr;        // [run_cap][C] overlaps of a run
   uint32_t* d_run_masks = nullptr;  // [run_cap][mask_words]
   uint32_t run_cap = 0;
+  uint32_t* d_xspan = nullptr;      // [2][xspan_ctas] input-word span of each batch CTA
+  uint32_t xspan_ctas = 0;
   uint32_t* d_conn = nullptr;       // [C][conn_words] connected bits of a dense run
   uint32_t conn_words = 0;
   bool unit_boost = true;

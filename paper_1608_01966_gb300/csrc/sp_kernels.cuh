@@ -35,6 +35,7 @@ struct StepArgs {
   uint32_t* result_copy;     // optional second copy of result[0..n] (serving), or nullptr
   float* duty;               // [C] active-duty cycles updated each frame, or nullptr
   float duty_period;
+  const uint32_t* xspan;     // per CTA: [lo, hi) input words its columns read, or nullptr
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k;
@@ -54,6 +55,7 @@ struct BatchDesc {
   uint32_t* hist;       // nullptr unless global inhibition with unit boosts
   float* duty;          // nullptr unless duty cycles are tracked
   float duty_period;
+  const uint32_t* xspan;  // per CTA of this SP: [lo, hi) input words read (nullable)
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
   uint32_t C, S, n_words, mask_words;
@@ -87,12 +89,20 @@ struct BatchArgs {
                                 // uniform fields above are then ignored
   uint32_t* results_out;        // with tick: per-SP [count, ascending list]
   uint32_t stage_cap;           // bytes of dynamic shared memory for staging state (0: none)
+  uint32_t xspan_cap;           // bytes of shared memory for a CTA's input span (0: none)
   uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
 };
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream);
-// Shared memory a batch CTA needs to stage its columns' pools and permanences.
+// Per-CTA input-word spans of an SP split into n_ctas blocks of consecutive
+// columns: out[2b], out[2b+1] = lowest and one past the highest input word
+// that block b's pools index (0, 0 for an empty block).
+cudaError_t launch_xspan(const uint32_t* idx, uint32_t C, uint32_t S, uint32_t n_ctas,
+                         uint32_t* out, cudaStream_t stream);
+
+// Shared memory a batch CTA needs for its warps' rings of column slots (pool and
+// permanence rows staged by bulk copy); 0 when the SP cannot be staged.
 uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas);
 
 // Learning of one frame applied on its own (used to flush pending learning).

@@ -184,6 +184,7 @@ sp_status start_launch(sp_server* s, LaunchSlot& L) {
     stage = std::max(stage, s->streams[m.first].stage_bytes);
   }
   a.stage_cap = batch_stage_cap(stage);
+  a.xspan_cap = batch_xspan_cap();
   a.err = L.d_err;
   SP_CUDA(sp::launch_batch_step(a, ctas, max_C, L.st));
   SP_CUDA(cudaMemcpyAsync(L.h_results, L.d_results, (size_t)count * row * 4,

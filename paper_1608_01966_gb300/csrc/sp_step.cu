@@ -63,6 +63,18 @@ __device__ __forceinline__ uint32_t count4(const float4& p, const uint4& id, flo
          connected_active(p.z, thr, x, id.z) + connected_active(p.w, thr, x, id.w);
 }
 
+// count4 against input words staged in shared memory: xs[w - xlo] holds
+// input word w for every word the column's pool indexes.
+__device__ __forceinline__ uint32_t staged_bit(float p, float thr, const uint32_t* xs,
+                                               uint32_t xlo, uint32_t i) {
+  return (p >= thr) ? (xs[(i >> 5) - xlo] >> (i & 31u)) & 1u : 0u;
+}
+__device__ __forceinline__ uint32_t count4_staged(const float4& p, const uint4& id, float thr,
+                                                  const uint32_t* xs, uint32_t xlo) {
+  return staged_bit(p.x, thr, xs, xlo, id.x) + staged_bit(p.y, thr, xs, xlo, id.y) +
+         staged_bit(p.z, thr, xs, xlo, id.z) + staged_bit(p.w, thr, xs, xlo, id.w);
+}
+
 __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArgs& a) {
   p.x = learn_one(p.x, input_bit(a.x_prev, id.x), a.inc, a.dec);
   p.y = learn_one(p.y, input_bit(a.x_prev, id.y), a.inc, a.dec);
@@ -74,9 +86,10 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
 // the previous frame's learning is applied first and written back.  With
 // VEC = 4 every lane loads two 16-byte vectors of indices and permanences
 // before its first bit gather, so all of a column's state is in flight at once.
-template <int VEC, bool STREAM>
+template <int VEC, bool STREAM, bool SX = false>
 __device__ __forceinline__ uint32_t column_overlap(const StepArgs& a, uint32_t c, bool learn_now,
-                                                   int lane) {
+                                                   int lane, const uint32_t* xs = nullptr,
+                                                   uint32_t xlo = 0u) {
   const uint64_t base = (uint64_t)c * a.S;
   uint32_t cnt = 0;
   if (VEC == 4) {
@@ -102,8 +115,13 @@ __device__ __forceinline__ uint32_t column_overlap(const StepArgs& a, uint32_t c
           p4[jb] = pb;
         }
       }
-      if (va) cnt += count4(pa, ida, a.thr, a.x);
-      if (vb) cnt += count4(pb, idb, a.thr, a.x);
+      if (SX) {
+        if (va) cnt += count4_staged(pa, ida, a.thr, xs, xlo);
+        if (vb) cnt += count4_staged(pb, idb, a.thr, xs, xlo);
+      } else {
+        if (va) cnt += count4(pa, ida, a.thr, a.x);
+        if (vb) cnt += count4(pb, idb, a.thr, a.x);
+      }
     }
   } else {
     for (uint32_t s = lane; s < a.S; s += 32) {
@@ -237,10 +255,20 @@ __device__ __forceinline__ void column_overlap_pair(const StepArgs& a, uint32_t 
 #define SP_PAIR_COLUMNS 0
 #endif
 
-constexpr uint32_t kStageWaitLimit = 1u << 26;  // mbarrier polls before giving up
+#ifndef SP_STAGE_RING
+#define SP_STAGE_RING 3
+#endif
+constexpr uint32_t kRing = SP_STAGE_RING;               // column slots per warp
+constexpr unsigned long long kStageWaitNs = 1000000000ull;  // give up after 1 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 // Copy one contiguous block of global memory into shared memory with the
@@ -253,8 +281,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Wait for phase `parity` of mbar to complete; false after kStageWaitNs.
 __device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < kStageWaitLimit; ++i) {
+  unsigned long long t0 = 0;
+  for (uint32_t i = 0;; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -263,31 +293,17 @@ __device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_addr(mbar)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((i & 255u) == 0u) {
+      const unsigned long long t = global_ns();
+      if (i == 0) t0 = t;
+      else if (t - t0 > kStageWaitNs) return false;
+    }
   }
-  return false;
 }
 
-// Raw overlap of column c from its pool and permanences staged in shared
-// memory (rows ri/rp); the learning of the previous frame, if due, updates
-// the staged row and the global row.
-__device__ __forceinline__ uint32_t staged_overlap(const StepArgs& a, uint32_t c,
-                                                   const uint32_t* ri, float* rp, bool learn_now,
-                                                   int lane) {
-  uint32_t cnt = 0;
-  const uint32_t n4 = a.S >> 2;
-  const uint4* id4 = reinterpret_cast<const uint4*>(ri);
-  float4* p4 = reinterpret_cast<float4*>(rp);
-  float4* g4 = reinterpret_cast<float4*>(a.perm + (uint64_t)c * a.S);
-  for (uint32_t j = lane; j < n4; j += 32) {
-    const uint4 id = id4[j];
-    float4 p = p4[j];
-    if (learn_now) {
-      learn4(p, id, a);
-      g4[j] = p;
-    }
-    cnt += count4(p, id, a.thr, a.x);
-  }
-  return __reduce_add_sync(kFull, cnt);
+// Bytes of one warp's ring of column slots (pool row + permanence row each).
+__host__ __device__ __forceinline__ uint32_t stage_ring_bytes(uint32_t S) {
+  return kRing * 2u * S * 4u;
 }
 
 // One frame of one SP, run by nb CTAs of which this is number bid.  With
@@ -296,7 +312,7 @@ __device__ __forceinline__ uint32_t staged_overlap(const StepArgs& a, uint32_t c
 template <int VEC, bool STREAM, bool STAGE = false>
 __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint32_t nb,
                                           uint32_t* dyn_smem, uint32_t stage_cap = 0u,
-                                          uint32_t* err = nullptr) {
+                                          uint32_t* err = nullptr, uint32_t xspan_cap = 0u) {
   __shared__ uint32_t s_ticket;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -304,7 +320,6 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     for (uint32_t i = bid * kStepThreads + threadIdx.x; i < a.n_words; i += nb * kStepThreads)
       a.x_save[i] = __ldg(a.x + i);
   }
-  bool wrote = false;
   uint32_t c_first, c_end, c_step;
   if (SP_CONTIG_COLUMNS) {
     const uint32_t per = (a.C + nb - 1u) / nb;
@@ -320,51 +335,74 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     a.ov[c] = dev::boosted(raw, a.min_overlap, __ldg(a.boost + c));
     // unit boosts: the overlap is the count, histogrammed for the select
     if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
-    wrote = true;
   };
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
-  const uint32_t n_cols = c_end > c_first - warp ? c_end - (c_first - warp) : 0u;
-  const uint32_t stage = n_cols * a.S * 4u;  // bytes of pools (and of permanences)
-  if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && n_cols > 0u && 2u * stage <= stage_cap) {
-    // the CTA's columns are contiguous: two bulk copies bring all their
-    // pools and permanences into shared memory at once
-    __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ uint32_t s_fail;
-    const uint32_t c_lo = c_first - warp;
-    uint32_t* s_idx = dyn_smem;
-    float* s_perm = reinterpret_cast<float*>(dyn_smem + n_cols * a.S);
-    if (threadIdx.x == 0) {
-      s_fail = 0u;
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&s_mbar)) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.S <= 512u &&
+      kStepWarps * stage_ring_bytes(a.S) <= stage_cap) {
+    // Each warp streams its columns' pool and permanence rows through a ring
+    // of kRing shared-memory slots with bulk copies: the copies of the next
+    // columns are in flight while this one is counted.
+    __shared__ __align__(8) uint64_t s_mbar[kStepWarps][kRing];
+    const uint32_t row = a.S * 4u;
+    uint8_t* ring = reinterpret_cast<uint8_t*>(dyn_smem) + warp * stage_ring_bytes(a.S);
+    uint64_t* mb = s_mbar[warp];
+    const uint32_t n_mine = c_first < c_end ? (c_end - c_first + c_step - 1u) / c_step : 0u;
+    auto issue = [&](uint32_t i) {  // lane 0
+      const uint32_t c = c_first + i * c_step;
+      uint8_t* dst = ring + (i % kRing) * 2u * row;
+      uint64_t* bar = mb + (i % kRing);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
-                       smem_addr(&s_mbar)),
-                   "r"(2u * stage)
+                       smem_addr(bar)),
+                   "r"(2u * row)
                    : "memory");
-      bulk_g2s(s_idx, a.idx + (uint64_t)c_lo * a.S, stage, &s_mbar);
-      bulk_g2s(s_perm, a.perm + (uint64_t)c_lo * a.S, stage, &s_mbar);
+      bulk_g2s(dst, a.idx + (uint64_t)c * a.S, row, bar);
+      bulk_g2s(dst + row, a.perm + (uint64_t)c * a.S, row, bar);
+    };
+    if (lane == 0) {
+      for (uint32_t k = 0; k < kRing; ++k)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mb + k))
+                     : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      for (uint32_t i = 0; i < n_mine && i < kRing; ++i) issue(i);
     }
-    if (!stage_wait(&s_mbar, 0u)) s_fail = 1u;
-    __syncthreads();
-    if (s_fail) {
-      stage_wait(&s_mbar, 0u);  // bounded: let the copies land before leaving
-      if (threadIdx.x == 0 && err) atomicExch(err, 1u);
-      for (uint32_t c = c_first; c < c_end; c += c_step)
-        if (lane == 0) publish(c, 0u);
-    } else {
-      for (uint32_t c = c_first; c < c_end; c += c_step) {
-        const uint32_t r = c - c_lo;
-        const uint32_t raw =
-            staged_overlap(a, c, s_idx + r * a.S, s_perm + r * a.S, learning(c), lane);
-        if (lane == 0) publish(c, raw);
+    __syncwarp();
+    uint32_t i = 0;
+    for (; i < n_mine; ++i) {
+      const uint32_t c = c_first + i * c_step;
+      const bool ok = stage_wait(mb + (i % kRing), (i / kRing) & 1u);
+      if (__any_sync(kFull, !ok)) break;
+      const uint8_t* slot = ring + (i % kRing) * 2u * row;
+      const uint4* id4 = reinterpret_cast<const uint4*>(slot);
+      const float4* p4 = reinterpret_cast<const float4*>(slot + row);
+      float4* g4 = reinterpret_cast<float4*>(a.perm + (uint64_t)c * a.S);
+      const bool learn_now = learning(c);
+      uint32_t cnt = 0;
+      for (uint32_t j = lane; j < (a.S >> 2); j += 32) {
+        const uint4 id = id4[j];
+        float4 p = p4[j];
+        if (learn_now) {
+          learn4(p, id, a);
+          g4[j] = p;
+        }
+        cnt += count4(p, id, a.thr, a.x);
       }
+      cnt = __reduce_add_sync(kFull, cnt);
+      if (lane == 0) publish(c, cnt);
+      __syncwarp();  // every lane is done with the slot before it is refilled
+      if (lane == 0 && i + kRing < n_mine) issue(i + kRing);
     }
-    __syncthreads();  // the staging area becomes the last CTA's working memory
+    if (i < n_mine) {
+      // a copy did not complete in time: report it, publish nothing useful,
+      // and wait (bounded) for the copies still in flight before leaving
+      if (lane == 0 && err) atomicExch(err, 1u);
+      for (uint32_t k = i; k < n_mine && k < i + kRing; ++k) stage_wait(mb + (k % kRing), (k / kRing) & 1u);
+      for (uint32_t k = i; k < n_mine; ++k)
+        if (lane == 0) publish(c_first + k * c_step, 0u);
+    }
+    __syncthreads();  // the rings become the last CTA's working memory
   } else if (SP_PAIR_COLUMNS && VEC == 4 && STREAM && a.S <= 256u) {
     for (uint32_t c = c_first; c < c_end; c += 2u * c_step) {
       const uint32_t c1 = c + c_step;
@@ -378,17 +416,44 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
       }
     }
   } else {
-    for (uint32_t c = c_first; c < c_end; c += c_step) {
-      const uint32_t raw = column_overlap<VEC, STREAM>(a, c, learning(c), lane);
-      if (lane == 0) publish(c, raw);
+    uint32_t xlo = 0u, xhi = 0u;
+    if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.xspan) {
+      xlo = __ldg(a.xspan + 2u * bid);
+      xhi = __ldg(a.xspan + 2u * bid + 1u);
+    }
+    if (xhi > xlo && (xhi - xlo) * 4u <= xspan_cap) {
+      // copy the input words this CTA's pools index into shared memory once;
+      // every bit gather of its columns then reads shared memory
+      uint32_t* xs = dyn_smem;
+      const uint32_t n = xhi - xlo;
+      for (uint32_t w = threadIdx.x; w < n; w += kStepThreads) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(xs + w)),
+                     "l"(a.x + xlo + w)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+      for (uint32_t c = c_first; c < c_end; c += c_step) {
+        const uint32_t raw = column_overlap<VEC, STREAM, true>(a, c, learning(c), lane, xs, xlo);
+        if (lane == 0) publish(c, raw);
+      }
+      __syncthreads();  // the span becomes the last CTA's working memory
+    } else {
+      for (uint32_t c = c_first; c < c_end; c += c_step) {
+        const uint32_t raw = column_overlap<VEC, STREAM>(a, c, learning(c), lane);
+        if (lane == 0) publish(c, raw);
+      }
     }
   }
-  // publish this CTA's overlaps (only their writers need the fence; the
-  // other stores are read by the next launch), then take a ticket: the last
-  // CTA runs the inhibition
-  if (wrote) __threadfence();
+  // publish this CTA's overlaps and histogram counts, then take a ticket:
+  // the last CTA runs the inhibition.  The barrier orders every thread's
+  // writes before thread 0's fence, which releases them (cumulatively) ahead
+  // of its ticket; the other stores are read only by the next launch.
   __syncthreads();
-  if (threadIdx.x == 0) s_ticket = atomicAdd(a.counter, 1u);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_ticket = atomicAdd(a.counter, 1u);
+  }
   __syncthreads();
   if (s_ticket != nb - 1u) return;
   __threadfence();
@@ -448,6 +513,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.hist = d.hist;
   a.duty = d.duty;
   a.duty_period = d.duty_period;
+  a.xspan = d.xspan;
   a.C = d.C;
   a.S = d.S;
   a.n_words = d.n_words;
@@ -463,7 +529,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.radius = d.radius;
   const uint32_t bid = blockIdx.x - cta_first;
   if ((a.S & 3u) == 0u)
-    step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, ba.stage_cap, ba.err);
+    step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, ba.stage_cap, ba.err, ba.xspan_cap);
   else
     step_body<1, true>(a, bid, d.n_ctas, dyn_smem);
 }
@@ -498,15 +564,54 @@ cudaError_t kernels_init() {
                               bytes);
 }
 
-uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas) {
-  if (S % 4u) return 0u;
+// Block b of `per` consecutive columns: lowest and one past the highest input
+// word its pools index.
+__global__ void __launch_bounds__(256) sp_xspan_kernel(const uint32_t* idx, uint32_t C,
+                                                       uint32_t S, uint32_t per, uint32_t* out) {
+  __shared__ uint32_t s_lo[8], s_hi[8];
+  const uint32_t c0 = min(C, blockIdx.x * per), c1 = min(C, (blockIdx.x + 1u) * per);
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint64_t e = (uint64_t)c0 * S + threadIdx.x; e < (uint64_t)c1 * S; e += blockDim.x) {
+    const uint32_t w = __ldg(idx + e) >> 5;
+    lo = min(lo, w);
+    hi = max(hi, w + 1u);
+  }
+  lo = __reduce_min_sync(kFull, lo);
+  hi = __reduce_max_sync(kFull, hi);
+  if ((threadIdx.x & 31u) == 0u) {
+    s_lo[threadIdx.x >> 5] = lo;
+    s_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (uint32_t w = 1; w < blockDim.x / 32u; ++w) {
+      lo = min(lo, s_lo[w]);
+      hi = max(hi, s_hi[w]);
+    }
+    out[2u * blockIdx.x] = hi > 0u ? lo : 0u;
+    out[2u * blockIdx.x + 1u] = hi;
+  }
+}
+
+cudaError_t launch_xspan(const uint32_t* idx, uint32_t C, uint32_t S, uint32_t n_ctas,
+                         uint32_t* out, cudaStream_t stream) {
   const uint32_t per = (C + n_ctas - 1u) / n_ctas;
-  return per * S * 8u;
+  sp_xspan_kernel<<<n_ctas, 256, 0, stream>>>(idx, C, S, per, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas) {
+  (void)C;
+  (void)n_ctas;
+  if (S % 4u || S > 512u) return 0u;
+  return kStepWarps * stage_ring_bytes(S);
 }
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream) {
-  const size_t smem = std::max<size_t>(step_smem_bytes(max_C), a.stage_cap);
+  const size_t smem =
+      std::max<size_t>(step_smem_bytes(max_C), std::max(a.stage_cap, a.xspan_cap));
   sp_batch_step_kernel<<<n_ctas, kStepThreads, smem, stream>>>(a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
