@@ -123,6 +123,29 @@ def algorithmic_bytes_per_frame(case, learn=True):
     return b
 
 
+def compact_form(case):
+    """Whether the batch runs this SP on its compact form: 16-bit pool offsets
+    from a per-column base plus one connected bit per synapse (S a multiple
+    of 32 up to 256, every pool spanning at most 65536 inputs)."""
+    if os.environ.get("SP_BATCH_COMPACT", "1").startswith("0"):
+        return False
+    if case.S % 32 or case.S > 256:
+        return False
+    return int((case.idx.max(axis=1) - case.idx.min(axis=1)).max()) <= 0xFFFF
+
+
+def compact_bytes_per_frame(case, learn=True):
+    """Bytes one SP frame moves on the compact form: offsets (2 B) and
+    connected bits (1/8 B) per synapse, a base per column, the frame, the
+    overlaps, the winner list and, when learning, the winners' permanence rows
+    read and written plus their connected bits rewritten."""
+    b = (case.C * case.S * 2 + case.C * case.S // 8 + case.C * 4 + case.n_words * 4
+         + case.C * 4 + case.k * 4)
+    if learn:
+        b += case.k * case.S * 8 + case.k * case.S // 8
+    return b
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -134,7 +157,7 @@ def read_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sp_step.cu", "sp_kernels.cuh", "sp_device.cuh"):
+    for f in ("sp_step.cu", "sp_kernels.cuh", "sp_device.cuh", "sp_abi.cu"):
         with open(os.path.join(ROOT, "paper_1608_01966_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -543,6 +566,9 @@ def main():
     peak, peak_kind = read_peaks()
     per_launch = sum(algorithmic_bytes_per_frame(c) for c in cases)
     achieved = per_launch / (ms / 1000.0) / 1e9  # one batch-step launch per step
+    compact = all(compact_form(c) for c in cases)
+    moved = sum(compact_bytes_per_frame(c) if compact_form(c) else algorithmic_bytes_per_frame(c)
+                for c in cases)
     traffic = read_traffic()
 
     cpu = None
@@ -569,6 +595,11 @@ def main():
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_launch": per_launch,
+                         "form": ("compact: 16-bit pool offsets + connected bits, fp32 "
+                                  "permanences touched only by learning columns") if compact
+                                 else "full: 32-bit pools + fp32 permanences",
+                         "form_bytes_per_launch": moved,
+                         "form_frac": moved / (ms / 1000.0) / 1e9 / peak,
                          "avg_launch_us": ms * 1000.0},
             "e2e": {"value": e2e_value, "unit": "frames/s",
                     "h2d_bytes_per_step": int(info["frame_words"] * 4),

@@ -121,6 +121,7 @@ void free_handle(sp_handle* h) {
   if (h->d_run_masks) cudaFree(h->d_run_masks);
   if (h->d_conn) cudaFree(h->d_conn);
   if (h->d_xspan) cudaFree(h->d_xspan);
+  if (h->d_compact) cudaFree(h->d_compact);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -605,6 +606,39 @@ const uint32_t* handle_xspan(sp_handle* h, uint32_t n_ctas) {
   return h->d_xspan;
 }
 
+// Derive the compact form of the handle's pools and connectivity from its
+// current state (S % 32 == 0, S <= 256, every pool spanning at most 65536
+// inputs); false if the SP does not qualify or the form cannot be had, which
+// leaves batches on the full form.  SP_BATCH_COMPACT=0 turns it off.
+bool handle_compact(sp_handle* h) {
+  if (const char* e = std::getenv("SP_BATCH_COMPACT"))
+    if (e[0] == '0') return false;
+  if (h->S % 32u != 0u || h->S > 256u) return false;
+  DeviceGuard g(h->device);
+  const size_t CS = (size_t)h->C * h->S;
+  const size_t b_cidx = align256(CS * 2), b_base = align256((size_t)h->C * 4),
+               b_conn = align256(CS / 8);
+  if (!h->d_compact) {
+    if (device_malloc(&h->d_compact, b_cidx + b_base + b_conn + 256) != cudaSuccess) {
+      h->d_compact = nullptr;
+      return false;
+    }
+    char* p = static_cast<char*>(h->d_compact);
+    h->d_cidx = reinterpret_cast<uint16_t*>(p);
+    h->d_cbase = reinterpret_cast<uint32_t*>(p + b_cidx);
+    h->d_cconn = reinterpret_cast<uint32_t*>(p + b_cidx + b_base);
+    h->d_cwide = reinterpret_cast<uint32_t*>(p + b_cidx + b_base + b_conn);
+  }
+  uint32_t wide = 1;
+  if (cudaMemsetAsync(h->d_cwide, 0, 4, h->stream) != cudaSuccess ||
+      sp::launch_compact(h->d_idx, h->d_perm, h->C, h->S, h->cfg.connect_threshold, h->d_cidx,
+                         h->d_cbase, h->d_cconn, h->d_cwide, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&wide, h->d_cwide, 4, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return false;
+  return wide == 0;
+}
+
 void fill_desc(sp_handle* h, sp::BatchDesc* d) {
   *d = sp::BatchDesc{};
   d->idx = h->d_idx;
@@ -635,6 +669,11 @@ void fill_desc(sp_handle* h, sp::BatchDesc* d) {
   d->radius = h->cfg.local_radius;
   d->n_ctas = batch_ctas(h->C, h->S);
   d->xspan = handle_xspan(h, d->n_ctas);
+  if (handle_compact(h)) {
+    d->cidx = h->d_cidx;
+    d->cbase = h->d_cbase;
+    d->conn = h->d_cconn;
+  }
 }
 
 }  // namespace rt
@@ -1068,7 +1107,7 @@ namespace rt {
 // so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
 // per-CTA ticket and fence cost small).  SP_BATCH_COLS_PER_WARP overrides.
 uint32_t batch_ctas(uint32_t C, uint32_t S) {
-  uint32_t cpw = S >= 128u ? 4u : (S >= 32u ? 8u : 16u);
+  uint32_t cpw = S >= 128u ? 8u : (S >= 32u ? 8u : 16u);
   if (const char* e = std::getenv("SP_BATCH_COLS_PER_WARP")) {
     const long v = std::strtol(e, nullptr, 10);
     if (v >= 1 && v <= 64) cpw = (uint32_t)v;

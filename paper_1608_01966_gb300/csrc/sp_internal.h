@@ -159,6 +159,11 @@ struct sp_handle {
   float* d_run_ov = nullptr;        // [run_cap][C] overlaps of a run
   uint32_t* d_run_masks = nullptr;  // [run_cap][mask_words]
   uint32_t run_cap = 0;
+  void* d_compact = nullptr;        // batch compact form: cidx | cbase | conn | wide flag
+  uint16_t* d_cidx = nullptr;
+  uint32_t* d_cbase = nullptr;
+  uint32_t* d_cconn = nullptr;
+  uint32_t* d_cwide = nullptr;
   uint32_t* d_xspan = nullptr;      // [2][xspan_ctas] input-word span of each batch CTA
   uint32_t xspan_ctas = 0;
   uint32_t* d_conn = nullptr;       // [C][conn_words] connected bits of a dense run

@@ -36,6 +36,11 @@ struct StepArgs {
   float* duty;               // [C] active-duty cycles updated each frame, or nullptr
   float duty_period;
   const uint32_t* xspan;     // per CTA: [lo, hi) input words its columns read, or nullptr
+  // compact form (batches; nullptr = use idx/perm only), laid out as described
+  // at launch_compact
+  const uint16_t* cidx;
+  const uint32_t* cbase;
+  uint32_t* conn;
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k;
@@ -56,6 +61,9 @@ struct BatchDesc {
   float* duty;          // nullptr unless duty cycles are tracked
   float duty_period;
   const uint32_t* xspan;  // per CTA of this SP: [lo, hi) input words read (nullable)
+  const uint16_t* cidx;   // compact form (nullable), as in StepArgs
+  const uint32_t* cbase;
+  uint32_t* conn;
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
   uint32_t C, S, n_words, mask_words;
@@ -95,6 +103,14 @@ struct BatchArgs {
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream);
+// Compact form of an SP's pools and connectivity (S % 32 == 0, S <= 256):
+// cbase[c] = min_s idx[c][s], cidx[c][s] = idx[c][s] - cbase[c],
+// conn[c][s / 32] bit s % 32 = perm[c][s] >= thr.  *wide is set to 1 if some
+// column's pool spans more than 65536 inputs (the form is unusable then).
+cudaError_t launch_compact(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
+                           float thr, uint16_t* cidx, uint32_t* cbase, uint32_t* conn,
+                           uint32_t* wide, cudaStream_t stream);
+
 // Per-CTA input-word spans of an SP split into n_ctas blocks of consecutive
 // columns: out[2b], out[2b+1] = lowest and one past the highest input word
 // that block b's pools index (0, 0 for an empty block).

@@ -82,6 +82,65 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
   p.w = learn_one(p.w, input_bit(a.x_prev, id.w), a.inc, a.dec);
 }
 
+// ---- compact form: 16-bit pool offsets and connected bits -------------------
+//
+// A lane holds 8 consecutive synapses of a column: one 16-byte vector of
+// offsets and one byte of connected bits, so a warp keeps kCompactCols
+// columns in flight with a few registers each.  A column that learns reads and
+// writes its fp32 permanences and rewrites its connected bits; the others
+// never touch permanences.
+
+#ifndef SP_COMPACT_COLS
+#define SP_COMPACT_COLS 2
+#endif
+constexpr int kCompactCols = SP_COMPACT_COLS;
+
+__device__ __forceinline__ uint32_t off16(const uint4& o, int k) {
+  const uint32_t w = k < 2 ? o.x : (k < 4 ? o.y : (k < 6 ? o.z : o.w));
+  return (k & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+// Apply the pending learning to column c (lane: synapses 8 lane .. 8 lane + 7)
+// and return the lane's new byte of connected bits; writes perm and conn.
+// Rare (winners of the previous frame only), so kept out of line with its
+// own loads to leave the common path's registers alone.
+__device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx,
+                                               const uint32_t* cbase, uint32_t* conn,
+                                               const uint32_t* x_prev, uint32_t c, uint32_t S,
+                                               float thr, float inc, float dec) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < (int)(S >> 3);
+  uint32_t nb = 0;
+  if (act) {
+    const uint4 o = reinterpret_cast<const uint4*>(cidx + (uint64_t)c * S)[lane];
+    const uint32_t base = cbase[c];
+    float4* p4 = reinterpret_cast<float4*>(perm + (uint64_t)c * S) + 2 * lane;
+    float4 q[2] = {p4[0], p4[1]};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float* f = k < 4 ? &q[0].x + k : &q[1].x + (k - 4);
+      *f = learn_one(*f, input_bit(x_prev, base + off16(o, k)), inc, dec);
+      nb |= (*f >= thr ? 1u : 0u) << k;
+    }
+    p4[0] = q[0];
+    p4[1] = q[1];
+  }
+  uint32_t word = nb << (8u * (lane & 3));
+  word |= __shfl_xor_sync(kFull, word, 1);
+  word |= __shfl_xor_sync(kFull, word, 2);
+  if (act && (lane & 3) == 0) conn[(uint64_t)c * (S >> 5) + (lane >> 2)] = word;
+  return nb;
+}
+
+__device__ __forceinline__ uint32_t compact_count(const uint32_t* x, uint32_t base, const uint4& o,
+                                                  uint32_t cb) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((cb >> k) & 1u) n += input_bit(x, base + off16(o, k));
+  return n;
+}
+
 // Raw overlap of column c (Alg. 1), computed by one warp.  When learn_now,
 // the previous frame's learning is applied first and written back.  With
 // VEC = 4 every lane loads two 16-byte vectors of indices and permanences
@@ -339,7 +398,89 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
-  if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.S <= 512u &&
+  if (STAGE && a.cidx) {
+    // compact form: kCompactCols columns per warp in flight; the input words
+    // the CTA's pools index are first copied to shared memory when they fit
+    // (the copy overlaps the first group's loads), so the bit gathers read
+    // shared memory instead of making one L1 lookup per lane
+    const bool act = lane < (int)(a.S >> 3);
+    const uint32_t cw = a.S >> 5;
+    uint32_t xlo = 0u, xhi = 0u;
+    if (SP_CONTIG_COLUMNS && a.xspan) {
+      xlo = __ldg(a.xspan + 2u * bid);
+      xhi = __ldg(a.xspan + 2u * bid + 1u);
+    }
+    const bool sx = xhi > xlo && (xhi - xlo) * 4u <= xspan_cap;
+    uint32_t* xs = dyn_smem;
+    if (sx) {
+      for (uint32_t w = threadIdx.x; w < xhi - xlo; w += kStepThreads)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(xs + w)),
+                     "l"(a.x + xlo + w)
+                     : "memory");
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    uint4 o[kCompactCols];
+    uint32_t cb[kCompactCols], base[kCompactCols];
+    auto load_group = [&](uint32_t c0) {
+#pragma unroll
+      for (int j = 0; j < kCompactCols; ++j) {
+        const uint32_t c = c0 + j * c_step;
+        const bool ok = c < c_end;
+        o[j] = (ok && act)
+                   ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.cidx + (uint64_t)c * a.S) + lane)
+                   : make_uint4(0u, 0u, 0u, 0u);
+        cb[j] = (ok && act)
+                    ? (ld_state<STREAM>(a.conn + (uint64_t)c * cw + (lane >> 2)) >> (8u * (lane & 3))) & 255u
+                    : 0u;
+        base[j] = ok ? __ldg(a.cbase + c) : 0u;
+      }
+    };
+    auto run_group = [&](uint32_t c0, auto count) {
+#pragma unroll
+      for (int j = 0; j < kCompactCols; ++j) {
+        const uint32_t c = c0 + j * c_step;
+        if (c < c_end && learning(c))
+          cb[j] = compact_learn(a.perm, a.cidx, a.cbase, a.conn, a.x_prev, c, a.S, a.thr, a.inc,
+                                a.dec);
+      }
+      uint32_t cnt[kCompactCols];
+#pragma unroll
+      for (int j = 0; j < kCompactCols; ++j) cnt[j] = count(base[j], o[j], cb[j]);
+#pragma unroll
+      for (int j = 0; j < kCompactCols; ++j) {
+        const uint32_t c = c0 + j * c_step;
+        const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
+        if (c < c_end && lane == 0) publish(c, r);
+      }
+    };
+    if (sx) {
+      load_group(c_first);  // in flight while the span lands
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+      auto count_s = [&](uint32_t b, const uint4& q, uint32_t m) {
+        uint32_t n = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t i = b + off16(q, k);
+          if ((m >> k) & 1u) n += (xs[(i >> 5) - xlo] >> (i & 31u)) & 1u;
+        }
+        return n;
+      };
+      for (uint32_t c0 = c_first; c0 < c_end; c0 += kCompactCols * c_step) {
+        if (c0 != c_first) load_group(c0);
+        run_group(c0, count_s);
+      }
+      __syncthreads();  // the span becomes the last CTA's working memory
+    } else {
+      auto count_g = [&](uint32_t b, const uint4& q, uint32_t m) {
+        return compact_count(a.x, b, q, m);
+      };
+      for (uint32_t c0 = c_first; c0 < c_end; c0 += kCompactCols * c_step) {
+        load_group(c0);
+        run_group(c0, count_g);
+      }
+    }
+  } else if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.S <= 512u &&
       kStepWarps * stage_ring_bytes(a.S) <= stage_cap) {
     // Each warp streams its columns' pool and permanence rows through a ring
     // of kRing shared-memory slots with bulk copies: the copies of the next
@@ -514,6 +655,9 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.duty = d.duty;
   a.duty_period = d.duty_period;
   a.xspan = d.xspan;
+  a.cidx = d.cidx;
+  a.cbase = d.cbase;
+  a.conn = d.conn;
   a.C = d.C;
   a.S = d.S;
   a.n_words = d.n_words;
@@ -562,6 +706,42 @@ cudaError_t kernels_init() {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sp_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               bytes);
+}
+
+// One warp per column: base, 16-bit offsets and connected bits.
+__global__ void __launch_bounds__(256) sp_compact_kernel(const uint32_t* idx, const float* perm,
+                                                         uint32_t C, uint32_t S, float thr,
+                                                         uint16_t* cidx, uint32_t* cbase,
+                                                         uint32_t* conn, uint32_t* wide) {
+  const uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5), lane = threadIdx.x & 31u;
+  if (c >= C) return;
+  const uint32_t* row = idx + (uint64_t)c * S;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t s = lane; s < S; s += 32) {
+    lo = min(lo, row[s]);
+    hi = max(hi, row[s]);
+  }
+  lo = __reduce_min_sync(kFull, lo);
+  hi = __reduce_max_sync(kFull, hi);
+  if (hi - lo > 0xffffu) {
+    if (lane == 0) atomicOr(wide, 1u);
+    return;
+  }
+  for (uint32_t s = lane; s < S; s += 32) {
+    cidx[(uint64_t)c * S + s] = (uint16_t)(row[s] - lo);
+    const uint32_t bits = __ballot_sync(kFull, perm[(uint64_t)c * S + s] >= thr);
+    if (lane == 0) conn[(uint64_t)c * (S >> 5) + (s >> 5)] = bits;
+  }
+  if (lane == 0) cbase[c] = lo;
+}
+
+cudaError_t launch_compact(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
+                           float thr, uint16_t* cidx, uint32_t* cbase, uint32_t* conn,
+                           uint32_t* wide, cudaStream_t stream) {
+  sp_compact_kernel<<<(C + 7u) / 8u, 256, 0, stream>>>(idx, perm, C, S, thr, cidx, cbase, conn,
+                                                      wide);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
 }
 
 // Block b of `per` consecutive columns: lowest and one past the highest input

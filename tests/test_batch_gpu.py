@@ -101,6 +101,38 @@ def test_batch_staged_state(monkeypatch, cpw):
     _check(cases, frames, True, acts, perms, ovs, f"staged cpw={cpw}")
 
 
+@pytest.mark.parametrize("xspan_kb", ["0", "16"])
+@pytest.mark.parametrize("compact", ["1", "0"])
+def test_batch_compact_form(monkeypatch, compact, xspan_kb):
+    """Members whose synapse count is a multiple of 32 (<= 256) and whose pools
+    span at most 65536 inputs run on 16-bit offsets and connected bits; the
+    others (a pool spread over a 960x540 frame, S = 48) on the full form.
+    Both must equal the oracle, learning included, with the CTAs' input words
+    read from global memory or first copied to shared memory."""
+    monkeypatch.setenv("SP_BATCH_COMPACT", compact)
+    monkeypatch.setenv("SP_BATCH_XSPAN_KB", xspan_kb)
+    cases, frames = [], []
+    for i, S in enumerate((32, 64, 128, 256)):
+        c = wl.grid_case(f"win{S}", 256, S, wl.BASE_SEED + 400 + i, W=320, H=180, rf=32, k=6,
+                         inhibition=1 if S == 64 else 0, radius=3)
+        if S == 128:
+            c.boost = synth.perm_uniform(wl.BASE_SEED + 7, (256,), 0.5, 2.0)
+        cases.append(c)
+        frames.append(wl.blob_frames(10, W=320, H=180, seed=wl.BASE_SEED + 400 + i))
+    n_in = 960 * 540
+    wide = wl.Case("wide", 960, 540, 128, 64,
+                   synth.pool_uniform(wl.BASE_SEED + 410, 128, 64, n_in),
+                   synth.perm_uniform(wl.BASE_SEED + 411, (128, 64), 0.1, 0.3),
+                   np.ones(128, np.float32), k=5, min_overlap=1)
+    cases.append(wide)
+    frames.append(wl.blob_frames(10, seed=wl.BASE_SEED + 412))
+    odd = wl.grid_case("s48", 256, 48, wl.BASE_SEED + 413, W=320, H=180, rf=32, k=6)
+    cases.append(odd)
+    frames.append(wl.blob_frames(10, W=320, H=180, seed=wl.BASE_SEED + 414))
+    acts, perms, ovs = _run_batch(cases, frames, True, [3, 7])
+    _check(cases, frames, True, acts, perms, ovs, f"compact={compact} xspan={xspan_kb}")
+
+
 def test_batch_equals_members_alone_and_hands_back_state():
     """A batch, then each member continued alone: the same as the oracle over
     the whole sequence (pending learning handed back by the batch)."""
