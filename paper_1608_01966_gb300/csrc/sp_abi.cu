@@ -668,7 +668,7 @@ void fill_desc(sp_handle* h, sp::BatchDesc* d) {
   d->gh = h->cfg.col_grid_h;
   d->radius = h->cfg.local_radius;
   d->n_ctas = batch_ctas(h->C, h->S);
-  d->xspan = handle_xspan(h, d->n_ctas);
+  d->xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d->n_ctas) : nullptr;
   if (handle_compact(h)) {
     d->cidx = h->d_cidx;
     d->cbase = h->d_cbase;
