@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core run")
     ap.add_argument("--no-encoder", action="store_true", help="skip the frame-encoder runs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default CTA split instead of autotuning it")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="open-loop serving run (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -487,6 +489,10 @@ def main():
             batch[t, o:o + nw] = pool_packed[(7 * i + t) % FRAME_POOL]
     d_batch = torch.from_numpy(batch.view(np.int32)).to(dev)
     d_masks = torch.zeros((FRAME_POOL, mw), dtype=torch.int32, device=dev)
+    cols_per_warp = None
+    if not args.no_autotune:  # set-up, outside the timed region
+        cols_per_warp = spg.sp_batch_autotune(b, d_batch, 8, fw)
+        info = spg.sp_batch_get_info(b)
 
     def step(t):
         r = t % FRAME_POOL
@@ -587,6 +593,8 @@ def main():
             "config": {"workload": WORKLOAD, "columns": 1024, "synapses": 256,
                        "input": "960x540", "winners_set_size": 40, "learn": True,
                        "instances_per_gpu": n, "frames_per_step_per_instance": 1,
+                       "cols_per_warp": cols_per_warp, "autotuned": cols_per_warp is not None,
+                       "ctas_per_launch": int(info["ctas"]),
                        "state_bytes_per_gpu": int(sum(c.C * c.S * 8 for c in cases)),
                        "l2": "inputs larger than L2 (SP state streamed every step), no flush",
                        "parallelism": f"{world} GPU(s) x {n} independent instances"},

@@ -270,6 +270,22 @@ SP_API void sp_batch_destroy(sp_batch* b);
 
 SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out);
 
+/* Autotune the batch step's CTA shape on the caller's frames: for each
+ * candidate split (each member's default, or 4 warps x {2, 4, 8, 16} columns
+ * per warp for every member) run n_frames inference frames from d_frames
+ * (device batch frames laid out as for sp_batch_compute_device, stride in
+ * words) three times and keep the fastest; the default stays unless another
+ * split is more than 3 % faster (inference frames leave out learning).
+ * *cols_per_warp (nullable) receives the columns per warp chosen, 0 for the
+ * default.  The members' permanences, learning and duty cycles are left as
+ * they were; their last-frame overlaps and active columns are those of the
+ * last tuning frame.  Tuning is a property of the workload and the device
+ * (Section 4.4's sweeps show the cost moving with columns and synapses), so
+ * call it once after sp_batch_create.  SP_EBUSY if learning is pending (tune
+ * before the first learning frame); blocks until done (bounded waits). */
+SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                   uint64_t stride, uint32_t* cols_per_warp);
+
 /* Per-member word offsets inside a batch frame and a batch mask record
  * (arrays of `members` entries; either may be NULL). */
 SP_API sp_status sp_batch_offsets(const sp_batch* b, uint64_t* frame_off, uint64_t* mask_off);

@@ -139,6 +139,7 @@ def lib():
         L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
                                        ct.c_uint64]
         L.sp_batch_sync.argtypes = [vp]
+        L.sp_batch_autotune.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, _u32p]
         L.sp_batch_infer_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_server_create.argtypes = [ct.POINTER(SpServerConfig), ct.POINTER(vp)]
         L.sp_server_destroy.argtypes = [vp]
@@ -367,6 +368,15 @@ def sp_batch_compute_device(b, d_frames, n_frames, stride_words, learn, d_masks=
     _check(lib().sp_batch_compute_device(b, _addr(d_frames), n_frames, stride_words,
                                          1 if learn else 0, _addr(d_masks), mask_stride_words,
                                          _stream(stream)), "sp_batch_compute_device")
+
+
+def sp_batch_autotune(b, d_frames, n_frames, stride_words):
+    """Pick the batch step's CTA split on device batch frames; returns the
+    columns per warp chosen (0: each member's default)."""
+    out = ct.c_uint32(0)
+    _check(lib().sp_batch_autotune(b, _addr(d_frames), n_frames, stride_words, ct.byref(out)),
+           "sp_batch_autotune")
+    return out.value
 
 
 def sp_batch_compute(b, frames, learn, masks_out=None):

@@ -1076,6 +1076,8 @@ struct sp_batch {
   sp::BatchDesc* d_desc = nullptr;
   uint32_t* d_cta_inst = nullptr;
   uint32_t n_ctas = 0, max_C = 0;
+  std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
+  uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
@@ -1106,12 +1108,13 @@ namespace rt {
 // CTAs given to one SP in a batch launch: every warp takes several columns
 // so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
 // per-CTA ticket and fence cost small).  SP_BATCH_COLS_PER_WARP overrides.
-uint32_t batch_ctas(uint32_t C, uint32_t S) {
+uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp) {
   uint32_t cpw = S >= 128u ? 8u : (S >= 32u ? 8u : 16u);
   if (const char* e = std::getenv("SP_BATCH_COLS_PER_WARP")) {
     const long v = std::strtol(e, nullptr, 10);
     if (v >= 1 && v <= 64) cpw = (uint32_t)v;
   }
+  if (cols_per_warp) cpw = cols_per_warp;
   const uint32_t per_cta = (uint32_t)sp::kStepWarps * cpw;
   return (C + per_cta - 1u) / per_cta;
 }
@@ -1346,6 +1349,7 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   b->frame_words = foff;
   b->mask_words = moff;
   b->n_ctas = (uint32_t)cta_inst.size();
+  b->h_desc = desc;
   const size_t desc_bytes = align256(sizeof(sp::BatchDesc) * n);
   cudaError_t e = device_malloc((void**)&b->d_block, desc_bytes + cta_inst.size() * 4);
   if (e == cudaSuccess) {
@@ -1578,6 +1582,128 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
   b->cur ^= 1;
   b->frames += n_frames;
   return SP_OK;
+}
+
+namespace {
+
+// Re-split every member into CTAs of 4 * cols_per_warp columns (0: each
+// member's default) and upload the descriptors and CTA map.  The batch must
+// be idle.
+sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
+  std::vector<uint32_t> cta_inst;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    sp_handle* h = b->members[i];
+    sp::BatchDesc& d = b->h_desc[i];
+    d.n_ctas = batch_ctas(h->C, h->S, cols_per_warp);
+    d.cta_first = (uint32_t)cta_inst.size();
+    d.xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d.n_ctas) : nullptr;
+    for (uint32_t c = 0; c < d.n_ctas; ++c) cta_inst.push_back((uint32_t)i);
+  }
+  const size_t n = b->members.size();
+  const size_t desc_bytes = align256(sizeof(sp::BatchDesc) * n);
+  if (cta_inst.size() > b->n_ctas) {  // the CTA map grows: a new block
+    void* blk = nullptr;
+    SP_CUDA(device_malloc(&blk, desc_bytes + cta_inst.size() * 4));
+    cudaFree(b->d_block);
+    b->d_block = blk;
+    b->d_desc = static_cast<sp::BatchDesc*>(blk);
+    b->d_cta_inst = reinterpret_cast<uint32_t*>(static_cast<char*>(blk) + desc_bytes);
+  }
+  SP_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(sp::BatchDesc) * n,
+                          cudaMemcpyHostToDevice, b->stream));
+  SP_CUDA(cudaMemcpyAsync(b->d_cta_inst, cta_inst.data(), cta_inst.size() * 4,
+                          cudaMemcpyHostToDevice, b->stream));
+  SP_CUDA(cudaStreamSynchronize(b->stream));
+  b->n_ctas = (uint32_t)cta_inst.size();
+  b->cols_per_warp = cols_per_warp;
+  for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);  // recorded with the old grid
+  b->graphs.clear();
+  return SP_OK;
+}
+
+}  // namespace
+
+SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                   uint64_t stride, uint32_t* cols_per_warp) {
+  if (!b || !d_frames || n_frames == 0) return fail(SP_EINVAL, "NULL argument or no frames");
+  if (stride < b->frame_words && n_frames > 1)
+    return fail(SP_EINVAL, "frame stride below the batch frame");
+  if (reinterpret_cast<uintptr_t>(d_frames) % 16u || (n_frames > 1 && stride % 4u))
+    return fail(SP_EINVAL, "batch frames must be 16-byte aligned (stride a multiple of 4 words)");
+  if (b->pending) return fail(SP_EBUSY, "learning is pending: tune before learning frames");
+  DeviceGuard g(b->device);
+  sp_status s = batch_wait(b);
+  if (s != SP_OK) return s;
+  // duty cycles advance on every frame: keep a copy and put it back after
+  std::vector<std::pair<float*, size_t>> duty;
+  size_t duty_bytes = 0;
+  for (sp_handle* h : b->members)
+    if (h->cfg.duty_period > 0.0f) {
+      duty.emplace_back(h->d_duty, (size_t)h->C * 4);
+      duty_bytes += align256((size_t)h->C * 4);
+    }
+  char* d_keep = nullptr;
+  if (duty_bytes) SP_CUDA(device_malloc((void**)&d_keep, duty_bytes));
+  size_t off = 0;
+  for (auto& d : duty) {
+    SP_CUDA(cudaMemcpyAsync(d_keep + off, d.first, d.second, cudaMemcpyDeviceToDevice, b->stream));
+    off += align256(d.second);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SP_CUDA(cudaEventCreate(&e0));
+  SP_CUDA(cudaEventCreate(&e1));
+  const uint32_t candidates[] = {0u, 2u, 4u, 8u, 16u};  // 0: each member's default
+  std::vector<std::pair<uint32_t, float>> times;
+  uint32_t best = 0;
+  float best_ms = 0.0f;
+  bool any = false;
+  for (uint32_t cpw : candidates) {
+    s = batch_relayout(b, cpw);
+    if (s != SP_OK) break;
+    float ms_min = 0.0f;
+    for (int rep = 0; rep < 3 && s == SP_OK; ++rep) {
+      cudaError_t e = cudaEventRecord(e0, b->stream);
+      for (uint32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
+        sp::BatchArgs a{};
+        a.desc = b->d_desc;
+        a.cta_inst = b->d_cta_inst;
+        a.frames = d_frames + (uint64_t)t * stride;
+        a.cur = (uint32_t)b->cur;  // inference with nothing pending: parity unchanged
+        a.stage_cap = b->stage_cap;
+        a.xspan_cap = b->xspan_cap;
+        a.err = b->d_err;
+        e = sp::launch_batch_step(a, b->n_ctas, b->max_C, b->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) s = batch_wait(b);
+      else s = fail(SP_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+      float ms = 0.0f;
+      if (s == SP_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        ms_min = rep == 0 ? ms : std::min(ms_min, ms);
+    }
+    if (s == SP_OK) times.emplace_back(cpw, ms_min);
+    if (s == SP_OK && (!any || ms_min < best_ms)) {
+      best = cpw;
+      best_ms = ms_min;
+      any = true;
+    }
+  }
+  // inference frames leave out the learning pass, so a split must beat the
+  // members' default by more than 3 % to replace it
+  for (auto& t : times)
+    if (t.first == 0u && t.second <= best_ms * 1.03f) best = 0u;
+  if (s == SP_OK) s = batch_relayout(b, best);
+  off = 0;
+  for (auto& d : duty) {
+    cudaMemcpyAsync(d.first, d_keep + off, d.second, cudaMemcpyDeviceToDevice, b->stream);
+    off += align256(d.second);
+  }
+  cudaStreamSynchronize(b->stream);
+  if (d_keep) cudaFree(d_keep);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == SP_OK && cols_per_warp) *cols_per_warp = best;
+  return s;
 }
 
 SP_API sp_status sp_batch_sync(sp_batch* b) {

@@ -65,7 +65,7 @@ inline size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
 bool all_ones(const float* v, size_t n);
 sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
-uint32_t batch_ctas(uint32_t C, uint32_t S);
+uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp = 0);
 uint32_t batch_stage_cap(uint32_t need);
 void fill_desc(sp_handle* h, sp::BatchDesc* d);
 uint32_t batch_xspan_cap();

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 
 #include "sp_device.cuh"
 
@@ -614,8 +615,18 @@ __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a)
 #endif
 
 // One frame for every SP of a batch: CTA b works on SP cta_inst[b].
+//
+// Launched with programmatic stream serialization: every CTA lets the next
+// launch in the stream start at once, reads only the batch's static tables
+// (descriptors and CTA map, written at batch creation) and then waits for
+// the previous grid to complete and flush before it touches any frame or
+// state, so the next frame's CTAs take SM slots freed during this frame's
+// tail.  Without a programmatic predecessor the wait returns at once.
 __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_step_kernel(const BatchArgs ba) {
   extern __shared__ __align__(128) uint32_t dyn_smem[];
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  // serving launches copy their tables right before the launch: wait first
+  if (ba.tick) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   const uint32_t inst = __ldg(ba.cta_inst + blockIdx.x);
   const BatchDesc& d = ba.desc[inst];
   StepArgs a;
@@ -658,6 +669,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.cidx = d.cidx;
   a.cbase = d.cbase;
   a.conn = d.conn;
+  if (!ba.tick) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   a.C = d.C;
   a.S = d.S;
   a.n_words = d.n_words;
@@ -792,9 +804,23 @@ cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_
                               cudaStream_t stream) {
   const size_t smem =
       std::max<size_t>(step_smem_bytes(max_C), std::max(a.stage_cap, a.xspan_cap));
-  sp_batch_step_kernel<<<n_ctas, kStepThreads, smem, stream>>>(a);
+  static const bool pdl = [] {
+    const char* e = std::getenv("SP_DISABLE_PDL");
+    return !(e && e[0] == '1');
+  }();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_ctas);
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, sp_batch_step_kernel, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t stream) {

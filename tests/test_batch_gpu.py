@@ -191,3 +191,48 @@ def test_batch_rejects_bad_members():
     assert e.value.status == 5
     spg.sp_batch_destroy(b)
     spg.sp_destroy(h)
+
+
+def test_batch_autotune_keeps_state():
+    """Autotuning times inference frames on every candidate split and keeps
+    the fastest; permanences, learning and duty cycles continue exactly as
+    if it had not run (oracle over the real frames only)."""
+    import oracle
+    from helpers import oracle_params
+    cases = [wl.frame_case(seed=wl.BASE_SEED + 500 + i) for i in range(2)]
+    unv, dens = wl.uneven_cases(3, c_range=(200, 900), n_in_range=(512, 4096))
+    cases += unv
+    period = 25.0
+    real = [wl.blob_frames(6, seed=wl.BASE_SEED + 500 + i) for i in range(2)]
+    real += [wl.bernoulli_frames(i, c.n_in, dens[i], 6) for i, c in enumerate(unv)]
+    tune = [wl.blob_frames(3, seed=wl.BASE_SEED + 520 + i) for i in range(2)]
+    tune += [wl.bernoulli_frames(i, c.n_in, dens[i], 3, start=100) for i, c in enumerate(unv)]
+    hs = [spg.sp_create_from_state(c.config(duty_period=period), c.idx, c.perm, c.boost)
+          for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    d_tune = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in tune], fo, fw).view(np.int32)).cuda()
+    cpw = spg.sp_batch_autotune(b, d_tune, 3, fw)
+    assert cpw in (0, 2, 4, 8, 16)
+    d_real = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in real], fo, fw).view(np.int32)).cuda()
+    mw = info["mask_words"]
+    dm = torch.zeros((6, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_compute_device(b, d_real, 6, fw, True, dm, mw, torch.cuda.current_stream())
+    spg.sp_batch_sync(b)
+    masks = dm.cpu().numpy().view(np.uint32)
+    spg.sp_batch_destroy(b)
+    for i, (c, h) in enumerate(zip(cases, hs)):
+        perm = c.perm.copy()
+        duty = np.zeros(c.C, np.float32)
+        acts = []
+        for t in range(6):
+            a = oracle.run(oracle_params(c), c.idx, perm, c.boost, real[i][t:t + 1], True)[0]
+            oracle.duty_update(duty, a, period)
+            acts.append(a)
+        got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+        assert first_diff(got, np.stack(acts)) is None, f"member {i}"
+        np.testing.assert_array_equal(spg.sp_get_permanences(h), perm, err_msg=f"member {i}")
+        np.testing.assert_array_equal(spg.sp_get_duty_cycles(h), duty, err_msg=f"member {i}")
+        spg.sp_destroy(h)
