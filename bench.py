@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true", help="skip the single-SP sequence")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core run")
     ap.add_argument("--no-encoder", action="store_true", help="skip the frame-encoder runs")
+    ap.add_argument("--per-frame-calls", action="store_true",
+                    help="one API call (one launch) per step instead of one per run of steps")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default CTA split instead of autotuning it")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
@@ -165,14 +167,15 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """DRAM bytes per launch of the batch step kernel from the committed ncu
-    summary, only while the kernel source is unchanged since the capture."""
+def read_traffic(kernel):
+    """DRAM bytes per step (one batch frame) of the batch kernel from the
+    committed ncu summary, only while the kernel source is unchanged since
+    the capture and the capture is of the same kernel."""
     try:
         with open(os.path.join(ROOT, "profiles", "sp_batch_step_traffic.json")) as f:
             d = json.load(f)
-        if d.get("source_sha") == kernel_source_sha():
-            return d.get("dram_bytes_per_launch")
+        if d.get("source_sha") == kernel_source_sha() and d.get("kernel") == kernel:
+            return d.get("dram_bytes_per_step")
     except Exception:
         pass
     return None
@@ -498,8 +501,22 @@ def main():
         r = t % FRAME_POOL
         spg.sp_batch_compute_device(b, d_batch[r], 1, fw, True, d_masks[r], mw, stream)
 
-    for w in range(max(3, args.warmup)):
-        step(w)
+    def steps(t0, k):
+        """k consecutive steps from step t0: one call per run of pool frames
+        (a call over several frames is one persistent launch)."""
+        if args.per_frame_calls:
+            for t in range(t0, t0 + k):
+                step(t)
+            return
+        t = t0
+        while t < t0 + k:
+            r = t % FRAME_POOL
+            m = min(t0 + k - t, FRAME_POOL - r)
+            spg.sp_batch_compute_device(b, d_batch[r], m, fw, True, d_masks[r], mw, stream)
+            t += m
+
+    warm = max(3, args.warmup)
+    steps(0, warm)
     spg.sp_batch_sync(b)
     torch.cuda.synchronize()
 
@@ -511,8 +528,7 @@ def main():
     clocks.start()
     launches0 = spg.sp_kernel_launch_count()
     start.record(stream)
-    for s in range(args.steps):
-        step(max(3, args.warmup) + s)
+    steps(warm, args.steps)
     end.record(stream)
     torch.cuda.synchronize()
     launches = spg.sp_kernel_launch_count() - launches0
@@ -571,11 +587,15 @@ def main():
 
     peak, peak_kind = read_peaks()
     per_launch = sum(algorithmic_bytes_per_frame(c) for c in cases)
-    achieved = per_launch / (ms / 1000.0) / 1e9  # one batch-step launch per step
+    achieved = per_launch / (ms / 1000.0) / 1e9  # bytes of one step / time of one step
     compact = all(compact_form(c) for c in cases)
     moved = sum(compact_bytes_per_frame(c) if compact_form(c) else algorithmic_bytes_per_frame(c)
                 for c in cases)
-    traffic = read_traffic()
+    persistent = (not args.per_frame_calls and args.steps > 1
+                  and os.environ.get("SP_DISABLE_PERSISTENT", "0") != "1")
+    kernel_name = "sp_batch_run_kernel" if persistent else "sp_batch_step_kernel"
+    steps_per_launch = (args.steps / max(1, launches)) if persistent else 1
+    traffic = read_traffic(kernel_name)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,16 +619,17 @@ def main():
                        "l2": "inputs larger than L2 (SP state streamed every step), no flush",
                        "parallelism": f"{world} GPU(s) x {n} independent instances"},
             "column_updates_per_s": value * 1024,
-            "roofline": {"bound": "hbm", "kernel": "sp_batch_step_kernel", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": per_launch,
+                         "algorithmic_bytes_per_step": per_launch,
                          "form": ("compact: 16-bit pool offsets + connected bits, fp32 "
                                   "permanences touched only by learning columns") if compact
                                  else "full: 32-bit pools + fp32 permanences",
-                         "form_bytes_per_launch": moved,
+                         "form_bytes_per_step": moved,
                          "form_frac": moved / (ms / 1000.0) / 1e9 / peak,
-                         "avg_launch_us": ms * 1000.0},
+                         "avg_us_per_step": ms * 1000.0,
+                         "steps_per_launch": steps_per_launch},
             "e2e": {"value": e2e_value, "unit": "frames/s",
                     "h2d_bytes_per_step": int(info["frame_words"] * 4),
                     "d2h_bytes_per_step": int(mw * 4)},

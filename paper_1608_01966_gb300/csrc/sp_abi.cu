@@ -1077,6 +1077,7 @@ struct sp_batch {
   uint32_t* d_cta_inst = nullptr;
   uint32_t n_ctas = 0, max_C = 0;
   std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
+  void* d_sync = nullptr;             // persistent launches: work counter, abort, done[n]
   uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
@@ -1199,6 +1200,7 @@ void free_batch(sp_batch* b) {
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   if (b->d_block) cudaFree(b->d_block);
   if (b->d_infer_args) cudaFree(b->d_infer_args);
+  if (b->d_sync) cudaFree(b->d_sync);
   if (b->h_err) cudaFreeHost(b->h_err);
   for (sp_handle* h : b->members) {
     if (h->batch != b) continue;
@@ -1245,8 +1247,42 @@ sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, ui
   return SP_OK;
 }
 
+// Whether sequences of batch frames run as one persistent launch
+// (SP_DISABLE_PERSISTENT=1 keeps one launch per frame).
+bool persistent_enabled() {
+  const char* e = std::getenv("SP_DISABLE_PERSISTENT");
+  return !(e && e[0] == '1');
+}
+
 sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t stride, int learn,
                     uint32_t* masks, uint64_t mstride) {
+  if (n >= 2 && persistent_enabled()) {
+    sp::BatchRunArgs r{};
+    r.desc = b->d_desc;
+    r.cta_inst = b->d_cta_inst;
+    r.items_per_frame = b->n_ctas;
+    r.n_frames = n;
+    r.frames = x_base;
+    r.stride = stride;
+    r.masks_out = masks;
+    r.mstride = mstride;
+    r.cur0 = (uint32_t)b->cur;
+    r.pending0 = b->pending ? 1u : 0u;
+    r.learn = learn ? 1u : 0u;
+    r.epoch = (uint32_t)b->frames;
+    r.work = static_cast<unsigned long long*>(b->d_sync);
+    r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
+    r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
+    r.err = b->d_err;
+    r.stage_cap = b->stage_cap;
+    r.xspan_cap = b->xspan_cap;
+    SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16, b->stream));
+    SP_CUDA(sp::launch_batch_run(r, b->max_C, b->stream));
+    b->pending = learn != 0;
+    b->cur ^= (int)(n & 1u);
+    b->frames += n;
+    return SP_OK;
+  }
   if (n < kGraphMinFrames || !graphs_enabled()) {
     sp_status s = batch_enqueue(b, b->stream, x_base, n, stride, learn, masks, mstride);
     if (s == SP_OK) b->frames += n;
@@ -1359,7 +1395,9 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_switch, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_wait, cudaEventDisableTiming);
-  if (e == cudaSuccess && b->stage_cap) {
+  if (e == cudaSuccess) e = device_malloc(&b->d_sync, 16 + (size_t)n * 4);
+  if (e == cudaSuccess) e = cudaMemset(b->d_sync, 0, 16 + (size_t)n * 4);
+  if (e == cudaSuccess) {
     e = cudaHostAlloc((void**)&b->h_err, 4, cudaHostAllocMapped);
     if (e == cudaSuccess) {
       *b->h_err = 0u;

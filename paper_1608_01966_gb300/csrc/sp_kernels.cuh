@@ -72,6 +72,25 @@ struct BatchDesc {
   uint32_t cta_first, n_ctas;  // this SP's CTAs in the batch grid
 };
 
+// A sequence of batch frames in one persistent launch (see sp_batch_run_kernel).
+struct BatchRunArgs {
+  const BatchDesc* desc;
+  const uint32_t* cta_inst;     // [items_per_frame] SP of each CTA of one frame's grid
+  uint32_t items_per_frame;
+  uint32_t n_frames;
+  const uint32_t* frames;       // batch frame t at frames + t * stride
+  uint64_t stride;
+  uint32_t* masks_out;          // batch mask record t at masks_out + t * mstride (nullable)
+  uint64_t mstride;
+  uint32_t cur0, pending0, learn;  // parity and pending learning before frame 0
+  uint32_t epoch;               // frames the batch completed before this launch
+  unsigned long long* work;     // item counter, 0 at launch
+  uint32_t* abort;              // 0 at launch; set when a wait gives up
+  uint32_t* done;               // per SP: epoch + t + 1 once frame t is complete
+  uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
+  uint32_t stage_cap, xspan_cap;
+};
+
 // Per-launch entry of one SP when a launch steps a chosen subset of SPs,
 // each with its own state (serving: streams advance independently).
 struct TickMember {
@@ -103,6 +122,9 @@ struct BatchArgs {
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream);
+// One persistent launch over r.n_frames batch frames (grid sized to the
+// resident CTAs); r.work and r.abort must be 0.
+cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream);
 // Compact form of an SP's pools and connectivity (S % 32 == 0, S <= 256):
 // cbase[c] = min_s idx[c][s], cidx[c][s] = idx[c][s] - cbase[c],
 // conn[c][s / 32] bit s % 32 = perm[c][s] >= thr.  *wide is set to 1 if some

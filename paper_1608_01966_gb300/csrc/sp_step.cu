@@ -372,7 +372,8 @@ __host__ __device__ __forceinline__ uint32_t stage_ring_bytes(uint32_t S) {
 template <int VEC, bool STREAM, bool STAGE = false>
 __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint32_t nb,
                                           uint32_t* dyn_smem, uint32_t stage_cap = 0u,
-                                          uint32_t* err = nullptr, uint32_t xspan_cap = 0u) {
+                                          uint32_t* err = nullptr, uint32_t xspan_cap = 0u,
+                                          uint32_t* done = nullptr, uint32_t done_value = 0u) {
   __shared__ uint32_t s_ticket;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -397,7 +398,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
   };
   auto learning = [&](uint32_t c) {
-    return a.mask_prev && ((__ldg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
+    return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
   if (STAGE && a.cidx) {
     // compact form: kCompactCols columns per warp in flight; the input words
@@ -601,6 +602,15 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
   __threadfence();
   last_cta_inhibit(a, dyn_smem, dyn_smem + a.C);
   if (threadIdx.x == 0) atomicExch(a.counter, 0u);
+  if (done) {
+    // release this frame's results (mask, list, reset counter and
+    // histogram) to the CTAs of the SP's next frame in the same launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(done, done_value);
+    }
+  }
 }
 
 template <int VEC>
@@ -708,12 +718,125 @@ size_t step_smem_bytes(uint32_t C) { return ((size_t)C + (C + 31u) / 32u) * size
 
 int step_grid(uint32_t C) { return (int)((C + kStepWarps - 1) / kStepWarps); }
 
+// Persistent launch over a whole sequence of batch frames.  CTAs take work
+// items in order from a counter: item (t, k) is CTA k of frame t's grid.  An
+// item of frame t > 0 first waits until its SP's frame t - 1 is complete
+// (the SP's last CTA of that frame releases done[inst] = epoch + t).  The
+// items it waits for were taken earlier by CTAs that are running, so the
+// wait always ends; it is bounded all the same (1 s of %globaltimer, then
+// the launch is aborted and the error word set).  Frame t + 1 of one SP thus
+// overlaps frame t of the others instead of waiting for a whole grid.
+constexpr unsigned long long kDoneWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_run_kernel(const BatchRunArgs r) {
+  extern __shared__ __align__(128) uint32_t dyn_smem[];
+  __shared__ uint32_t s_t, s_k, s_go;
+  const unsigned long long total = (unsigned long long)r.items_per_frame * r.n_frames;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      uint32_t go = 0u;
+      if (ld_acquire(r.abort) == 0u) {
+        const unsigned long long it = atomicAdd(r.work, 1ull);
+        if (it < total) {
+          s_t = (uint32_t)(it / r.items_per_frame);
+          s_k = (uint32_t)(it % r.items_per_frame);
+          go = 1u;
+        }
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const uint32_t t = s_t, k = s_k;
+    const uint32_t inst = __ldg(r.cta_inst + k);
+    const BatchDesc& d = r.desc[inst];
+    if (t > 0u) {
+      if (threadIdx.x == 0) {
+        const uint32_t target = r.epoch + t;
+        const unsigned long long t0 = global_ns();
+        uint32_t ok = 1u;
+        for (uint32_t i = 0;; ++i) {
+          if ((int32_t)(ld_acquire(r.done + inst) - target) >= 0) break;
+          if (ld_acquire(r.abort) != 0u || global_ns() - t0 > kDoneWaitNs) {
+            ok = 0u;
+            break;
+          }
+          __nanosleep(i < 64u ? 32u : 256u);
+        }
+        if (!ok) {
+          atomicExch(r.abort, 1u);
+          if (r.err) atomicExch(r.err, 1u);
+        }
+        s_go = ok;
+      }
+      __syncthreads();
+      if (!s_go) return;
+    }
+    StepArgs a;
+    const uint32_t cur = r.cur0 ^ (t & 1u);
+    const uint32_t pending = t > 0u ? r.learn : r.pending0;
+    const uint32_t save = t + 1u == r.n_frames ? 1u : 0u;
+    a.idx = d.idx;
+    a.perm = d.perm;
+    a.boost = d.boost;
+    a.ov = d.ov;
+    a.result_copy = nullptr;
+    a.x = r.frames + (uint64_t)t * r.stride + d.frame_off;
+    a.x_prev = !pending ? nullptr
+               : (t > 0u ? r.frames + (uint64_t)(t - 1u) * r.stride + d.frame_off
+                         : (cur ? d.xsave0 : d.xsave1));
+    a.mask_prev = pending ? (cur ? d.mask0 : d.mask1) : nullptr;
+    a.x_save = (r.learn && save) ? (cur ? d.xsave1 : d.xsave0) : nullptr;
+    a.mask_out = cur ? d.mask1 : d.mask0;
+    a.mask_copy = r.masks_out ? r.masks_out + (uint64_t)t * r.mstride + d.mask_off : nullptr;
+    a.result = d.result;
+    a.counter = d.counter;
+    a.hist = d.hist;
+    a.duty = d.duty;
+    a.duty_period = d.duty_period;
+    a.xspan = d.xspan;
+    a.cidx = d.cidx;
+    a.cbase = d.cbase;
+    a.conn = d.conn;
+    a.C = d.C;
+    a.S = d.S;
+    a.n_words = d.n_words;
+    a.mask_words = d.mask_words;
+    a.thr = d.thr;
+    a.inc = d.inc;
+    a.dec = d.dec;
+    a.min_overlap = d.min_overlap;
+    a.k = d.k;
+    a.inhibition = d.inhibition;
+    a.gw = d.gw;
+    a.gh = d.gh;
+    a.radius = d.radius;
+    const uint32_t bid = k - d.cta_first;
+    if ((a.S & 3u) == 0u)
+      step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, r.stage_cap, r.err, r.xspan_cap,
+                               r.done + inst, r.epoch + t + 1u);
+    else
+      step_body<1, true>(a, bid, d.n_ctas, dyn_smem, 0u, nullptr, 0u, r.done + inst,
+                         r.epoch + t + 1u);
+    __syncthreads();  // shared memory is reused by the next item
+  }
+}
+
 cudaError_t kernels_init() {
   const int bytes = (int)step_smem_bytes(SP_MAX_COLUMNS);
   cudaError_t e = cudaFuncSetAttribute(sp_step_kernel<4>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(sp_batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(sp_batch_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sp_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -789,6 +912,24 @@ cudaError_t launch_xspan(const uint32_t* idx, uint32_t C, uint32_t S, uint32_t n
                          uint32_t* out, cudaStream_t stream) {
   const uint32_t per = (C + n_ctas - 1u) / n_ctas;
   sp_xspan_kernel<<<n_ctas, 256, 0, stream>>>(idx, C, S, per, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream) {
+  const size_t smem =
+      std::max<size_t>(step_smem_bytes(max_C), std::max(r.stage_cap, r.xspan_cap));
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sp_batch_run_kernel, kStepThreads,
+                                                      smem);
+  if (e != cudaSuccess) return e;
+  const unsigned long long total = (unsigned long long)r.items_per_frame * r.n_frames;
+  const unsigned long long resident = (unsigned long long)std::max(1, sms * std::max(1, per_sm));
+  const uint32_t grid = (uint32_t)std::min(total, resident);
+  sp_batch_run_kernel<<<grid, kStepThreads, smem, stream>>>(r);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

@@ -236,3 +236,20 @@ def test_batch_autotune_keeps_state():
         np.testing.assert_array_equal(spg.sp_get_permanences(h), perm, err_msg=f"member {i}")
         np.testing.assert_array_equal(spg.sp_get_duty_cycles(h), duty, err_msg=f"member {i}")
         spg.sp_destroy(h)
+
+
+@pytest.mark.parametrize("persistent", ["1", "0"])
+def test_batch_long_sequence_in_one_call(monkeypatch, persistent):
+    """40 learning frames of uneven members (compact and full forms, local
+    inhibition, duty cycles) in one call: one persistent launch in which each
+    member's frame t + 1 waits only for that member's frame t, or one launch
+    per frame."""
+    monkeypatch.setenv("SP_DISABLE_PERSISTENT", "0" if persistent == "1" else "1")
+    cases, dens = wl.uneven_cases(5, c_range=(64, 1200), n_in_range=(256, 4096))
+    g = wl.grid_case("local", 256, 64, 7, W=320, H=180, rf=32, k=5, inhibition=1, radius=4)
+    cases.append(g)
+    dens.append(None)
+    frames = [wl.blob_frames(40, W=320, H=180, seed=11) if d is None
+              else wl.bernoulli_frames(i, c.n_in, d, 40) for i, (c, d) in enumerate(zip(cases, dens))]
+    acts, perms, ovs = _run_batch(cases, frames, True, [40])
+    _check(cases, frames, True, acts, perms, ovs, f"persistent={persistent}")
