@@ -255,6 +255,75 @@ def oracle_sample(cases, pool_u8, seconds, start_step=0):
         step += 1
 
 
+def oracle_sample_parallel(cases, pool_u8, seconds, threads):
+    """The same oracle on `threads` host threads, each stepping its own
+    instances in order (the SPs are independent; the oracle's C code runs
+    without the GIL).  Returns (SP frames/s over all threads, frames done)."""
+    import threading
+    import oracle
+    stop = time.perf_counter() + seconds
+    counts = [0] * threads
+
+    def work(j):
+        mine = [(i, c, oracle.params(c.C, c.S, c.n_in, c.thr, c.inc, c.dec, c.min_overlap, c.k),
+                 c.perm.copy()) for i, c in enumerate(cases) if i % threads == j]
+        step = 0
+        while time.perf_counter() < stop:
+            for i, c, p, perm in mine:
+                oracle.run(p, c.idx, perm, c.boost, pool_u8[(7 * i + step) % FRAME_POOL][None, :],
+                           True)
+                counts[j] += 1
+                if time.perf_counter() >= stop:
+                    return
+            step += 1
+
+    ts = [threading.Thread(target=work, args=(j,)) for j in range(threads)]
+    t0 = time.perf_counter()
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    el = time.perf_counter() - t0
+    return sum(counts) / el, sum(counts)
+
+
+def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
+    """64 independent SPs of uneven shapes (columns 128..4096, synapses
+    16..256, inputs 256..16384 bits at 2-20 % density, k = 2 % of columns,
+    learning on), autotuned, stepped by persistent launches of 16 frames."""
+    from paper_1608_01966_gb300 import workloads as wl
+    cases, dens = wl.uneven_cases(members)
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    fr = [wl.pack(wl.bernoulli_frames(i, c.n_in, dens[i], frames)) for i, c in enumerate(cases)]
+    d = torch.from_numpy(wl.batch_frames(fr, fo, fw).view(np.int32)).to(dev)
+    mw = info["mask_words"]
+    dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
+    cpw = spg.sp_batch_autotune(b, d, 4, fw)
+    spg.sp_batch_compute_device(b, d, frames, fw, True, dm, mw, stream)
+    spg.sp_batch_sync(b)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(steps):
+        spg.sp_batch_compute_device(b, d, frames, fw, True, dm, mw, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / (steps * frames)
+    spg.sp_batch_destroy(b)
+    for h in hs:
+        spg.sp_destroy(h)
+    upd = sum(c.C for c in cases)
+    return {"workload": f"{members} uneven SPs (C 128..4096, S 16..256, inputs 256..16384 bits), "
+                        f"learning on, {frames} frames per persistent launch, autotuned",
+            "cols_per_warp": cpw, "us_per_batch_frame": ms * 1000.0,
+            "frames_per_s": members / (ms / 1000.0),
+            "column_updates_per_s": upd / (ms / 1000.0)}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -574,6 +643,10 @@ def main():
     if not args.no_dense:
         dense_tc = run_dense_tc(spg, torch, dev, stream)
 
+    uneven = None
+    if not args.no_dense:
+        uneven = run_uneven_batch(spg, torch, dev, stream)
+
     encoder = None
     if not args.no_encoder:
         encoder = [run_encoder(spg, torch, dev, stream, reduce=1),
@@ -603,6 +676,12 @@ def main():
         cpu = {"value": fps_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} SP frames of the same workload (first 16 instances in step "
                          f"order), one thread, ~{args.cpu_seconds:.0f} s"}
+        threads = os.cpu_count() or 1
+        fps_all, done_all = oracle_sample_parallel(cases[:max(16, threads)], pool_u8,
+                                                   args.cpu_seconds / 2, threads)
+        cpu["all_cores"] = {"value": fps_all, "unit": "frames/s", "cores": threads,
+                            "sample": f"{done_all} SP frames, instances split over {threads} "
+                                      f"threads, ~{args.cpu_seconds / 2:.0f} s"}
 
     if rank == 0:
         line = {
@@ -637,6 +716,7 @@ def main():
             "clocks": clk,
             "single_sp": single,
             "dense_tc": dense_tc,
+            "uneven_batch": uneven,
             "encoder": encoder,
             "serve": serve,
             "cpu_baseline": cpu,

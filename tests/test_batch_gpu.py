@@ -253,3 +253,22 @@ def test_batch_long_sequence_in_one_call(monkeypatch, persistent):
               else wl.bernoulli_frames(i, c.n_in, d, 40) for i, (c, d) in enumerate(zip(cases, dens))]
     acts, perms, ovs = _run_batch(cases, frames, True, [40])
     _check(cases, frames, True, acts, perms, ovs, f"persistent={persistent}")
+
+
+@pytest.mark.parametrize("C", [256, 1024, 4096])
+def test_batch_parameter_sweep(C):
+    """The 54 synapse x min_overlap x k x {global, 9x9 local} combinations of
+    the sweep workload for one column count, as members of one batch (compact
+    form for S = 64 and 256, full form for S = 16), 8 learning frames in one
+    persistent launch, every member against the oracle."""
+    frames1 = wl.blob_frames(8, seed=wl.BASE_SEED + 3)
+    cases, frames = [], []
+    for S in (16, 64, 256):
+        for m in (2, 4, 8):
+            for k in (8, 32, 128):
+                for inh in (0, 1):
+                    cases.append(wl.grid_case("sweep", C, S, wl.BASE_SEED + 3 + C + S,
+                                              min_overlap=m, k=k, inhibition=inh, radius=4))
+                    frames.append(frames1)
+    acts, perms, ovs = _run_batch(cases, frames, True, [8])
+    _check(cases, frames, True, acts, perms, ovs, f"sweep C{C}")
