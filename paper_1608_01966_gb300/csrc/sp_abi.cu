@@ -1078,6 +1078,7 @@ struct sp_batch {
   uint32_t n_ctas = 0, max_C = 0;
   std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
   void* d_sync = nullptr;             // persistent launches: work counter, abort, done[n]
+  uint32_t run_epoch = 0;             // frames issued by persistent launches (done flags)
   uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
@@ -1110,7 +1111,7 @@ namespace rt {
 // so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
 // per-CTA ticket and fence cost small).  SP_BATCH_COLS_PER_WARP overrides.
 uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp) {
-  uint32_t cpw = S >= 128u ? 8u : (S >= 32u ? 8u : 16u);
+  uint32_t cpw = S >= 128u ? 16u : (S >= 32u ? 8u : 16u);
   if (const char* e = std::getenv("SP_BATCH_COLS_PER_WARP")) {
     const long v = std::strtol(e, nullptr, 10);
     if (v >= 1 && v <= 64) cpw = (uint32_t)v;
@@ -1269,7 +1270,7 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.cur0 = (uint32_t)b->cur;
     r.pending0 = b->pending ? 1u : 0u;
     r.learn = learn ? 1u : 0u;
-    r.epoch = (uint32_t)b->frames;
+    r.epoch = b->run_epoch;
     r.work = static_cast<unsigned long long*>(b->d_sync);
     r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
     r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
@@ -1278,6 +1279,7 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.xspan_cap = b->xspan_cap;
     SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16, b->stream));
     SP_CUDA(sp::launch_batch_run(r, b->max_C, b->stream));
+    b->run_epoch += n;
     b->pending = learn != 0;
     b->cur ^= (int)(n & 1u);
     b->frames += n;
@@ -1701,16 +1703,38 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
     float ms_min = 0.0f;
     for (int rep = 0; rep < 3 && s == SP_OK; ++rep) {
       cudaError_t e = cudaEventRecord(e0, b->stream);
-      for (uint32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
-        sp::BatchArgs a{};
-        a.desc = b->d_desc;
-        a.cta_inst = b->d_cta_inst;
-        a.frames = d_frames + (uint64_t)t * stride;
-        a.cur = (uint32_t)b->cur;  // inference with nothing pending: parity unchanged
-        a.stage_cap = b->stage_cap;
-        a.xspan_cap = b->xspan_cap;
-        a.err = b->d_err;
-        e = sp::launch_batch_step(a, b->n_ctas, b->max_C, b->stream);
+      if (n_frames >= 2 && persistent_enabled()) {
+        // the launch form sequences use: one persistent launch, inference
+        sp::BatchRunArgs r{};
+        r.desc = b->d_desc;
+        r.cta_inst = b->d_cta_inst;
+        r.items_per_frame = b->n_ctas;
+        r.n_frames = n_frames;
+        r.frames = d_frames;
+        r.stride = stride;
+        r.cur0 = (uint32_t)b->cur;
+        r.epoch = b->run_epoch;
+        r.work = static_cast<unsigned long long*>(b->d_sync);
+        r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
+        r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
+        r.err = b->d_err;
+        r.stage_cap = b->stage_cap;
+        r.xspan_cap = b->xspan_cap;
+        e = cudaMemsetAsync(b->d_sync, 0, 16, b->stream);
+        if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->stream);
+        b->run_epoch += n_frames;
+      } else {
+        for (uint32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
+          sp::BatchArgs a{};
+          a.desc = b->d_desc;
+          a.cta_inst = b->d_cta_inst;
+          a.frames = d_frames + (uint64_t)t * stride;
+          a.cur = (uint32_t)b->cur;  // inference with nothing pending: parity unchanged
+          a.stage_cap = b->stage_cap;
+          a.xspan_cap = b->xspan_cap;
+          a.err = b->d_err;
+          e = sp::launch_batch_step(a, b->n_ctas, b->max_C, b->stream);
+        }
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) s = batch_wait(b);

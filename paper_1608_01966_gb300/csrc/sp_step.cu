@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a)
 
 // Resident CTAs per SM the batch kernel is compiled for (register budget).
 #ifndef SP_BATCH_MIN_BLOCKS
-#define SP_BATCH_MIN_BLOCKS 16
+#define SP_BATCH_MIN_BLOCKS 12
 #endif
 
 // One frame for every SP of a batch: CTA b works on SP cta_inst[b].
