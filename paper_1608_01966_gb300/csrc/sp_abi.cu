@@ -1111,7 +1111,7 @@ namespace rt {
 // so each CTA streams a few tens of KB of state (fewer, fatter CTAs keep the
 // per-CTA ticket and fence cost small).  SP_BATCH_COLS_PER_WARP overrides.
 uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp) {
-  uint32_t cpw = S >= 128u ? 16u : (S >= 32u ? 8u : 16u);
+  uint32_t cpw = S >= 128u ? 32u : (S >= 32u ? 8u : 16u);
   if (const char* e = std::getenv("SP_BATCH_COLS_PER_WARP")) {
     const long v = std::strtol(e, nullptr, 10);
     if (v >= 1 && v <= 64) cpw = (uint32_t)v;

@@ -423,20 +423,22 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     }
     uint4 o[kCompactCols];
     uint32_t cb[kCompactCols], base[kCompactCols];
-    auto load_group = [&](uint32_t c0) {
+    auto load_into = [&](uint32_t c0, uint4(&oo)[kCompactCols], uint32_t(&cc)[kCompactCols],
+                         uint32_t(&bb)[kCompactCols]) {
 #pragma unroll
       for (int j = 0; j < kCompactCols; ++j) {
         const uint32_t c = c0 + j * c_step;
         const bool ok = c < c_end;
-        o[j] = (ok && act)
-                   ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.cidx + (uint64_t)c * a.S) + lane)
-                   : make_uint4(0u, 0u, 0u, 0u);
-        cb[j] = (ok && act)
+        oo[j] = (ok && act)
+                    ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.cidx + (uint64_t)c * a.S) + lane)
+                    : make_uint4(0u, 0u, 0u, 0u);
+        cc[j] = (ok && act)
                     ? (ld_state<STREAM>(a.conn + (uint64_t)c * cw + (lane >> 2)) >> (8u * (lane & 3))) & 255u
                     : 0u;
-        base[j] = ok ? __ldg(a.cbase + c) : 0u;
+        bb[j] = ok ? __ldg(a.cbase + c) : 0u;
       }
     };
+    auto load_group = [&](uint32_t c0) { load_into(c0, o, cb, base); };
     auto run_group = [&](uint32_t c0, auto count) {
 #pragma unroll
       for (int j = 0; j < kCompactCols; ++j) {
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(kStepThreads) sp_step_kernel(const StepArgs a)
 
 // Resident CTAs per SM the batch kernel is compiled for (register budget).
 #ifndef SP_BATCH_MIN_BLOCKS
-#define SP_BATCH_MIN_BLOCKS 12
+#define SP_BATCH_MIN_BLOCKS 10
 #endif
 
 // One frame for every SP of a batch: CTA b works on SP cta_inst[b].
