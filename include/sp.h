@@ -391,6 +391,18 @@ SP_API sp_status sp_server_close_stream(sp_server* s, uint32_t stream_id);
 SP_API sp_status sp_server_submit(sp_server* s, uint32_t stream_id, const uint32_t* frame_bits,
                                   int learn, uint64_t* request_id);
 
+/* Queue frames for several streams in one call (one lock, one wake-up of the
+ * worker): entry i is the frame at frames[i] (host, stream ids[i]'s
+ * input_words words, copied before return) with learn[i] (NULL = no
+ * learning).  statuses[i] receives SP_OK, SP_EBUSY (that stream's queue is
+ * full; nothing queued for it), SP_EINVAL (closed stream or NULL frame) or
+ * SP_ECUDA; request_ids[i] (nullable array) the request id or 0.  Entries
+ * for one stream are queued in order.  Returns SP_EINVAL only for NULL
+ * arrays. */
+SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t* stream_ids,
+                                       const uint32_t* const* frames, const int* learn,
+                                       uint64_t* request_ids, sp_status* statuses);
+
 /* Take up to max_results finished frames (oldest first), their active lists
  * copied into active[0..active_cap); waits up to wait_ms for the first one.
  * *n_results may be 0.  Results whose lists do not fit stay queued. */

@@ -150,6 +150,9 @@ def lib():
         L.sp_server_close_stream.argtypes = [vp, ct.c_uint32]
         L.sp_server_submit.argtypes = [vp, ct.c_uint32, _u32p, ct.c_int,
                                        ct.POINTER(ct.c_uint64)]
+        L.sp_server_submit_many.argtypes = [vp, ct.c_uint32, _u32p, ct.POINTER(vp),
+                                            ct.POINTER(ct.c_int), ct.POINTER(ct.c_uint64),
+                                            ct.POINTER(ct.c_int)]
         L.sp_server_poll.argtypes = [vp, ct.POINTER(SpServerResult), ct.c_uint32, _u32p,
                                      ct.c_uint32, _u32p, ct.c_uint32]
         L.sp_server_get_permanences.argtypes = [vp, ct.c_uint32, _f32p]
@@ -445,6 +448,36 @@ def sp_server_submit(s, sid, frame_bits, learn):
     _check(lib().sp_server_submit(s, sid, p, 1 if learn else 0, ct.byref(rid)),
            "sp_server_submit")
     return rid.value
+
+
+def sp_server_submit_many(srv, stream_ids, frames, learn=True):
+    """Queue one frame per entry (frames: list of uint32 arrays, C-contiguous).
+    Returns (statuses int array, request ids uint64 array)."""
+    n = len(stream_ids)
+    frames = [np.ascontiguousarray(f, dtype=np.uint32) for f in frames]
+    ptrs = np.array([f.ctypes.data for f in frames], dtype=np.uint64)
+    lf = learn if hasattr(learn, "__len__") else [learn] * n
+    larr = np.array([1 if x else 0 for x in lf], dtype=np.int32)
+    return sp_server_submit_many_ptrs(srv, np.asarray(stream_ids, dtype=np.uint32), ptrs, larr)
+
+
+def sp_server_submit_many_ptrs(srv, stream_ids, frame_ptrs, learn):
+    """sp_server_submit_many on prepared arrays: stream ids (uint32), host
+    addresses of the frames (uint64; the caller keeps the frames alive until
+    the call returns) and learn flags (int32).  Returns (statuses, ids)."""
+    n = len(stream_ids)
+    ids = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+    ptrs = np.ascontiguousarray(frame_ptrs, dtype=np.uint64)
+    larr = np.ascontiguousarray(learn, dtype=np.int32)
+    rid = np.zeros(n, np.uint64)
+    st = np.zeros(n, np.int32)
+    _check(lib().sp_server_submit_many(srv, n, ids.ctypes.data_as(_u32p),
+                                       ptrs.ctypes.data_as(ct.POINTER(ct.c_void_p)),
+                                       larr.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                       rid.ctypes.data_as(ct.POINTER(ct.c_uint64)),
+                                       st.ctypes.data_as(ct.POINTER(ct.c_int))),
+           "sp_server_submit_many")
+    return st, rid
 
 
 def sp_server_poll(s, max_results=256, active_cap=1 << 16, wait_ms=0):

@@ -489,6 +489,50 @@ SP_API sp_status sp_server_submit(sp_server* s, uint32_t id, const uint32_t* bit
   return SP_OK;
 }
 
+SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t* ids,
+                                       const uint32_t* const* frames, const int* learn,
+                                       uint64_t* request_ids, sp_status* statuses) {
+  if (!s || (n && (!ids || !frames || !statuses))) return fail(SP_EINVAL, "NULL argument");
+  DeviceGuard g(s->device);
+  uint32_t queued = 0;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (uint32_t i = 0; i < n; ++i) {
+      statuses[i] = SP_OK;
+      if (request_ids) request_ids[i] = 0;
+      const uint32_t id = ids[i];
+      if (id >= s->streams.size() || !s->streams[id].open || !frames[i]) {
+        statuses[i] = SP_EINVAL;
+        continue;
+      }
+      Stream& S = s->streams[id];
+      if (S.outstanding >= s->cfg.queue_depth) {
+        statuses[i] = SP_EBUSY;
+        continue;
+      }
+      const uint32_t ring = S.head;
+      uint32_t* hs = S.h_ring + (size_t)ring * S.input_words;
+      std::memcpy(hs, frames[i], (size_t)S.input_words * 4);
+      if (cudaMemcpyAsync(S.d_ring + (size_t)ring * S.input_words, hs,
+                          (size_t)S.input_words * 4, cudaMemcpyHostToDevice,
+                          s->copy_stream) != cudaSuccess ||
+          cudaEventRecord(S.ev_h2d[ring], s->copy_stream) != cudaSuccess) {
+        statuses[i] = SP_ECUDA;
+        continue;
+      }
+      S.head = (S.head + 1) % s->cfg.queue_depth;
+      Request r{s->next_id++, S.next_seq++, ring, learn && learn[i] != 0, Clock::now()};
+      S.queue.push_back(r);
+      S.outstanding += 1;
+      ++s->submitted;
+      if (request_ids) request_ids[i] = r.id;
+      ++queued;
+    }
+  }
+  if (queued) s->cv_work.notify_one();
+  return SP_OK;
+}
+
 SP_API sp_status sp_server_poll(sp_server* s, sp_server_result* results, uint32_t max_results,
                                 uint32_t* active, uint32_t active_cap, uint32_t* n_results,
                                 uint32_t wait_ms) {

@@ -112,40 +112,42 @@ def run_open_loop(srv, sids, res, pools, seconds, fps, seed):
 
 
 def run_closed_loop(srv, sids, res, pools, seconds):
-    """Every stream resubmits as soon as its queue has room (saturation)."""
+    """Every stream's queue is kept full (saturation): one producer thread
+    offers the next frame of every stream in one sp_server_submit_many call
+    per round; streams whose queues are full refuse it and get it again in
+    the next round."""
     stop = threading.Event()
-    submitted = [0]
-    lock = threading.Lock()
+    n = len(sids)
+    depth = min(p.shape[0] for p in pools.values())
+    # host address of frame j of stream i's pool
+    ptr = np.array([[pools[res[i]][j].ctypes.data for j in range(depth)] for i in range(n)],
+                   dtype=np.uint64)
+    ids = np.asarray(sids, dtype=np.uint32)
+    learn = np.ones(n, np.int32)
+    rows = np.arange(n)
 
-    def producer(members):
-        k = 0
+    def producer():
+        seq = np.zeros(n, np.int64)
         while not stop.is_set():
-            for i in members:
-                pool = pools[res[i]]
-                try:
-                    spg.sp_server_submit(srv, sids[i], pool[k % pool.shape[0]], True)
-                    with lock:
-                        submitted[0] += 1
-                except spg.SpError as e:
-                    if e.status != 5:
-                        raise
-            k += 1
-            time.sleep(0)
+            st, _ = spg.sp_server_submit_many_ptrs(srv, ids, ptr[rows, seq % depth], learn)
+            ok = st == 0
+            if not ((st == 0) | (st == 5)).all():  # anything but a full queue
+                raise spg.SpError(int(st[~ok & (st != 5)][0]), "sp_server_submit_many", "")
+            seq += ok
+            if not ok.any():
+                time.sleep(0)
 
     lat = []
-    threads = [threading.Thread(target=producer, args=(list(range(j, len(sids), 4)),),
-                                daemon=True) for j in range(4)]
+    th = threading.Thread(target=producer, daemon=True)
     spg.sp_server_get_stats(srv, reset=True)
     t0 = time.perf_counter()
-    for th in threads:
-        th.start()
+    th.start()
     while time.perf_counter() - t0 < seconds:
         for r, _ in spg.sp_server_poll(srv, max_results=1024, wait_ms=10):
             lat.append(r["latency_us"])
     elapsed = time.perf_counter() - t0
     stop.set()
-    for th in threads:
-        th.join()
+    th.join()
     while True:  # drain
         got = spg.sp_server_poll(srv, max_results=1024, wait_ms=100)
         if not got:

@@ -153,3 +153,49 @@ def test_duty_cycles_match_the_oracle():
     np.testing.assert_array_equal(spg.sp_get_duty_cycles(h), duty)
     np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
     spg.sp_destroy(h)
+
+
+def test_submit_many_matches_the_oracle():
+    """Frames offered for every stream at once (sp_server_submit_many), full
+    queues refusing and the frame offered again next round: every stream's
+    results and permanences equal the oracle's."""
+    n, F = 5, 12
+    cases, frames = _streams(n, F)
+    learn = [[(t + i) % 5 != 4 for t in range(F)] for i in range(n)]
+    words = max(wl.pack(f).shape[1] for f in frames)
+    srv = spg.sp_server_create(max_streams=8, queue_depth=2, max_input_words=words,
+                               device_budget_bytes=1 << 30, max_active=64)
+    sids = [spg.sp_server_open_stream(srv, c.config(), state=(c.idx, c.perm, c.boost))
+            for c in cases]
+    packed = [wl.pack(f) for f in frames]
+    nxt = [0] * n
+    got = {i: {} for i in range(n)}
+    done, deadline = 0, time.time() + 60
+    while done < n * F and time.time() < deadline:
+        todo = [i for i in range(n) if nxt[i] < F]
+        if todo:
+            st, rid = spg.sp_server_submit_many(srv, [sids[i] for i in todo],
+                                                [packed[i][nxt[i]] for i in todo],
+                                                [learn[i][nxt[i]] for i in todo])
+            for j, i in enumerate(todo):
+                assert st[j] in (0, 5)
+                if st[j] == 0:
+                    assert rid[j] > 0
+                    nxt[i] += 1
+        for r, act in spg.sp_server_poll(srv, wait_ms=1):
+            assert r["status"] == 0
+            got[sids.index(r["stream_id"])][r["frame_seq"]] = act
+            done += 1
+    assert done == n * F
+    # an unknown stream is refused per entry, not for the call
+    st, _ = spg.sp_server_submit_many(srv, [999], [packed[0][0]], True)
+    assert st[0] == 1
+    for i, c in enumerate(cases):
+        ref, perm, _ = _oracle_lists(c, frames[i], learn[i])
+        for t in range(F):
+            np.testing.assert_array_equal(got[i][t], ref[t], err_msg=f"stream {i} frame {t}")
+        np.testing.assert_array_equal(
+            spg.sp_server_get_permanences(srv, sids[i], (c.C, c.S)), perm)
+    for sid in sids:
+        spg.sp_server_close_stream(srv, sid)
+    spg.sp_server_destroy(srv)
