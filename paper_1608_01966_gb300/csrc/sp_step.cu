@@ -252,67 +252,11 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
   }
 }
 
-// Two columns by one warp with all four 16-byte vectors of each lane in
-// flight before the first gather (S <= 256, S % 4 == 0): twice the bytes in
-// flight of column_overlap.  has1 = false leaves the second column out.
-template <bool STREAM>
-__device__ __forceinline__ void column_overlap_pair(const StepArgs& a, uint32_t c0, uint32_t c1,
-                                                    bool has1, bool learn0, bool learn1,
-                                                    int lane, uint32_t& raw0, uint32_t& raw1) {
-  const uint32_t n4 = a.S >> 2;  // <= 64
-  const uint32_t ja = lane, jb = 32u + lane;
-  const bool va = ja < n4, vb = jb < n4;
-  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-  const float4 f4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const uint4* i0 = reinterpret_cast<const uint4*>(a.idx + (uint64_t)c0 * a.S);
-  const uint4* i1 = reinterpret_cast<const uint4*>(a.idx + (uint64_t)c1 * a.S);
-  float4* q0 = reinterpret_cast<float4*>(a.perm + (uint64_t)c0 * a.S);
-  float4* q1 = reinterpret_cast<float4*>(a.perm + (uint64_t)c1 * a.S);
-  const uint4 ida0 = va ? ld_state<STREAM>(i0 + ja) : z4;
-  const uint4 idb0 = vb ? ld_state<STREAM>(i0 + jb) : z4;
-  float4 pa0 = va ? ld_state<STREAM>(q0 + ja) : f4;
-  float4 pb0 = vb ? ld_state<STREAM>(q0 + jb) : f4;
-  const uint4 ida1 = (has1 && va) ? ld_state<STREAM>(i1 + ja) : z4;
-  const uint4 idb1 = (has1 && vb) ? ld_state<STREAM>(i1 + jb) : z4;
-  float4 pa1 = (has1 && va) ? ld_state<STREAM>(q1 + ja) : f4;
-  float4 pb1 = (has1 && vb) ? ld_state<STREAM>(q1 + jb) : f4;
-  if (learn0) {
-    if (va) {
-      learn4(pa0, ida0, a);
-      q0[ja] = pa0;
-    }
-    if (vb) {
-      learn4(pb0, idb0, a);
-      q0[jb] = pb0;
-    }
-  }
-  if (has1 && learn1) {
-    if (va) {
-      learn4(pa1, ida1, a);
-      q1[ja] = pa1;
-    }
-    if (vb) {
-      learn4(pb1, idb1, a);
-      q1[jb] = pb1;
-    }
-  }
-  uint32_t n0 = 0, n1 = 0;
-  if (va) n0 += count4(pa0, ida0, a.thr, a.x);
-  if (vb) n0 += count4(pb0, idb0, a.thr, a.x);
-  if (has1 && va) n1 += count4(pa1, ida1, a.thr, a.x);
-  if (has1 && vb) n1 += count4(pb1, idb1, a.thr, a.x);
-  raw0 = __reduce_add_sync(kFull, n0);
-  raw1 = __reduce_add_sync(kFull, n1);
-}
-
 // Columns of one SP given to CTA bid of nb: a contiguous range when
 // SP_CONTIG_COLUMNS (neighbouring receptive fields share cached input
 // words), else every nb-th group of kStepWarps columns.
 #ifndef SP_CONTIG_COLUMNS
 #define SP_CONTIG_COLUMNS 1
-#endif
-#ifndef SP_PAIR_COLUMNS
-#define SP_PAIR_COLUMNS 0
 #endif
 
 #ifndef SP_STAGE_RING
@@ -548,18 +492,6 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
         if (lane == 0) publish(c_first + k * c_step, 0u);
     }
     __syncthreads();  // the rings become the last CTA's working memory
-  } else if (SP_PAIR_COLUMNS && VEC == 4 && STREAM && a.S <= 256u) {
-    for (uint32_t c = c_first; c < c_end; c += 2u * c_step) {
-      const uint32_t c1 = c + c_step;
-      const bool has1 = c1 < c_end;
-      uint32_t raw0, raw1;
-      column_overlap_pair<STREAM>(a, c, has1 ? c1 : c, has1, learning(c), has1 && learning(c1),
-                                  lane, raw0, raw1);
-      if (lane == 0) {
-        publish(c, raw0);
-        if (has1) publish(c1, raw1);
-      }
-    }
   } else {
     uint32_t xlo = 0u, xhi = 0u;
     if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.xspan) {
