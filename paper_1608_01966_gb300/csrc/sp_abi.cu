@@ -1094,8 +1094,14 @@ struct sp_batch {
   cudaEvent_t ev_switch = nullptr, ev_wait = nullptr;
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
-  // sp_batch_infer_device: per-member kernel arguments on the device
+  // sp_batch_infer_device: per-member kernel arguments on the device, staged
+  // through two pinned host halves used in turn (each reused only after the
+  // copy that read it two calls ago has run)
   void* d_infer_args = nullptr;
+  void* h_infer_args = nullptr;
+  size_t infer_half = 0;
+  int infer_turn = 0;
+  cudaEvent_t ev_infer[2] = {nullptr, nullptr};
   // sp_batch_compute staging
   uint32_t* d_stage = nullptr;
   uint32_t* d_mstage = nullptr;
@@ -1201,6 +1207,9 @@ void free_batch(sp_batch* b) {
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   if (b->d_block) cudaFree(b->d_block);
   if (b->d_infer_args) cudaFree(b->d_infer_args);
+  if (b->h_infer_args) cudaFreeHost(b->h_infer_args);
+  for (int i = 0; i < 2; ++i)
+    if (b->ev_infer[i]) cudaEventDestroy(b->ev_infer[i]);
   if (b->d_sync) cudaFree(b->d_sync);
   if (b->h_err) cudaFreeHost(b->h_err);
   for (sp_handle* h : b->members) {
@@ -1599,15 +1608,25 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
   }
   if (sp::frame_inhibit_smem(max_C, max_S) > sp::frame_inhibit_smem_limit())
     return fail(SP_ENOTSUP, "members too large for one per-frame inhibition launch");
-  if (!b->d_infer_args)
-    SP_CUDA(device_malloc((void**)&b->d_infer_args, (sizeof(sp::DenseArgs) + sizeof(sp::FrameInhibitArgs)) * n));
+  const size_t arg_bytes = (sizeof(sp::DenseArgs) + sizeof(sp::FrameInhibitArgs)) * n;
+  if (!b->d_infer_args) {
+    SP_CUDA(device_malloc((void**)&b->d_infer_args, arg_bytes));
+    b->infer_half = align256(arg_bytes);
+    SP_CUDA(cudaMallocHost(&b->h_infer_args, 2 * b->infer_half));
+    for (int i = 0; i < 2; ++i) SP_CUDA(cudaEventCreateWithFlags(&b->ev_infer[i], cudaEventDisableTiming));
+  }
   sp::DenseArgs* d_dargs = static_cast<sp::DenseArgs*>(b->d_infer_args);
   sp::FrameInhibitArgs* d_fargs = reinterpret_cast<sp::FrameInhibitArgs*>(d_dargs + n);
-  // the argument arrays go through the stream so earlier launches keep theirs
-  SP_CUDA(cudaMemcpyAsync(d_dargs, dargs.data(), sizeof(sp::DenseArgs) * n,
-                          cudaMemcpyHostToDevice, b->stream));
-  SP_CUDA(cudaMemcpyAsync(d_fargs, fargs.data(), sizeof(sp::FrameInhibitArgs) * n,
-                          cudaMemcpyHostToDevice, b->stream));
+  // the argument arrays go through the stream (earlier launches keep theirs)
+  // from a pinned half whose previous copy has completed
+  const int turn = b->infer_turn;
+  b->infer_turn ^= 1;
+  SP_CUDA(cudaEventSynchronize(b->ev_infer[turn]));
+  char* h_args = static_cast<char*>(b->h_infer_args) + (size_t)turn * b->infer_half;
+  std::memcpy(h_args, dargs.data(), sizeof(sp::DenseArgs) * n);
+  std::memcpy(h_args + sizeof(sp::DenseArgs) * n, fargs.data(), sizeof(sp::FrameInhibitArgs) * n);
+  SP_CUDA(cudaMemcpyAsync(d_dargs, h_args, arg_bytes, cudaMemcpyHostToDevice, b->stream));
+  SP_CUDA(cudaEventRecord(b->ev_infer[turn], b->stream));
   SP_CUDA(sp::launch_conn_pack(d_dargs, n, max_C, max_cw, b->stream));
   SP_CUDA(sp::launch_dense_overlap_many(d_dargs, n, max_C, n_frames, b->stream));
   SP_CUDA(sp::launch_frame_inhibit_many(d_fargs, n, max_C, max_S, n_frames, b->stream));
@@ -1617,8 +1636,6 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
       SP_CUDA(sp::launch_duty_run(fargs[i].masks_out, n_frames, (uint32_t)fargs[i].masks_stride,
                                   h->C, h->d_duty, h->cfg.duty_period, b->stream));
   }
-  // host copies of the argument arrays must outlive the asynchronous copies
-  SP_CUDA(cudaStreamSynchronize(b->stream));
   b->cur ^= 1;
   b->frames += n_frames;
   return SP_OK;
