@@ -390,7 +390,7 @@ __global__ void sp_duty_run_kernel(const uint32_t* masks, uint32_t n_frames, uin
 // Connected bits of one dense SP: word w of column c holds [perm >= thr] of
 // inputs 32w .. 32w+31 (LSB first; zero beyond K and in the padding word).
 // One warp per word: lane i reads input 32w + i (coalesced) and a ballot packs.
-__global__ void sp_conn_pack_kernel(const DenseLaunch L) {
+__global__ void __launch_bounds__(256) sp_conn_pack_kernel(const DenseLaunch L) {
   DenseArgs a;
   if (L.many)
     a = L.many[blockIdx.y];
@@ -398,8 +398,45 @@ __global__ void sp_conn_pack_kernel(const DenseLaunch L) {
     a = L.one;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (blockDim.x >> 5) * gridDim.x;
-  const uint32_t total = a.C * a.conn_words;
   const uint32_t first = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  uint32_t* conn = const_cast<uint32_t*>(a.conn);
+  if ((a.K & 3u) == 0u) {
+    // a warp takes 4 words (128 synapses) per row block: one 16-byte load per
+    // lane (4 synapses, 4 bits); 8 lanes OR their nibbles into a word; four
+    // blocks' loads are in flight together
+    const uint32_t blocks_per_row = (a.conn_words + 3u) / 4u;
+    const uint32_t total = a.C * blocks_per_row;
+    for (uint32_t b0 = first; b0 < total; b0 += 4u * warps) {
+      uint32_t nib[4];
+#pragma unroll
+      for (uint32_t q = 0; q < 4u; ++q) {
+        const uint32_t b = b0 + q * warps;
+        const uint32_t c = b / blocks_per_row, blk = b - c * blocks_per_row;
+        const uint32_t k = blk * 128u + lane * 4u;
+        nib[q] = 0u;
+        if (b < total && k < a.K) {
+          const float4 p = __ldcs(reinterpret_cast<const float4*>(a.perm + (uint64_t)c * a.K + k));
+          nib[q] = (p.x >= a.thr ? 1u : 0u) | (p.y >= a.thr ? 2u : 0u) |
+                   (p.z >= a.thr ? 4u : 0u) | (p.w >= a.thr ? 8u : 0u);
+        }
+      }
+#pragma unroll
+      for (uint32_t q = 0; q < 4u; ++q) {
+        const uint32_t b = b0 + q * warps;
+        uint32_t word = nib[q] << (4u * (lane & 7u));
+        word |= __shfl_xor_sync(kFull, word, 1);
+        word |= __shfl_xor_sync(kFull, word, 2);
+        word |= __shfl_xor_sync(kFull, word, 4);
+        if (b < total && (lane & 7u) == 0u) {
+          const uint32_t c = b / blocks_per_row, blk = b - c * blocks_per_row;
+          const uint32_t w = blk * 4u + (lane >> 3);
+          if (w < a.conn_words) conn[(uint64_t)c * a.conn_words + w] = word;
+        }
+      }
+    }
+    return;
+  }
+  const uint32_t total = a.C * a.conn_words;
   // four words per round, their loads issued together
   for (uint32_t gw0 = first; gw0 < total; gw0 += 4u * warps) {
     bool on[4];
@@ -414,7 +451,7 @@ __global__ void sp_conn_pack_kernel(const DenseLaunch L) {
     for (uint32_t q = 0; q < 4u; ++q) {
       const uint32_t gw = gw0 + q * warps;
       const uint32_t bits = __ballot_sync(kFull, on[q]);
-      if (lane == 0 && gw < total) const_cast<uint32_t*>(a.conn)[gw] = bits;
+      if (lane == 0 && gw < total) conn[gw] = bits;
     }
   }
 }
@@ -423,8 +460,8 @@ __global__ void sp_conn_pack_kernel(const DenseLaunch L) {
 
 cudaError_t launch_conn_pack(const DenseArgs* args, uint32_t n, uint32_t max_C,
                              uint32_t max_conn_words, cudaStream_t stream) {
-  const uint32_t words = max_C * max_conn_words;  // one warp each, 8 warps per CTA
-  const dim3 grid(std::min<uint32_t>((words + 7u) / 8u, 1024u), n, 1);
+  const uint32_t words = max_C * max_conn_words;  // 8 warps per CTA, 16 words per warp-round
+  const dim3 grid(std::max<uint32_t>(1u, std::min<uint32_t>((words + 127u) / 128u, 64u)), n, 1);
   DenseLaunch L{args, DenseArgs{}};
   sp_conn_pack_kernel<<<grid, 256, 0, stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -434,7 +471,7 @@ cudaError_t launch_conn_pack(const DenseArgs* args, uint32_t n, uint32_t max_C,
 cudaError_t launch_conn_pack_one(const DenseArgs& a, cudaStream_t stream) {
   const uint32_t words = a.C * a.conn_words;
   DenseLaunch L{nullptr, a};
-  sp_conn_pack_kernel<<<std::min<uint32_t>((words + 7u) / 8u, 1024u), 256, 0, stream>>>(L);
+  sp_conn_pack_kernel<<<std::max<uint32_t>(1u, std::min<uint32_t>((words + 127u) / 128u, 608u)), 256, 0, stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

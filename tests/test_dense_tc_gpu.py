@@ -118,7 +118,7 @@ def test_dense_run_after_learning_uses_learned_state():
 def test_batch_of_dense_sps_infers_in_two_launches():
     """Dense SPs of different shapes in one batch: all overlaps in one
     tensor-core launch, Alg. 2 for every frame and SP in one more."""
-    shapes = [(1024, 1024), (300, 500), (700, 2048), (1024, 1024)]
+    shapes = [(1024, 1024), (300, 500), (700, 2048), (257, 999), (1024, 1024)]
     cases = [_dense_case(C, n, 50 + i, k=max(1, (2 * C + 50) // 100))
              for i, (C, n) in enumerate(shapes)]
     F = 130
