@@ -56,7 +56,7 @@ ALU_TOPS = 152 * 128 * 2.07e9 / 1e12  # int32 lane operations per second, in T
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--instances", type=int, default=INSTANCES)
