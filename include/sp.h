@@ -403,6 +403,17 @@ SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t*
                                        const uint32_t* const* frames, const int* learn,
                                        uint64_t* request_ids, sp_status* statuses);
 
+/* sp_server_submit_many for frames already on the device (d_frames[i]: the
+ * stream's input_words words, 4-byte aligned): each is copied into the
+ * stream's queue on `stream` (a cudaStream_t; NULL = legacy default), so
+ * work the caller queued earlier on `stream` (say, an encoder producing the
+ * frame) is finished first, and the caller may reuse its buffer once
+ * `stream` has passed the call.  Statuses as for sp_server_submit_many. */
+SP_API sp_status sp_server_submit_many_device(sp_server* s, uint32_t n, const uint32_t* stream_ids,
+                                              const uint32_t* const* d_frames, const int* learn,
+                                              uint64_t* request_ids, sp_status* statuses,
+                                              void* stream);
+
 /* Take up to max_results finished frames (oldest first), their active lists
  * copied into active[0..active_cap); waits up to wait_ms for the first one.
  * *n_results may be 0.  Results whose lists do not fit stay queued. */

@@ -11,8 +11,8 @@ from ._binding import (  # noqa: F401
     sp_compute_frames_device, sp_config_init, sp_create, sp_create_from_state, sp_destroy,
     sp_get_boost, sp_get_duty_cycles, sp_get_info, sp_get_overlaps, sp_get_permanences, sp_get_pool,
     sp_kernel_launch_count, sp_last_error, sp_load, sp_save, sp_set_boost, sp_set_timeout_ms, sp_status_str,
-    sp_server_close_stream, sp_server_create, sp_server_destroy, sp_server_get_permanences,
-    sp_server_get_stats, sp_server_open_stream, sp_server_poll, sp_server_submit, sp_server_submit_many, sp_server_submit_many_ptrs,
+    sp_server_close_stream, sp_server_create, sp_server_drain, sp_server_destroy, sp_server_get_permanences,
+    sp_server_get_stats, sp_server_open_stream, sp_server_poll, sp_server_submit, sp_server_submit_many, sp_server_submit_many_device, sp_server_submit_many_ptrs,
     sp_step_noalloc, sp_sync,
     SpEncoderConfig, sp_encode_compute, sp_encode_compute_device, sp_encode_device,
     sp_encoder_config_init, sp_encoder_create, sp_encoder_destroy, sp_encoder_get_info,

@@ -153,6 +153,10 @@ def lib():
         L.sp_server_submit_many.argtypes = [vp, ct.c_uint32, _u32p, ct.POINTER(vp),
                                             ct.POINTER(ct.c_int), ct.POINTER(ct.c_uint64),
                                             ct.POINTER(ct.c_int)]
+        L.sp_server_submit_many_device.argtypes = [vp, ct.c_uint32, _u32p, ct.POINTER(vp),
+                                                   ct.POINTER(ct.c_int),
+                                                   ct.POINTER(ct.c_uint64),
+                                                   ct.POINTER(ct.c_int), vp]
         L.sp_server_poll.argtypes = [vp, ct.POINTER(SpServerResult), ct.c_uint32, _u32p,
                                      ct.c_uint32, _u32p, ct.c_uint32]
         L.sp_server_get_permanences.argtypes = [vp, ct.c_uint32, _f32p]
@@ -480,6 +484,25 @@ def sp_server_submit_many_ptrs(srv, stream_ids, frame_ptrs, learn):
     return st, rid
 
 
+def sp_server_submit_many_device(srv, stream_ids, d_frame_ptrs, learn, stream=None):
+    """sp_server_submit_many for device frames: stream ids (uint32), device
+    addresses of the frames (uint64) and learn flags (int32); the copies run
+    on `stream` (torch stream or handle; None = legacy default).
+    Returns (statuses, request ids)."""
+    n = len(stream_ids)
+    ids = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+    ptrs = np.ascontiguousarray(d_frame_ptrs, dtype=np.uint64)
+    larr = np.ascontiguousarray(learn, dtype=np.int32)
+    rid = np.zeros(n, np.uint64)
+    st = np.zeros(n, np.int32)
+    _check(lib().sp_server_submit_many_device(
+        srv, n, ids.ctypes.data_as(_u32p), ptrs.ctypes.data_as(ct.POINTER(ct.c_void_p)),
+        larr.ctypes.data_as(ct.POINTER(ct.c_int)), rid.ctypes.data_as(ct.POINTER(ct.c_uint64)),
+        st.ctypes.data_as(ct.POINTER(ct.c_int)), _stream(stream) or CUDA_STREAM_LEGACY),
+        "sp_server_submit_many_device")
+    return st, rid
+
+
 def sp_server_poll(s, max_results=256, active_cap=1 << 16, wait_ms=0):
     """Returns a list of (result dict, active ndarray)."""
     res = (SpServerResult * max_results)()
@@ -493,6 +516,24 @@ def sp_server_poll(s, max_results=256, active_cap=1 << 16, wait_ms=0):
         d = {f: getattr(r, f) for f, _ in SpServerResult._fields_}
         out.append((d, act[r.active_offset:r.active_offset + r.n_active].copy()))
     return out
+
+
+_drain_bufs = {}
+
+
+def sp_server_drain(s, wait_ms=0, max_results=4096, active_cap=1 << 18):
+    """Take up to max_results finished frames without building per-result
+    objects (latency percentiles stay available from sp_server_get_stats).
+    Returns (frames taken, frames whose status was not SP_OK)."""
+    key = (max_results, active_cap)
+    if key not in _drain_bufs:
+        _drain_bufs[key] = ((SpServerResult * max_results)(), np.zeros(active_cap, np.uint32))
+    res, act = _drain_bufs[key]
+    n = ct.c_uint32()
+    _check(lib().sp_server_poll(s, res, max_results, act.ctypes.data_as(_u32p), active_cap,
+                                ct.byref(n), wait_ms), "sp_server_poll")
+    bad = sum(1 for i in range(n.value) if res[i].status != 0) if n.value else 0
+    return n.value, bad
 
 
 def sp_server_get_permanences(s, sid, shape):

@@ -639,7 +639,7 @@ bool handle_compact(sp_handle* h) {
   return wide == 0;
 }
 
-void fill_desc(sp_handle* h, sp::BatchDesc* d) {
+void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp) {
   *d = sp::BatchDesc{};
   d->idx = h->d_idx;
   d->perm = h->d_perm;
@@ -667,7 +667,7 @@ void fill_desc(sp_handle* h, sp::BatchDesc* d) {
   d->gw = h->cfg.col_grid_w;
   d->gh = h->cfg.col_grid_h;
   d->radius = h->cfg.local_radius;
-  d->n_ctas = batch_ctas(h->C, h->S);
+  d->n_ctas = batch_ctas(h->C, h->S, cols_per_warp);
   d->xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d->n_ctas) : nullptr;
   if (handle_compact(h)) {
     d->cidx = h->d_cidx;
@@ -1078,7 +1078,6 @@ struct sp_batch {
   uint32_t n_ctas = 0, max_C = 0;
   std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
   void* d_sync = nullptr;             // persistent launches: work counter, abort, done[n]
-  uint32_t run_epoch = 0;             // frames issued by persistent launches (done flags)
   uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
@@ -1279,16 +1278,17 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.cur0 = (uint32_t)b->cur;
     r.pending0 = b->pending ? 1u : 0u;
     r.learn = learn ? 1u : 0u;
-    r.epoch = b->run_epoch;
+    r.epoch = 0u;
     r.work = static_cast<unsigned long long*>(b->d_sync);
     r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
     r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
     r.err = b->d_err;
     r.stage_cap = b->stage_cap;
     r.xspan_cap = b->xspan_cap;
-    SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16, b->stream));
+    // counter, abort word and done flags start at 0 in every launch, so a
+    // launch recorded into a graph and replayed sees no stale flags
+    SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
     SP_CUDA(sp::launch_batch_run(r, b->max_C, b->stream));
-    b->run_epoch += n;
     b->pending = learn != 0;
     b->cur ^= (int)(n & 1u);
     b->frames += n;
@@ -1730,16 +1730,15 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         r.frames = d_frames;
         r.stride = stride;
         r.cur0 = (uint32_t)b->cur;
-        r.epoch = b->run_epoch;
+        r.epoch = 0u;
         r.work = static_cast<unsigned long long*>(b->d_sync);
         r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
         r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
         r.err = b->d_err;
         r.stage_cap = b->stage_cap;
         r.xspan_cap = b->xspan_cap;
-        e = cudaMemsetAsync(b->d_sync, 0, 16, b->stream);
+        e = cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream);
         if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->stream);
-        b->run_epoch += n_frames;
       } else {
         for (uint32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
           sp::BatchArgs a{};

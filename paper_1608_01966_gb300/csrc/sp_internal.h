@@ -67,7 +67,7 @@ sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
 uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp = 0);
 uint32_t batch_stage_cap(uint32_t need);
-void fill_desc(sp_handle* h, sp::BatchDesc* d);
+void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp = 0);
 uint32_t batch_xspan_cap();
 
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames

@@ -83,7 +83,7 @@ struct BatchRunArgs {
   uint32_t* masks_out;          // batch mask record t at masks_out + t * mstride (nullable)
   uint64_t mstride;
   uint32_t cur0, pending0, learn;  // parity and pending learning before frame 0
-  uint32_t epoch;               // frames the batch completed before this launch
+  uint32_t epoch;               // base of the done values (0: flags cleared per launch)
   unsigned long long* work;     // item counter, 0 at launch
   uint32_t* abort;              // 0 at launch; set when a wait gives up
   uint32_t* done;               // per SP: epoch + t + 1 once frame t is complete

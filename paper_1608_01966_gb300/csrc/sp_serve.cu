@@ -16,6 +16,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -28,6 +29,7 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 constexpr int kLaunchSlots = 2;
+constexpr uint32_t kServeColsPerWarp = 4;
 constexpr uint32_t kMaxServerStreams = 4096;
 
 struct Request {
@@ -36,6 +38,8 @@ struct Request {
   uint32_t ring;  // ring slot of its frame
   bool learn;
   Clock::time_point t_submit;
+  bool copied = true;  // false: its frame could not be copied (failed, never launched)
+  bool device = false;  // copied on a caller's stream: the launch waits for its event
 };
 
 struct Stream {
@@ -48,10 +52,11 @@ struct Stream {
   std::deque<Request> queue;   // submitted, not yet launched
   uint32_t outstanding = 0;    // queued + in flight (ring slots in use)
   uint32_t head = 0;           // next ring slot
-  bool in_flight = false;
+  uint32_t in_flight = 0;      // launches holding a frame of this stream (at most 2)
   int cur = 0;
   bool pending = false;
-  uint64_t next_seq = 0;
+  uint64_t next_seq = 0;       // next sequence number to reserve
+  uint64_t launch_seq = 0;     // the request that may launch next
   uint32_t n_ctas = 0, max_active = 0, input_words = 0;
   uint32_t stage_bytes = 0;    // shared memory to stage its CTAs' state
 };
@@ -73,6 +78,8 @@ struct LaunchSlot {
   uint32_t* d_results = nullptr;
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
   uint32_t* d_err = nullptr;
+  cudaEvent_t copies = nullptr;       // host frame copies issued before this launch
+  uint64_t launch_no = 0;             // order of the launches (results are delivered in it)
   std::vector<std::pair<uint32_t, Request>> members;  // (slot, request)
 };
 
@@ -131,7 +138,7 @@ void finish_launch(sp_server* s, LaunchSlot& L, sp_status st) {
     d.active.assign(res + 1, res + 1 + n);
     s->lat_us.push_back(d.r.latency_us);
     s->done.push_back(std::move(d));
-    S.in_flight = false;
+    S.in_flight -= 1;
     S.outstanding -= 1;
     ++pos;
     ++s->completed;
@@ -140,18 +147,41 @@ void finish_launch(sp_server* s, LaunchSlot& L, sp_status st) {
   L.busy = false;
 }
 
-// Form and enqueue one launch from the waiting streams (caller holds mu).
-sp_status start_launch(sp_server* s, LaunchSlot& L) {
+// Form and enqueue one launch from the waiting streams (caller holds mu).  A
+// stream whose previous frame is still in the other slot's launch may take
+// part: this launch then waits on the GPU for that one.
+sp_status start_launch(sp_server* s, LaunchSlot& L, const LaunchSlot& other) {
+  bool chained = false, host_copies = false;
   const uint32_t n = (uint32_t)s->streams.size();
   const uint32_t row = 1u + s->cfg.max_active;
   uint32_t ctas = 0, count = 0;
   for (uint32_t k = 0; k < n; ++k) {
     const uint32_t i = (s->rr + k) % n;
     Stream& S = s->streams[i];
-    if (!S.open || S.in_flight || S.queue.empty()) continue;
+    // a request whose frame could not be copied fails without a launch
+    while (!S.queue.empty() && S.queue.front().seq == S.launch_seq &&
+           !S.queue.front().copied) {
+      const Request& bad = S.queue.front();
+      Done d;
+      d.r.request_id = bad.id;
+      d.r.frame_seq = bad.seq;
+      d.r.stream_id = i;
+      d.r.status = SP_ECUDA;
+      d.r.latency_us = 0.0;
+      s->done.push_back(std::move(d));
+      S.queue.pop_front();
+      S.launch_seq += 1;
+      S.outstanding -= 1;
+      ++s->completed;
+    }
+    // requests launch in sequence order; one still being copied holds back
+    // the ones after it
+    if (!S.open || S.in_flight >= 2u || S.queue.empty() || S.queue.front().seq != S.launch_seq)
+      continue;
     if (ctas + S.n_ctas > s->max_ctas) break;
     Request r = S.queue.front();
     S.queue.pop_front();
+    S.launch_seq += 1;
     sp::TickMember& tm = L.h_table[i];
     tm.x = S.d_ring + (size_t)r.ring * S.input_words;
     tm.flags = (S.cur ? sp::kTickCur : 0u) | (S.pending ? sp::kTickPending : 0u) |
@@ -160,15 +190,27 @@ sp_status start_launch(sp_server* s, LaunchSlot& L) {
     tm.out_off = count * row;
     for (uint32_t c = 0; c < S.n_ctas; ++c) L.h_cta[ctas + c] = i;
     ctas += S.n_ctas;
-    S.in_flight = true;
+    chained = chained || S.in_flight > 0u;
+    S.in_flight += 1;
     S.pending = r.learn;
     S.cur ^= 1;
     L.members.emplace_back(i, r);
     ++count;
-    // the launch waits for this frame's copy
-    SP_CUDA(cudaStreamWaitEvent(L.st, S.ev_h2d[r.ring], 0));
+    // the launch waits for this frame's copy: frames copied on a caller's
+    // stream one by one, host frames all at once below
+    if (r.device)
+      SP_CUDA(cudaStreamWaitEvent(L.st, S.ev_h2d[r.ring], 0));
+    else
+      host_copies = true;
   }
   if (count == 0) return SP_OK;
+  if (host_copies) {
+    // every published host frame's copy was issued on the copy stream before
+    // its request was published
+    SP_CUDA(cudaEventRecord(L.copies, s->copy_stream));
+    SP_CUDA(cudaStreamWaitEvent(L.st, L.copies, 0));
+  }
+  if (chained) SP_CUDA(cudaStreamWaitEvent(L.st, other.done, 0));
   s->rr = (s->rr + 1) % n;
   SP_CUDA(cudaMemcpyAsync(L.d_table, L.h_table, sizeof(sp::TickMember) * n,
                           cudaMemcpyHostToDevice, L.st));
@@ -191,7 +233,7 @@ sp_status start_launch(sp_server* s, LaunchSlot& L) {
                           cudaMemcpyDeviceToHost, L.st));
   SP_CUDA(cudaEventRecord(L.done, L.st));
   L.busy = true;
-  ++s->launches;
+  L.launch_no = ++s->launches;
   s->frames_launched += count;
   return SP_OK;
 }
@@ -202,23 +244,28 @@ void worker_main(sp_server* s) {
   uint32_t idle_spins = 0;
   while (!s->stop.load()) {
     bool progress = false;
-    for (auto& L : s->slots) {
-      if (!L.busy) continue;
-      const cudaError_t e = cudaEventQuery(L.done);
-      if (e == cudaErrorNotReady) continue;
+    // deliver finished launches oldest first: a stream's frames can be in both
+    for (int pass = 0; pass < kLaunchSlots; ++pass) {
+      LaunchSlot* oldest = nullptr;
+      for (auto& L : s->slots)
+        if (L.busy && (!oldest || L.launch_no < oldest->launch_no)) oldest = &L;
+      if (!oldest) break;
+      const cudaError_t e = cudaEventQuery(oldest->done);
+      if (e == cudaErrorNotReady) break;
       sp_status st = e == cudaSuccess ? SP_OK : SP_ECUDA;
-      if (st == SP_OK && *reinterpret_cast<volatile uint32_t*>(L.h_err)) {
-        *L.h_err = 0u;
+      if (st == SP_OK && *reinterpret_cast<volatile uint32_t*>(oldest->h_err)) {
+        *oldest->h_err = 0u;
         st = SP_ETIMEOUT;
       }
-      finish_launch(s, L, st);
+      finish_launch(s, *oldest, st);
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
-    for (auto& L : s->slots) {
+    for (int li = 0; li < kLaunchSlots; ++li) {
+      LaunchSlot& L = s->slots[li];
       if (L.busy) continue;
       const uint64_t before = s->launches;
-      const sp_status st = start_launch(s, L);
+      const sp_status st = start_launch(s, L, s->slots[(li + 1) % kLaunchSlots]);
       if (st != SP_OK) {
         // the members of a launch that could not be enqueued fail
         finish_launch(s, L, st);
@@ -232,9 +279,10 @@ void worker_main(sp_server* s) {
       continue;
     }
     if (in_flight) {
-      // poll the launches in flight: short spins, then short sleeps
+      // poll the launches in flight: yield for a few milliseconds (a launch
+      // takes tens of microseconds; a sleep would overshoot it), then sleep
       lk.unlock();
-      if (++idle_spins < 64)
+      if (++idle_spins < 20000)
         std::this_thread::yield();
       else
         std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -275,6 +323,7 @@ void free_server(sp_server* s) {
     if (L.h_cta) cudaFreeHost(L.h_cta);
     if (L.h_results) cudaFreeHost(L.h_results);
     if (L.h_err) cudaFreeHost(L.h_err);
+    if (L.copies) cudaEventDestroy(L.copies);
     if (L.d_table) cudaFree(L.d_table);
     if (L.d_cta) cudaFree(L.d_cta);
     if (L.d_results) cudaFree(L.d_results);
@@ -312,7 +361,9 @@ sp_status admit(sp_server* s, sp_handle* h, uint32_t* stream_id) {
   S.input_words = info.input_words;
   S.max_active = info.max_active;
   sp::BatchDesc d;
-  fill_desc(h, &d);
+  // a launch carries one frame of a few tens of streams: small CTAs (16
+  // columns) keep every SM busy and the latency low
+  fill_desc(h, &d, kServeColsPerWarp);
   S.n_ctas = d.n_ctas;
   S.stage_bytes = sp::batch_stage_bytes(h->C, h->S, d.n_ctas);
   const size_t ring_bytes = (size_t)s->cfg.queue_depth * info.input_words * 4;
@@ -392,7 +443,7 @@ SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out) 
   s->cfg = *cfg;
   cudaGetDevice(&s->device);
   s->streams.resize(cfg->max_streams);
-  s->max_ctas = cfg->max_streams * batch_ctas(SP_MAX_COLUMNS, 128u);  // the largest share
+  s->max_ctas = cfg->max_streams * batch_ctas(SP_MAX_COLUMNS, 128u, kServeColsPerWarp);  // the largest share
   const uint32_t row = 1u + cfg->max_active;
   cudaError_t e = sp::kernels_init();
   if (e == cudaSuccess) e = device_malloc((void**)&s->d_desc, sizeof(sp::BatchDesc) * cfg->max_streams);
@@ -406,6 +457,7 @@ SP_API sp_status sp_server_create(const sp_server_config* cfg, sp_server** out) 
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_table, sizeof(sp::TickMember) * cfg->max_streams);
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_cta, (size_t)s->max_ctas * 4);
     if (e == cudaSuccess) e = device_malloc((void**)&L.d_results, (size_t)cfg->max_streams * row * 4);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.copies, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&L.h_err, 4, cudaHostAllocMapped);
     if (e == cudaSuccess) {
       *L.h_err = 0u;
@@ -464,37 +516,60 @@ SP_API sp_status sp_server_close_stream(sp_server* s, uint32_t id) {
   return SP_OK;
 }
 
+namespace {
+
+// One frame being submitted: its slot and sequence number are reserved under
+// the lock, its copies are made without it, and it is published under the
+// lock again in sequence order, so the worker never waits for a copy.
+struct Pending {
+  uint32_t entry, stream, ring;
+  uint64_t seq;
+  bool learn;
+  bool device;
+};
+
+void publish(sp_server* s, const std::vector<Pending>& ps, const std::vector<bool>& copied,
+             const Clock::time_point t, uint64_t* request_ids) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (size_t k = 0; k < ps.size(); ++k) {
+    Stream& S = s->streams[ps[k].stream];
+    Request r{s->next_id++, ps[k].seq, ps[k].ring, ps[k].learn, t, copied[k], ps[k].device};
+    auto it = S.queue.end();
+    while (it != S.queue.begin() && std::prev(it)->seq > r.seq) --it;
+    S.queue.insert(it, r);
+    ++s->submitted;
+    if (request_ids) request_ids[ps[k].entry] = r.id;
+  }
+}
+
+}  // namespace
+
 SP_API sp_status sp_server_submit(sp_server* s, uint32_t id, const uint32_t* bits, int learn,
                                   uint64_t* request_id) {
   if (!s || !bits) return fail(SP_EINVAL, "NULL argument");
-  DeviceGuard g(s->device);
-  std::unique_lock<std::mutex> lk(s->mu);
-  if (id >= s->streams.size() || !s->streams[id].open) return fail(SP_EINVAL, "stream %u is not open", id);
-  Stream& S = s->streams[id];
-  if (S.outstanding >= s->cfg.queue_depth) return fail(SP_EBUSY, "stream %u queue is full", id);
-  const uint32_t ring = S.head;
-  S.head = (S.head + 1) % s->cfg.queue_depth;
-  uint32_t* hs = S.h_ring + (size_t)ring * S.input_words;
-  std::memcpy(hs, bits, (size_t)S.input_words * 4);
-  SP_CUDA(cudaMemcpyAsync(S.d_ring + (size_t)ring * S.input_words, hs, (size_t)S.input_words * 4,
-                          cudaMemcpyHostToDevice, s->copy_stream));
-  SP_CUDA(cudaEventRecord(S.ev_h2d[ring], s->copy_stream));
-  Request r{s->next_id++, S.next_seq++, ring, learn != 0, Clock::now()};
-  S.queue.push_back(r);
-  S.outstanding += 1;
-  ++s->submitted;
-  if (request_id) *request_id = r.id;
-  lk.unlock();
-  s->cv_work.notify_one();
+  const int lf = learn != 0 ? 1 : 0;
+  sp_status st = SP_OK;
+  uint64_t rid = 0;
+  const sp_status call = sp_server_submit_many(s, 1, &id, &bits, &lf, &rid, &st);
+  if (call != SP_OK) return call;
+  if (st == SP_EINVAL) return fail(SP_EINVAL, "stream %u is not open", id);
+  if (st == SP_EBUSY) return fail(SP_EBUSY, "stream %u queue is full", id);
+  if (st != SP_OK) return fail(st, "copying the frame of stream %u failed", id);
+  if (request_id) *request_id = rid;
   return SP_OK;
 }
 
-SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t* ids,
-                                       const uint32_t* const* frames, const int* learn,
-                                       uint64_t* request_ids, sp_status* statuses) {
+namespace {
+
+// Reserve, copy (host frames through the pinned ring on the copy stream, or
+// device frames on the caller's stream), publish.
+sp_status submit_impl(sp_server* s, uint32_t n, const uint32_t* ids,
+                      const uint32_t* const* frames, const int* learn, uint64_t* request_ids,
+                      sp_status* statuses, bool device, cudaStream_t cst) {
   if (!s || (n && (!ids || !frames || !statuses))) return fail(SP_EINVAL, "NULL argument");
   DeviceGuard g(s->device);
-  uint32_t queued = 0;
+  std::vector<Pending> ps;
+  ps.reserve(n);
   {
     std::unique_lock<std::mutex> lk(s->mu);
     for (uint32_t i = 0; i < n; ++i) {
@@ -510,27 +585,53 @@ SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t*
         statuses[i] = SP_EBUSY;
         continue;
       }
-      const uint32_t ring = S.head;
-      uint32_t* hs = S.h_ring + (size_t)ring * S.input_words;
-      std::memcpy(hs, frames[i], (size_t)S.input_words * 4);
-      if (cudaMemcpyAsync(S.d_ring + (size_t)ring * S.input_words, hs,
-                          (size_t)S.input_words * 4, cudaMemcpyHostToDevice,
-                          s->copy_stream) != cudaSuccess ||
-          cudaEventRecord(S.ev_h2d[ring], s->copy_stream) != cudaSuccess) {
-        statuses[i] = SP_ECUDA;
-        continue;
-      }
+      ps.push_back(Pending{i, id, S.head, S.next_seq++, learn && learn[i] != 0, device});
       S.head = (S.head + 1) % s->cfg.queue_depth;
-      Request r{s->next_id++, S.next_seq++, ring, learn && learn[i] != 0, Clock::now()};
-      S.queue.push_back(r);
-      S.outstanding += 1;
-      ++s->submitted;
-      if (request_ids) request_ids[i] = r.id;
-      ++queued;
+      S.outstanding += 1;  // the slot stays reserved until its frame is done
     }
   }
-  if (queued) s->cv_work.notify_one();
+  if (ps.empty()) return SP_OK;
+  const Clock::time_point t = Clock::now();
+  std::vector<bool> copied(ps.size(), true);
+  for (size_t k = 0; k < ps.size(); ++k) {
+    // the stream cannot close while it has a reserved slot (outstanding > 0)
+    Stream& S = s->streams[ps[k].stream];
+    uint32_t* dst = S.d_ring + (size_t)ps[k].ring * S.input_words;
+    cudaError_t e;
+    if (device) {
+      e = cudaMemcpyAsync(dst, frames[ps[k].entry], (size_t)S.input_words * 4,
+                          cudaMemcpyDeviceToDevice, cst);
+      if (e == cudaSuccess) e = cudaEventRecord(S.ev_h2d[ps[k].ring], cst);
+    } else {
+      uint32_t* hs = S.h_ring + (size_t)ps[k].ring * S.input_words;
+      std::memcpy(hs, frames[ps[k].entry], (size_t)S.input_words * 4);
+      e = cudaMemcpyAsync(dst, hs, (size_t)S.input_words * 4, cudaMemcpyHostToDevice,
+                          s->copy_stream);
+    }
+    if (e != cudaSuccess) {
+      copied[k] = false;
+      statuses[ps[k].entry] = SP_ECUDA;
+    }
+  }
+  publish(s, ps, copied, t, request_ids);
+  s->cv_work.notify_one();
   return SP_OK;
+}
+
+}  // namespace
+
+SP_API sp_status sp_server_submit_many(sp_server* s, uint32_t n, const uint32_t* ids,
+                                       const uint32_t* const* frames, const int* learn,
+                                       uint64_t* request_ids, sp_status* statuses) {
+  return submit_impl(s, n, ids, frames, learn, request_ids, statuses, false, nullptr);
+}
+
+SP_API sp_status sp_server_submit_many_device(sp_server* s, uint32_t n, const uint32_t* ids,
+                                              const uint32_t* const* d_frames, const int* learn,
+                                              uint64_t* request_ids, sp_status* statuses,
+                                              void* stream) {
+  return submit_impl(s, n, ids, d_frames, learn, request_ids, statuses, true,
+                     static_cast<cudaStream_t>(stream));
 }
 
 SP_API sp_status sp_server_poll(sp_server* s, sp_server_result* results, uint32_t max_results,

@@ -137,25 +137,61 @@ def run_closed_loop(srv, sids, res, pools, seconds):
             if not ok.any():
                 time.sleep(0)
 
-    lat = []
+    return _saturate(srv, producer, stop, seconds)
+
+
+def _saturate(srv, producer, stop, seconds):
+    """Run `producer` in a thread for `seconds` while results are drained
+    (no per-result Python objects); latency percentiles from the server."""
     th = threading.Thread(target=producer, daemon=True)
     spg.sp_server_get_stats(srv, reset=True)
+    taken = bad = 0
     t0 = time.perf_counter()
     th.start()
     while time.perf_counter() - t0 < seconds:
-        for r, _ in spg.sp_server_poll(srv, max_results=1024, wait_ms=10):
-            lat.append(r["latency_us"])
+        n, b = spg.sp_server_drain(srv, wait_ms=10)
+        taken += n
+        bad += b
     elapsed = time.perf_counter() - t0
+    st = spg.sp_server_get_stats(srv)
     stop.set()
     th.join()
-    while True:  # drain
-        got = spg.sp_server_poll(srv, max_results=1024, wait_ms=100)
-        if not got:
-            break
-    lat = np.array(lat)
-    return {"frames": int(lat.size), "seconds": elapsed, "frames_per_s": lat.size / elapsed,
-            "p50_ms": float(np.percentile(lat, 50)) / 1000 if lat.size else None,
-            "p99_ms": float(np.percentile(lat, 99)) / 1000 if lat.size else None}
+    while spg.sp_server_drain(srv, wait_ms=100)[0]:
+        pass
+    return {"frames": taken, "errors": bad, "seconds": elapsed, "frames_per_s": taken / elapsed,
+            "p50_ms": st["p50_us"] / 1000, "p99_ms": st["p99_us"] / 1000}
+
+
+def run_closed_loop_device(srv, sids, res, pools, seconds):
+    """Saturation with frames already on the device (as an on-GPU decoder and
+    the frame encoder would leave them): one producer offers every stream's
+    next frame per sp_server_submit_many_device call."""
+    import torch
+    stop = threading.Event()
+    n = len(sids)
+    depth = min(p.shape[0] for p in pools.values())
+    d_pools = {k: torch.from_numpy(v[:depth].view(np.int32)).cuda() for k, v in pools.items()}
+    ptr = np.array([[d_pools[res[i]][j].data_ptr() for j in range(depth)] for i in range(n)],
+                   dtype=np.uint64)
+    ids = np.asarray(sids, dtype=np.uint32)
+    learn = np.ones(n, np.int32)
+    rows = np.arange(n)
+    torch.cuda.synchronize()
+
+    def producer():
+        seq = np.zeros(n, np.int64)
+        while not stop.is_set():
+            st, _ = spg.sp_server_submit_many_device(srv, ids, ptr[rows, seq % depth], learn)
+            ok = st == 0
+            if not ((st == 0) | (st == 5)).all():
+                raise spg.SpError(int(st[~ok & (st != 5)][0]), "sp_server_submit_many_device", "")
+            seq += ok
+            if not ok.any():
+                time.sleep(0)
+
+    out = _saturate(srv, producer, stop, seconds)
+    out["frames_from"] = "device"
+    return out
 
 
 def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=5.0, seed=0x5EED0005,
@@ -171,6 +207,8 @@ def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=5.0, seed=0x5E
                "open_loop": run_open_loop(srv, sids, res, pools, seconds, fps, seed)}
         if saturate_seconds > 0:
             out["closed_loop"] = run_closed_loop(srv, sids, res, pools, saturate_seconds)
+            out["closed_loop_device_frames"] = run_closed_loop_device(srv, sids, res, pools,
+                                                                      saturate_seconds)
         st = spg.sp_server_get_stats(srv)
         out["launches"] = st["launches"]
         out["frames_per_launch"] = st["frames_in_launches"] / max(1, st["launches"])

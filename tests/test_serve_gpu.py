@@ -155,10 +155,12 @@ def test_duty_cycles_match_the_oracle():
     spg.sp_destroy(h)
 
 
-def test_submit_many_matches_the_oracle():
-    """Frames offered for every stream at once (sp_server_submit_many), full
+@pytest.mark.parametrize("device", [False, True])
+def test_submit_many_matches_the_oracle(device):
+    """Frames offered for every stream at once (sp_server_submit_many, or
+    sp_server_submit_many_device with the frames already on the GPU), full
     queues refusing and the frame offered again next round: every stream's
-    results and permanences equal the oracle's."""
+    results and permanences equal the oracle's, in order."""
     n, F = 5, 12
     cases, frames = _streams(n, F)
     learn = [[(t + i) % 5 != 4 for t in range(F)] for i in range(n)]
@@ -168,15 +170,23 @@ def test_submit_many_matches_the_oracle():
     sids = [spg.sp_server_open_stream(srv, c.config(), state=(c.idx, c.perm, c.boost))
             for c in cases]
     packed = [wl.pack(f) for f in frames]
+    d_packed = [torch.from_numpy(p.view(np.int32)).cuda() for p in packed]
+    torch.cuda.synchronize()
     nxt = [0] * n
     got = {i: {} for i in range(n)}
+    seqs = {i: [] for i in range(n)}
     done, deadline = 0, time.time() + 60
     while done < n * F and time.time() < deadline:
         todo = [i for i in range(n) if nxt[i] < F]
-        if todo:
+        if todo and device:
+            st, rid = spg.sp_server_submit_many_device(
+                srv, [sids[i] for i in todo], [d_packed[i][nxt[i]].data_ptr() for i in todo],
+                [learn[i][nxt[i]] for i in todo], torch.cuda.current_stream())
+        elif todo:
             st, rid = spg.sp_server_submit_many(srv, [sids[i] for i in todo],
                                                 [packed[i][nxt[i]] for i in todo],
                                                 [learn[i][nxt[i]] for i in todo])
+        if todo:
             for j, i in enumerate(todo):
                 assert st[j] in (0, 5)
                 if st[j] == 0:
@@ -184,9 +194,13 @@ def test_submit_many_matches_the_oracle():
                     nxt[i] += 1
         for r, act in spg.sp_server_poll(srv, wait_ms=1):
             assert r["status"] == 0
-            got[sids.index(r["stream_id"])][r["frame_seq"]] = act
+            i = sids.index(r["stream_id"])
+            got[i][r["frame_seq"]] = act
+            seqs[i].append(r["frame_seq"])
             done += 1
     assert done == n * F
+    for i in range(n):
+        assert seqs[i] == list(range(F)), f"stream {i} results out of order"
     # an unknown stream is refused per entry, not for the call
     st, _ = spg.sp_server_submit_many(srv, [999], [packed[0][0]], True)
     assert st[0] == 1
