@@ -229,21 +229,26 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
       __syncthreads();
     }
     const uint32_t ws = (k0 % kSuperK) >> 5;  // word of this slice in the slab
-    // ---- expand: one 16-byte unit = 8 bf16 of one row from one byte of bits;
-    // rows 0..127 of the unit space are A (frames), 128..383 are B (columns)
-    for (uint32_t u = t; u < (kTM + kTN) * 8u; u += kThreads) {
-      // consecutive lanes take consecutive rows of the same 16-byte column
-      const uint32_t row = u % (kTM + kTN), j = u / (kTM + kTN);
+    // ---- expand: a thread takes whole rows of the slice (64 inputs = two
+    // words of bits -> eight 16-byte units of 8 bf16); rows 0..127 are A
+    // (frames), 128..383 B (columns); consecutive threads write consecutive
+    // 16-byte rows of a core matrix
+    for (uint32_t row = t; row < kTM + kTN; row += kThreads) {
       const bool is_a = row < kTM;
       const uint32_t r = is_a ? row : row - kTM;
       const uint32_t* bitsrow = is_a ? s_abits + r * kSlabStride : s_bbits + r * kSlabStride;
-      const uint32_t bits = (bitsrow[ws + (j >> 2)] >> ((j & 3u) * 8u)) & 0xFFu;
-      uint4 v;
-      v.x = two_bf16(bits & 1u, bits & 2u);
-      v.y = two_bf16(bits & 4u, bits & 8u);
-      v.z = two_bf16(bits & 16u, bits & 32u);
-      v.w = two_bf16(bits & 64u, bits & 128u);
-      *reinterpret_cast<uint4*>((is_a ? sA : sB) + tile_off(r, 8u * j)) = v;
+      const uint32_t w0 = bitsrow[ws], w1 = bitsrow[ws + 1u];
+      uint8_t* dst = (is_a ? sA : sB) + tile_off(r, 0u);
+#pragma unroll
+      for (uint32_t j = 0; j < 8u; ++j) {
+        const uint32_t bits = ((j < 4u ? w0 : w1) >> ((j & 3u) * 8u)) & 0xFFu;
+        uint4 v;
+        v.x = two_bf16(bits & 1u, bits & 2u);
+        v.y = two_bf16(bits & 4u, bits & 8u);
+        v.z = two_bf16(bits & 16u, bits & 32u);
+        v.w = two_bf16(bits & 64u, bits & 128u);
+        *reinterpret_cast<uint4*>(dst + j * kLBO) = v;
+      }
     }
     // make the tiles visible to the tensor core, then one thread issues
     fence_async_smem();
@@ -280,23 +285,29 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
     mbar_wait_bounded(&mbar[1], phase[1]);
     if (t == 0) atomicExch(a.err, 1u);
   } else if (warp < 4u) {
-    // ---- epilogue: warp w holds frames f0 + 32w .. f0 + 32w + 31
-    const uint32_t f = f0 + warp * 32u + lane;
+    // ---- epilogue: warp w holds frames f0 + 32w .. f0 + 32w + 31; each 32 x
+    // 32 block goes through shared memory (the operand stages are free now)
+    // so that every store writes 32 consecutive columns of one frame
+    float* tr = reinterpret_cast<float*>(smem) + warp * 32u * 33u;
+    const uint32_t c = c0 + lane;  // this lane's column within the block, below
 #pragma unroll 1
     for (uint32_t cb = 0; cb < kTN; cb += 32u) {
       uint32_t r[32];
       tmem_ld32(taddr + ((warp * 32u) << 16) + cb, r);
-      if (f < a.n_frames) {
-        float* out = a.ov + (uint64_t)f * a.C;
 #pragma unroll
-        for (uint32_t j = 0; j < 32; ++j) {
-          const uint32_t c = c0 + cb + j;
-          if (c < a.C) {
-            const uint32_t raw = (uint32_t)__uint_as_float(r[j]);
-            out[c] = dev::boosted(raw, a.min_overlap, __ldg(a.boost + c));
-          }
+      for (uint32_t j = 0; j < 32; ++j) tr[lane * 33u + j] = __uint_as_float(r[j]);
+      __syncwarp();
+      const bool col_ok = c + cb < a.C;
+      const float b = col_ok ? __ldg(a.boost + c + cb) : 0.0f;
+#pragma unroll 4
+      for (uint32_t i = 0; i < 32u; ++i) {
+        const uint32_t f = f0 + warp * 32u + i;
+        if (f < a.n_frames && col_ok) {
+          const uint32_t raw = (uint32_t)tr[i * 33u + lane];
+          a.ov[(uint64_t)f * a.C + c + cb] = dev::boosted(raw, a.min_overlap, b);
         }
       }
+      __syncwarp();
     }
   }
   fence_before_sync();
