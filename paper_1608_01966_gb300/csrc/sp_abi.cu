@@ -119,7 +119,8 @@ void free_handle(sp_handle* h) {
   if (h->d_mstage) cudaFree(h->d_mstage);
   if (h->d_run_ov) cudaFree(h->d_run_ov);
   if (h->d_run_masks) cudaFree(h->d_run_masks);
-  if (h->d_conn) cudaFree(h->d_conn);
+  if (h->d_bimg) cudaFree(h->d_bimg);
+  if (h->d_aimg) cudaFree(h->d_aimg);
   if (h->d_xspan) cudaFree(h->d_xspan);
   if (h->d_compact) cudaFree(h->d_compact);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
@@ -276,23 +277,6 @@ sp_status wait_handle(sp_handle* h) {
   }
 }
 
-sp_status bounded_stream_wait(cudaStream_t s, cudaEvent_t ev, uint32_t timeout_ms) {
-  SP_CUDA(cudaEventRecord(ev, s));
-  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
-  for (uint32_t spin = 0;; ++spin) {
-    const cudaError_t e = cudaEventQuery(ev);
-    if (e == cudaSuccess) return SP_OK;
-    if (e != cudaErrorNotReady)
-      return fail(SP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
-    if (std::chrono::steady_clock::now() > deadline)
-      return fail(SP_ETIMEOUT, "wait exceeded %u ms", timeout_ms);
-    if (spin < 2000)
-      std::this_thread::yield();
-    else
-      std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
-}
-
 // Order the handle's work on stream s after everything enqueued before.
 sp_status use_stream(sp_handle* h, cudaStream_t s) {
   if (!s) s = h->own_stream;
@@ -348,6 +332,7 @@ sp_status enqueue_frame(sp_handle* h, cudaStream_t st, const uint32_t* x, const 
   a.mask_copy = mask_copy;
   SP_CUDA(sp::launch_step(a, h->grid, st));
   h->pending = learn != 0;
+  if (learn) h->bimg_stale = true;  // the deferred update will change the permanences
   h->cur = cur ^ 1;
   h->frames++;
   return SP_OK;
@@ -401,25 +386,30 @@ sp_status ensure_dense_buffers(sp_handle* h, uint32_t n) {
     SP_CUDA(device_malloc((void**)&h->d_run_masks, (size_t)n * h->mask_words * 4));
     h->run_cap = n;
   }
-  if (!h->d_conn) {
-    h->conn_words = 2u * ((h->S + 63u) / 64u);
-    SP_CUDA(device_malloc((void**)&h->d_conn, (size_t)h->C * h->conn_words * 4));
+  const size_t abytes = sp::dense_aimg_bytes(n, h->S);
+  if (abytes > h->aimg_cap) {
+    if (h->d_aimg) cudaFree(h->d_aimg);
+    h->d_aimg = nullptr;
+    h->aimg_cap = 0;
+    SP_CUDA(device_malloc((void**)&h->d_aimg, abytes));
+    h->aimg_cap = abytes;
+  }
+  if (!h->d_bimg) {
+    SP_CUDA(device_malloc((void**)&h->d_bimg, sp::dense_bimg_bytes(h->C, h->S)));
+    h->bimg_stale = true;
   }
   return SP_OK;
 }
 
-// Inference run of a dense-pool SP on the tensor cores: all overlaps of the
-// run as one matrix product, then Alg. 2 per frame, then duty cycles in
-// frame order.
-sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
-                    uint32_t* masks) {
-  sp_status s = flush_learning(h);
-  if (s != SP_OK) return s;
-  if ((s = ensure_dense_buffers(h, n)) != SP_OK) return s;
+// The arguments of a dense run of n frames at x_base (the connection image is
+// rebuilt first when the permanences may have changed since it was built).
+sp::DenseArgs dense_args(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride) {
   sp::DenseArgs d{};
   d.perm = h->d_perm;
-  d.conn = h->d_conn;
-  d.conn_words = h->conn_words;
+  d.bimg = h->d_bimg;
+  d.aimg = h->d_aimg;
+  d.n_slices = sp::dense_slices(h->S);
+  d.pack = h->bimg_stale ? 1u : 0u;
   d.boost = h->d_boost;
   d.frames = x_base;
   d.stride = stride;
@@ -431,7 +421,18 @@ sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t s
   d.min_overlap = h->cfg.min_overlap;
   d.ov = h->d_run_ov;
   d.err = h->d_err;
-  SP_CUDA(sp::launch_conn_pack_one(d, h->stream));
+  return d;
+}
+
+sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
+                    uint32_t* masks) {
+  sp_status s = flush_learning(h);
+  if (s != SP_OK) return s;
+  if ((s = ensure_dense_buffers(h, n)) != SP_OK) return s;
+  const sp::DenseArgs d = dense_args(h, x_base, n, stride);
+  if (d.pack) SP_CUDA(sp::launch_conn_image_one(d, h->stream));
+  h->bimg_stale = false;
+  SP_CUDA(sp::launch_frame_image_one(d, h->stream));
   SP_CUDA(sp::launch_dense_overlap(d, h->stream));
   h->dense_used = true;
   const bool duty = h->cfg.duty_period > 0.0f;
@@ -466,6 +467,7 @@ sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t s
 
 sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
                        int learn, uint32_t* masks) {
+  if (learn) h->bimg_stale = true;
   if (!learn && h->dense && n >= kDenseMinFrames && dense_enabled())
     return run_dense(h, x_base, n, stride, masks);
   if (h->seq_ok && n >= kSeqMinFrames && seq_enabled()) {
@@ -1265,6 +1267,8 @@ bool persistent_enabled() {
 
 sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t stride, int learn,
                     uint32_t* masks, uint64_t mstride) {
+  if (learn)
+    for (sp_handle* h : b->members) h->bimg_stale = true;
   if (n >= 2 && persistent_enabled()) {
     sp::BatchRunArgs r{};
     r.desc = b->d_desc;
@@ -1564,26 +1568,15 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
   }
   std::vector<sp::DenseArgs> dargs(n);
   std::vector<sp::FrameInhibitArgs> fargs(n);
-  uint32_t max_C = 0, max_S = 0, max_cw = 0;
+  uint32_t max_C = 0, max_S = 0, max_K = 0;
+  bool all_global = true, any_pack = false;
   for (uint32_t i = 0; i < n; ++i) {
     sp_handle* h = b->members[i];
     if ((st = ensure_dense_buffers(h, n_frames)) != SP_OK) return st;
     sp::DenseArgs& d = dargs[i];
-    d.perm = h->d_perm;
-    d.conn = h->d_conn;
-    d.conn_words = h->conn_words;
-    max_cw = std::max(max_cw, h->conn_words);
-    d.boost = h->d_boost;
-    d.frames = d_frames + b->frame_off[i];
-    d.stride = stride;
-    d.n_frames = n_frames;
-    d.C = h->C;
-    d.K = h->S;
-    d.n_words = h->n_words;
-    d.thr = h->cfg.connect_threshold;
-    d.min_overlap = h->cfg.min_overlap;
-    d.ov = h->d_run_ov;
-    d.err = h->d_err;
+    d = dense_args(h, d_frames + b->frame_off[i], n_frames, stride);
+    any_pack = any_pack || d.pack != 0u;
+    max_K = std::max(max_K, h->S);
     h->dense_used = true;
     sp::FrameInhibitArgs& f = fargs[i];
     f.ov = h->d_run_ov;
@@ -1605,6 +1598,7 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
     f.ov_last = h->d_ov;
     max_C = std::max(max_C, h->C);
     max_S = std::max(max_S, f.unit_S);
+    all_global = all_global && f.inhibition == 0u;
   }
   if (sp::frame_inhibit_smem(max_C, max_S) > sp::frame_inhibit_smem_limit())
     return fail(SP_ENOTSUP, "members too large for one per-frame inhibition launch");
@@ -1627,9 +1621,12 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
   std::memcpy(h_args + sizeof(sp::DenseArgs) * n, fargs.data(), sizeof(sp::FrameInhibitArgs) * n);
   SP_CUDA(cudaMemcpyAsync(d_dargs, h_args, arg_bytes, cudaMemcpyHostToDevice, b->stream));
   SP_CUDA(cudaEventRecord(b->ev_infer[turn], b->stream));
-  SP_CUDA(sp::launch_conn_pack(d_dargs, n, max_C, max_cw, b->stream));
+  if (any_pack) SP_CUDA(sp::launch_conn_image(d_dargs, n, max_C, max_K, b->stream));
+  for (sp_handle* h : b->members) h->bimg_stale = false;
+  SP_CUDA(sp::launch_frame_image(d_dargs, n, n_frames, max_K, b->stream));
   SP_CUDA(sp::launch_dense_overlap_many(d_dargs, n, max_C, n_frames, b->stream));
-  SP_CUDA(sp::launch_frame_inhibit_many(d_fargs, n, max_C, max_S, n_frames, b->stream));
+  SP_CUDA(sp::launch_frame_inhibit_many(d_fargs, n, max_C, max_S, n_frames, all_global,
+                                        b->stream));
   for (uint32_t i = 0; i < n; ++i) {
     sp_handle* h = b->members[i];
     if (h->cfg.duty_period > 0.0f)

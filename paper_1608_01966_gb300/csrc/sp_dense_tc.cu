@@ -6,27 +6,36 @@
 //
 //     raw[f][c] = sum_i X[f][i] * Conn[c][i],   Conn[c][i] = [perm[c][i] >= thr],
 //
-// with X and Conn in {0, 1}.  Both operands are exact in bf16 and every
-// partial sum is an integer <= n_in < 2^24, exact in the fp32 accumulator,
-// so the tensor-core result equals the integer count bit for bit.
+// with X and Conn in {0, 1}.  Both operands are exact in fp8 (e4m3: 1.0 is
+// 0x38), each product is 0 or 1 and every partial sum is an integer <= n_in <
+// 2^24, exact in the fp32 accumulator, so the tensor-core result equals the
+// integer count bit for bit.
 //
-// sp_conn_pack_kernel packs [perm >= thr] into bits once per run.
-// sp_dense_overlap_kernel: one CTA (128 threads) per tile of 128 frames x 256
-// columns.  For each 64-input slice of K the threads expand the packed frame
-// bits and the packed connected bits into bf16 operand tiles in shared
-// memory (two stages: a slice is expanded while the previous slice's MMAs
-// run) (canonical K-major layout without swizzle: 8-row x 16-byte core
-// matrices, 128 B apart along K, 1024 B apart along M/N); one thread issues
-// four tcgen05.mma (M=128, N=256, K=16) into a 128-lane x 256-column fp32
-// accumulator in tensor memory and commits them to an mbarrier.  The
-// epilogue reads the accumulator with tcgen05.ld and writes the boosted
-// overlaps (min_overlap, boost: Alg. 1's tail) of every frame.
+// Operands live in global memory as images of the tensor core's shared-memory
+// operand layout (K-major, no swizzle: 8-row x 16-byte core matrices, 128 B
+// apart along K, 1024 B apart along M/N), one contiguous block per (tile of
+// rows, slice of 128 inputs), zero past the ends:
+//   sp_conn_image_kernel  Conn blocks (256 columns x 128 inputs, 32 KB) from
+//                         perm; the image is part of the SP's state and is
+//                         rebuilt only after the permanences changed;
+//   sp_frame_image_kernel X blocks (128 frames x 128 inputs, 16 KB) from the
+//                         packed frame bits of the run.
+// sp_dense_overlap_kernel: one CTA (256 threads) per tile of 128 frames x 256
+// columns.  Warp 0 streams the tile's blocks into four shared-memory stages
+// with bulk copies (cp.async.bulk, completion counted on an mbarrier); warp 1
+// issues four tcgen05.mma (kind::f8f6f4, M=128, N=256, K=32) per slice into a
+// 128-lane x 256-column fp32 accumulator in tensor memory and commits each
+// slice to the stage's "free" mbarrier.  All eight warps then read the
+// accumulator with tcgen05.ld and write the boosted overlaps (min_overlap,
+// boost: Alg. 1's tail) of every frame through a shared-memory transpose.
 //
-// sp_frame_inhibit_kernel: one CTA per frame runs Alg. 2 on its overlaps.
+// sp_frame_select_warp_kernel: one warp per frame runs Alg. 2 with global
+// inhibition on its overlaps; sp_frame_inhibit_kernel (one CTA per frame)
+// the other inhibition modes and wider SPs.
 //
-// The only wait is on the mbarrier the MMAs complete, bounded by an
-// iteration limit: on expiry the kernel records an error, stops issuing,
-// waits (bounded) for what it issued, frees its tensor memory and returns.
+// Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the kernel
+// records an error, stops issuing, waits (bounded) for the copies and MMAs it
+// issued, frees its tensor memory and returns.
 #include <algorithm>
 #include <atomic>
 
@@ -42,25 +51,28 @@ namespace {
 
 using dev::kFull;
 
-constexpr uint32_t kTM = 128;   // frames per tile (MMA M)
-constexpr uint32_t kTN = 256;   // columns per tile (MMA N)
-constexpr uint32_t kTK = 64;    // inputs per shared-memory slice
-constexpr uint32_t kMmaK = 16;  // K of one kind::f16 MMA
-constexpr uint32_t kThreads = 256;  // 8 warps expand operands; warps 0-3 read the accumulator
+constexpr uint32_t kTM = 128;       // frames per tile (MMA M)
+constexpr uint32_t kTN = 256;       // columns per tile (MMA N)
+constexpr uint32_t kTK = 128;       // inputs per slice (one byte each)
+constexpr uint32_t kMmaK = 32;      // K of one kind::f8f6f4 MMA
+constexpr uint32_t kStages = 4;
+constexpr uint32_t kThreads = 256;  // warp 0 copies, warp 1 issues; all 8 read the accumulator
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kABytes = kTM * kTK * 2;  // 16 KB
-constexpr uint32_t kBBytes = kTN * kTK * 2;  // 32 KB
-constexpr uint32_t kSuperK = 1024;           // inputs whose packed bits are staged at once
-constexpr uint32_t kSuperW = kSuperK / 32;   // words per row of a staged slab
-constexpr uint32_t kSlabStride = kSuperW + 1;  // padded: rows fall in different banks
-constexpr uint32_t kBitsBytes = (kTM + kTN) * kSlabStride * 4;  // ~49.5 KB
-constexpr uint32_t kLBO = 128;               // bytes between core matrices along K
-constexpr uint32_t kSBO = (kTK / 8) * 128;   // bytes between 8-row groups
-constexpr uint32_t kWaitLimit = 1u << 26;    // mbarrier polls before giving up
-constexpr uint16_t kBf16One = 0x3F80;
+constexpr uint32_t kABytes = kTM * kTK;  // 16 KB
+constexpr uint32_t kBBytes = kTN * kTK;  // 32 KB
+constexpr uint32_t kLBO = 128;           // bytes between core matrices along K
+constexpr uint32_t kSBO = (kTK / 16) * 128;  // bytes between 8-row groups
+constexpr uint64_t kWaitNs = 1000000000ull;  // bound of every mbarrier wait
+constexpr uint32_t kFp8One = 0x38;           // 1.0 in e4m3
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 // tcgen05 shared-memory matrix descriptor: start address, leading (K) and
@@ -74,10 +86,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
-// K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTN >> 3) << 17) |
-                            ((kTM >> 4) << 24);
+// Instruction descriptor of kind::f8f6f4: fp32 accumulator, e4m3 A and B
+// (format code 0), both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
@@ -95,17 +106,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0u;
 }
 
+// Wait for the phase with the given parity to complete; false after kWaitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < (1u << 30); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t taddr, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Global -> shared bulk copy (16-byte aligned ends, size a multiple of 16)
+// whose bytes complete on bar.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t taddr, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
       : "memory");
 }
@@ -122,9 +154,6 @@ __device__ __forceinline__ void fence_before_sync() {
 }
 __device__ __forceinline__ void fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 // 32 consecutive accumulator columns of this warp's 32 lanes.
@@ -143,17 +172,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// Offset of element (row, k) of an operand tile in the canonical layout.
-__device__ __forceinline__ uint32_t tile_off(uint32_t row, uint32_t k) {
-  return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7u) * 16u + (k & 7u) * 2u;
-}
-
-__device__ __forceinline__ uint32_t two_bf16(bool lo, bool hi) {
-  return (lo ? (uint32_t)kBf16One : 0u) | (hi ? ((uint32_t)kBf16One << 16) : 0u);
+// Four {0,1} bits -> four e4m3 bytes (bit i -> byte i): the multiply places
+// bit i at bit 8i (the four shifted copies do not overlap), the mask keeps
+// those bits and the second multiply turns each into 0x38.
+__device__ __forceinline__ uint32_t fp8_nibble(uint32_t n4) {
+  return ((n4 * 0x00204081u) & 0x01010101u) * kFp8One;
 }
 
 // One SP's arguments by value, or a device array of several SPs (one per
-// blockIdx.z).
+// blockIdx.z / blockIdx.y).
 struct DenseLaunch {
   const DenseArgs* many;
   DenseArgs one;
@@ -161,21 +188,20 @@ struct DenseLaunch {
 
 __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const DenseLaunch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[kStages], freed[kStages], done;
   __shared__ uint32_t s_taddr;
-  __shared__ uint32_t s_fail;
+  __shared__ volatile uint32_t s_fail;
+  __shared__ uint32_t s_issued, s_consumed;
   DenseArgs a;  // kept in registers
   if (L.many)
     a = L.many[blockIdx.z];
   else
     a = L.one;
-  uint32_t* s_abits = reinterpret_cast<uint32_t*>(smem + 2u * (kABytes + kBBytes));
-  uint32_t* s_bbits = s_abits + kTM * kSlabStride;
   const uint32_t t = threadIdx.x, warp = t >> 5, lane = t & 31u;
   const uint32_t f0 = blockIdx.y * kTM, c0 = blockIdx.x * kTN;
   if (f0 >= a.n_frames || c0 >= a.C) return;  // a smaller SP of the launch
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(&s_taddr)),
                  "r"(kTmemCols)
@@ -183,128 +209,99 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (t == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (uint32_t i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&freed[i], 1);
+    }
+    mbar_init(&done, 1);
     s_fail = 0u;
+    s_issued = 0u;
+    s_consumed = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t taddr = s_taddr;
+  const uint32_t n = a.n_slices;
+  const uint8_t* ablk = a.aimg + (uint64_t)blockIdx.y * n * kABytes;
+  const uint8_t* bblk = a.bimg + (uint64_t)blockIdx.x * n * kBBytes;
 
-  const uint32_t n_chunks = (a.K + kTK - 1) / kTK;
-  uint32_t phase[2] = {0u, 0u};
-  for (uint32_t kc = 0; kc < n_chunks; ++kc) {
-    const uint32_t st = kc & 1u;
-    uint8_t* sA = smem + st * (kABytes + kBBytes);
-    uint8_t* sB = sA + kABytes;
-    // this stage was last read by the MMAs of slice kc - 2
-    if (kc >= 2u) {
-      if (!mbar_wait_bounded(&mbar[st], phase[st])) s_fail = 1u;
-      phase[st] ^= 1u;
-    }
-    const uint32_t k0 = kc * kTK;
-    // ---- every kSuperK inputs: stage the packed bits of the CTA's rows
-    if ((k0 % kSuperK) == 0u) {
-      __syncthreads();  // the previous slab has been expanded
-      const uint32_t w0 = k0 >> 5;
-      for (uint32_t i = t; i < kTM * kSuperW; i += kThreads) {
-        const uint32_t r = i / kSuperW, w = i % kSuperW, f = f0 + r, wi = w0 + w;
-        uint32_t v = 0u;
-        if (f < a.n_frames && wi < a.n_words) {
-          v = __ldg(a.frames + (uint64_t)f * a.stride + wi);
-          // inputs at or beyond n_in are zero whatever the unused bits hold
-          const uint32_t base = wi * 32u;
-          if (base + 32u > a.K) v &= (a.K > base) ? ((1u << (a.K - base)) - 1u) : 0u;
-        }
-        s_abits[r * kSlabStride + w] = v;
+  if (t == 0) {
+    // ---- producer: slice kc into stage kc % kStages once its MMAs are done
+    uint32_t kc = 0;
+    for (; kc < n && !s_fail; ++kc) {
+      const uint32_t st = kc % kStages;
+      if (kc >= kStages && !mbar_wait_bounded(&freed[st], ((kc / kStages) - 1u) & 1u)) {
+        s_fail = 1u;
+        break;
       }
-      for (uint32_t i = t; i < kTN * kSuperW; i += kThreads) {
-        const uint32_t r = i / kSuperW, w = i % kSuperW, c = c0 + r, wi = w0 + w;
-        s_bbits[r * kSlabStride + w] = (c < a.C && wi < a.conn_words)
-                                           ? __ldg(a.conn + (uint64_t)c * a.conn_words + wi)
-                                           : 0u;
-      }
-      __syncthreads();
+      uint8_t* sA = smem + st * (kABytes + kBBytes);
+      mbar_expect_tx(&full[st], kABytes + kBBytes);
+      bulk_copy(sA, ablk + (uint64_t)kc * kABytes, kABytes, &full[st]);
+      bulk_copy(sA + kABytes, bblk + (uint64_t)kc * kBBytes, kBBytes, &full[st]);
     }
-    const uint32_t ws = (k0 % kSuperK) >> 5;  // word of this slice in the slab
-    // ---- expand: a thread takes whole rows of the slice (64 inputs = two
-    // words of bits -> eight 16-byte units of 8 bf16); rows 0..127 are A
-    // (frames), 128..383 B (columns); consecutive threads write consecutive
-    // 16-byte rows of a core matrix
-    for (uint32_t row = t; row < kTM + kTN; row += kThreads) {
-      const bool is_a = row < kTM;
-      const uint32_t r = is_a ? row : row - kTM;
-      const uint32_t* bitsrow = is_a ? s_abits + r * kSlabStride : s_bbits + r * kSlabStride;
-      const uint32_t w0 = bitsrow[ws], w1 = bitsrow[ws + 1u];
-      uint8_t* dst = (is_a ? sA : sB) + tile_off(r, 0u);
-#pragma unroll
-      for (uint32_t j = 0; j < 8u; ++j) {
-        const uint32_t bits = ((j < 4u ? w0 : w1) >> ((j & 3u) * 8u)) & 0xFFu;
-        uint4 v;
-        v.x = two_bf16(bits & 1u, bits & 2u);
-        v.y = two_bf16(bits & 4u, bits & 8u);
-        v.z = two_bf16(bits & 16u, bits & 32u);
-        v.w = two_bf16(bits & 64u, bits & 128u);
-        *reinterpret_cast<uint4*>(dst + j * kLBO) = v;
+    s_issued = kc;
+  } else if (t == 32) {
+    // ---- MMA issuer
+    uint32_t kc = 0;
+    for (; kc < n && !s_fail; ++kc) {
+      const uint32_t st = kc % kStages;
+      if (!mbar_wait_bounded(&full[st], (kc / kStages) & 1u)) {
+        s_fail = 1u;
+        break;
       }
-    }
-    // make the tiles visible to the tensor core, then one thread issues
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (s_fail) break;
-    if (t == 0) {
-      const uint64_t ad = smem_desc(smem_u32(sA)), bd = smem_desc(smem_u32(sB));
+      fence_after_sync();
+      const uint8_t* sA = smem + st * (kABytes + kBBytes);
+      const uint64_t ad = smem_desc(smem_u32(sA)), bd = smem_desc(smem_u32(sA + kABytes));
 #pragma unroll
       for (uint32_t s = 0; s < kTK / kMmaK; ++s) {
         // K advances by two core matrices (32 bytes of each row) per MMA
         const uint64_t step = (uint64_t)((2u * kLBO * s) >> 4);
-        mma_bf16(taddr, ad + step, bd + step, (kc | s) != 0u ? 1u : 0u);
+        mma_f8(taddr, ad + step, bd + step, (kc | s) != 0u ? 1u : 0u);
       }
-      mma_commit(&mbar[st]);
+      mma_commit(&freed[st]);
     }
+    s_consumed = kc;
+    mma_commit(&done);  // arrives when every MMA issued above has completed
   }
-  // the last one or two commits are still outstanding
-  if (!s_fail) {
-    for (uint32_t st = 0; st < 2u; ++st) {
-      const uint32_t issued = n_chunks > st ? (n_chunks - st + 1u) / 2u : 0u;
-      const uint32_t waited = n_chunks > st + 2u ? (n_chunks - st - 1u) / 2u : 0u;
-      if (issued > waited && !mbar_wait_bounded(&mbar[st], phase[st])) s_fail = 1u;
-    }
-  }
-  fence_before_sync();
   __syncthreads();
+  bool ok = !s_fail;
+  if (!ok) {
+    // copies issued but never consumed still land in shared memory: wait for them
+    if (t == 0)
+      for (uint32_t kc = s_consumed; kc < s_issued; ++kc)
+        mbar_wait_bounded(&full[kc % kStages], (kc / kStages) & 1u);
+  }
+  // every thread: the accumulator (and the stages' last readers) are done
+  if (!mbar_wait_bounded(&done, 0u)) ok = false;
   fence_after_sync();
-
-  if (s_fail) {
-    // let whatever was issued finish (bounded) before the memory is released
-    mbar_wait_bounded(&mbar[0], phase[0]);
-    mbar_wait_bounded(&mbar[1], phase[1]);
+  if (!ok) {
     if (t == 0) atomicExch(a.err, 1u);
-  } else if (warp < 4u) {
-    // ---- epilogue: warp w holds frames f0 + 32w .. f0 + 32w + 31; each 32 x
-    // 32 block goes through shared memory (the operand stages are free now)
-    // so that every store writes 32 consecutive columns of one frame
+  } else {
+    // ---- epilogue: warp w reads accumulator lanes 32(w % 4) .. + 31 (frames)
+    // and columns 128(w / 4) .. + 127; each 32 x 32 block goes through shared
+    // memory (the stages are free now) so that every store writes 32
+    // consecutive columns of one frame
     float* tr = reinterpret_cast<float*>(smem) + warp * 32u * 33u;
-    const uint32_t c = c0 + lane;  // this lane's column within the block, below
+    const uint32_t q = warp & 3u, h = warp >> 2;
 #pragma unroll 1
-    for (uint32_t cb = 0; cb < kTN; cb += 32u) {
+    for (uint32_t cb = h * 128u; cb < h * 128u + 128u; cb += 32u) {
       uint32_t r[32];
-      tmem_ld32(taddr + ((warp * 32u) << 16) + cb, r);
+      tmem_ld32(taddr + ((q * 32u) << 16) + cb, r);
 #pragma unroll
       for (uint32_t j = 0; j < 32; ++j) tr[lane * 33u + j] = __uint_as_float(r[j]);
       __syncwarp();
-      const bool col_ok = c + cb < a.C;
-      const float b = col_ok ? __ldg(a.boost + c + cb) : 0.0f;
+      const uint32_t c = c0 + cb + lane;
+      const bool col_ok = c < a.C;
+      const float b = col_ok ? __ldg(a.boost + c) : 0.0f;
+      const uint32_t fr0 = f0 + q * 32u;
+      float* out = a.ov + (uint64_t)fr0 * a.C + c;
 #pragma unroll 4
       for (uint32_t i = 0; i < 32u; ++i) {
-        const uint32_t f = f0 + warp * 32u + i;
-        if (f < a.n_frames && col_ok) {
+        if (fr0 + i < a.n_frames && col_ok) {
           const uint32_t raw = (uint32_t)tr[i * 33u + lane];
-          a.ov[(uint64_t)f * a.C + c + cb] = dev::boosted(raw, a.min_overlap, b);
+          out[(uint64_t)i * a.C] = dev::boosted(raw, a.min_overlap, b);
         }
       }
       __syncwarp();
@@ -313,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr),
                  "r"(kTmemCols)
                  : "memory");
@@ -384,6 +381,144 @@ __global__ void __launch_bounds__(kStepThreads) sp_frame_inhibit_kernel(const In
   }
 }
 
+// Alg. 2 with global inhibition, one warp per frame.  Lane l holds overlaps
+// l, l + 32, l + 64, ... in registers, so a ballot over step j is mask word j.
+// With unit boosts the overlaps are exact small integers and are compared as
+// such, otherwise as fp32 bit patterns (non-negative, so integer order is
+// value order).  T, the k-th largest overlap, is the largest t with at least
+// k overlaps >= t; it lies between a lower bound (for k <= 32: k lanes hold a
+// value >= the k-th largest lane maximum) and the maximum, so it shares their
+// common leading bits and only the bits below are searched, most significant
+// first.  Winners are the overlaps above T and the first k - #(> T) equal to
+// T in column order (none when T is 0: fewer than k nonzero overlaps).
+constexpr uint32_t kSelectWarps = 4;  // frames per CTA
+
+template <int V>  // overlaps per lane: at most 32 * V columns
+__global__ void __launch_bounds__(kSelectWarps * 32, V <= 32 ? 8 : 4) sp_frame_select_warp_kernel(
+    const InhibitLaunch L) {
+  constexpr int Q = (V + 31) / 32;  // mask words per lane
+  FrameInhibitArgs a;  // kept in registers
+  if (L.many)
+    a = L.many[blockIdx.y];
+  else
+    a = L.one;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t f = blockIdx.x * kSelectWarps + (threadIdx.x >> 5);
+  if (f >= a.n_frames) return;
+  const float* ov = a.ov + (uint64_t)f * a.C;
+  uint32_t key[V];
+  uint32_t lmax = 0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const uint32_t i = (uint32_t)j * 32u + lane;
+    const float x = i < a.C ? __ldg(ov + i) : 0.0f;
+    key[j] = a.unit_S ? __float2uint_rz(x) : __float_as_uint(x);
+    lmax = max(lmax, key[j]);
+  }
+  const uint32_t vmax = __reduce_max_sync(kFull, lmax);
+  const uint32_t k = a.k;
+  uint32_t T = 0u;
+  if (k == 0u) {
+    T = 0xffffffffu;  // nothing exceeds or equals it: no column wins
+  } else if (vmax != 0u) {
+    uint32_t lo = 0u;
+    if (k <= 32u) {
+      for (int b = 31 - __clz(vmax); b >= 0; --b) {
+        const uint32_t cand = lo | (1u << b);
+        if ((uint32_t)__popc(__ballot_sync(kFull, lmax >= cand)) >= k) lo = cand;
+      }
+    }
+    if (lo == vmax) {
+      T = vmax;
+    } else {
+      const int d = 31 - __clz(lo ^ vmax);  // highest bit where the bounds differ
+      T = d == 31 ? 0u : vmax & ~((2u << d) - 1u);
+      for (int b = d; b >= 0; --b) {
+        const uint32_t cand = T | (1u << b);
+        uint32_t ge = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) ge += key[j] >= cand;
+        if (__reduce_add_sync(kFull, ge) >= k) T = cand;
+      }
+    }
+  }
+  uint32_t G[Q], E[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) G[q] = E[q] = 0u;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    if ((uint32_t)j * 32u >= a.C) break;
+    const uint32_t g = __ballot_sync(kFull, key[j] > T);
+    const uint32_t e = __ballot_sync(kFull, key[j] == T);
+    if (lane == ((uint32_t)j & 31u)) {
+      G[j >> 5] = g;
+      E[j >> 5] = e;
+    }
+  }
+  uint32_t gt = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) gt += __popc(G[q]);
+  gt = __reduce_add_sync(kFull, gt);
+  const uint32_t need = (T == 0u || T == 0xffffffffu) ? 0u : k - gt;
+  uint32_t W[Q];
+  uint32_t before = 0;  // ties in earlier words (word order: q major, lane minor)
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    W[q] = G[q];
+    if (need != 0u) {
+      const uint32_t ce = __popc(E[q]);
+      uint32_t inc = ce;
+#pragma unroll
+      for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const uint32_t ex = before + inc - ce;
+      before += __shfl_sync(kFull, inc, 31);
+      const uint32_t take = need > ex ? min(need - ex, ce) : 0u;
+      uint32_t e = E[q], keep = 0u;
+      if (take == ce) {
+        keep = e;
+      } else {
+        for (uint32_t n = 0; n < take; ++n) {  // the lowest `take` tied columns
+          const uint32_t low = e & (0u - e);
+          keep |= low;
+          e ^= low;
+        }
+      }
+      W[q] |= keep;
+    }
+  }
+  const bool last = f + 1u == a.n_frames;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const uint32_t w = (uint32_t)q * 32u + lane;
+    if (w < a.mask_words) {
+      if (a.masks_out) a.masks_out[(uint64_t)f * a.masks_stride + w] = W[q];
+      if (last) a.mask_last[w] = W[q];
+    }
+  }
+  if (last) {
+    uint32_t base = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t c = __popc(W[q]);
+      uint32_t inc = c;
+#pragma unroll
+      for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+      }
+      uint32_t pos = base + inc - c;
+      base += __shfl_sync(kFull, inc, 31);
+      for (uint32_t w = W[q]; w != 0u; w &= w - 1u)
+        a.result[1 + pos++] = ((uint32_t)q * 32u + lane) * 32u + (uint32_t)(__ffs(w) - 1);
+    }
+    if (lane == 0u) a.result[0] = gt + need;
+    for (uint32_t i = lane; i < a.C; i += 32u) a.ov_last[i] = __ldg(ov + i);
+  }
+}
+
 // Duty cycles over a run of frames, in frame order (one thread per column).
 __global__ void sp_duty_run_kernel(const uint32_t* masks, uint32_t n_frames, uint32_t mask_words,
                                    uint32_t C, float* duty, float period) {
@@ -398,98 +533,150 @@ __global__ void sp_duty_run_kernel(const uint32_t* masks, uint32_t n_frames, uin
   duty[c] = d;
 }
 
-// Connected bits of one dense SP: word w of column c holds [perm >= thr] of
-// inputs 32w .. 32w+31 (LSB first; zero beyond K and in the padding word).
-// One warp per word: lane i reads input 32w + i (coalesced) and a ballot packs.
-__global__ void __launch_bounds__(256) sp_conn_pack_kernel(const DenseLaunch L) {
+// Image blocks of one dense SP.  Unit u of a block (16 bytes: one row, 16
+// consecutive inputs) sits at byte 16u of the block: u = 64 (r / 8) +
+// 8 (chunk) + r % 8 for row r and 16-input chunk of the slice, which is the
+// core-matrix layout; unit g of the whole image is block g / U, unit g % U
+// (U = rows per tile x 8), so consecutive threads write consecutive 16 bytes.
+__device__ __forceinline__ void image_unit(uint64_t g, uint32_t rows, uint32_t n_slices,
+                                           uint32_t& row, uint32_t& k0) {
+  const uint32_t per = rows * 8u;  // units per block
+  const uint64_t blk = g / per;
+  const uint32_t u = (uint32_t)(g - blk * per);
+  const uint32_t tile = (uint32_t)(blk / n_slices), slice = (uint32_t)(blk % n_slices);
+  row = tile * rows + (u >> 6) * 8u + (u & 7u);
+  k0 = slice * kTK + ((u >> 3) & 7u) * 16u;
+}
+
+// Conn[c][i] = [perm[c][i] >= thr] as e4m3 {0, 1}; only SPs whose pack flag
+// is set (their permanences changed since the image was built).
+__global__ void __launch_bounds__(256) sp_conn_image_kernel(const DenseLaunch L) {
   DenseArgs a;
   if (L.many)
     a = L.many[blockIdx.y];
   else
     a = L.one;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warps = (blockDim.x >> 5) * gridDim.x;
-  const uint32_t first = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  uint32_t* conn = const_cast<uint32_t*>(a.conn);
-  if ((a.K & 3u) == 0u) {
-    // a warp takes 4 words (128 synapses) per row block: one 16-byte load per
-    // lane (4 synapses, 4 bits); 8 lanes OR their nibbles into a word; four
-    // blocks' loads are in flight together
-    const uint32_t blocks_per_row = (a.conn_words + 3u) / 4u;
-    const uint32_t total = a.C * blocks_per_row;
-    for (uint32_t b0 = first; b0 < total; b0 += 4u * warps) {
-      uint32_t nib[4];
+  if (!a.pack) return;
+  const uint32_t n_ct = (a.C + kTN - 1) / kTN;
+  const uint64_t units = (uint64_t)n_ct * a.n_slices * kTN * 8u;
+  const bool vec = (a.K & 3u) == 0u;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < units;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t c, k0;
+    image_unit(g, kTN, a.n_slices, c, k0);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (c < a.C) {
+      const float* p = a.perm + (uint64_t)c * a.K;
+      if (vec && k0 + 16u <= a.K) {
 #pragma unroll
-      for (uint32_t q = 0; q < 4u; ++q) {
-        const uint32_t b = b0 + q * warps;
-        const uint32_t c = b / blocks_per_row, blk = b - c * blocks_per_row;
-        const uint32_t k = blk * 128u + lane * 4u;
-        nib[q] = 0u;
-        if (b < total && k < a.K) {
-          const float4 p = __ldcs(reinterpret_cast<const float4*>(a.perm + (uint64_t)c * a.K + k));
-          nib[q] = (p.x >= a.thr ? 1u : 0u) | (p.y >= a.thr ? 2u : 0u) |
-                   (p.z >= a.thr ? 4u : 0u) | (p.w >= a.thr ? 8u : 0u);
+        for (uint32_t q = 0; q < 4u; ++q) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(p + k0 + 4u * q));
+          w[q] = (v.x >= a.thr ? kFp8One : 0u) | (v.y >= a.thr ? kFp8One << 8 : 0u) |
+                 (v.z >= a.thr ? kFp8One << 16 : 0u) | (v.w >= a.thr ? kFp8One << 24 : 0u);
         }
-      }
-#pragma unroll
-      for (uint32_t q = 0; q < 4u; ++q) {
-        const uint32_t b = b0 + q * warps;
-        uint32_t word = nib[q] << (4u * (lane & 7u));
-        word |= __shfl_xor_sync(kFull, word, 1);
-        word |= __shfl_xor_sync(kFull, word, 2);
-        word |= __shfl_xor_sync(kFull, word, 4);
-        if (b < total && (lane & 7u) == 0u) {
-          const uint32_t c = b / blocks_per_row, blk = b - c * blocks_per_row;
-          const uint32_t w = blk * 4u + (lane >> 3);
-          if (w < a.conn_words) conn[(uint64_t)c * a.conn_words + w] = word;
+      } else {
+        uint64_t lo = 0u, hi = 0u;
+        for (uint32_t i = 0; i < 16u && k0 + i < a.K; ++i) {
+          const uint64_t byte = __ldcs(p + k0 + i) >= a.thr ? (uint64_t)kFp8One << (8u * (i & 7u)) : 0u;
+          if (i < 8u)
+            lo |= byte;
+          else
+            hi |= byte;
         }
+        w[0] = (uint32_t)lo;
+        w[1] = (uint32_t)(lo >> 32);
+        w[2] = (uint32_t)hi;
+        w[3] = (uint32_t)(hi >> 32);
       }
     }
-    return;
+    *reinterpret_cast<uint4*>(a.bimg + g * 16u) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  const uint32_t total = a.C * a.conn_words;
-  // four words per round, their loads issued together
-  for (uint32_t gw0 = first; gw0 < total; gw0 += 4u * warps) {
-    bool on[4];
-#pragma unroll
-    for (uint32_t q = 0; q < 4u; ++q) {
-      const uint32_t gw = gw0 + q * warps;
-      const uint32_t c = gw / a.conn_words, w = gw % a.conn_words;
-      const uint32_t k = w * 32u + lane;
-      on[q] = gw < total && k < a.K && __ldg(a.perm + (uint64_t)c * a.K + k) >= a.thr;
+}
+
+// X[f][i] = bit i of frame f as e4m3 {0, 1}; bits at or past K are zero
+// whatever the frame's unused high bits hold.
+__global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L) {
+  DenseArgs a;
+  if (L.many)
+    a = L.many[blockIdx.y];
+  else
+    a = L.one;
+  const uint32_t n_ft = (a.n_frames + kTM - 1) / kTM;
+  const uint64_t units = (uint64_t)n_ft * a.n_slices * kTM * 8u;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < units;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t f, k0;
+    image_unit(g, kTM, a.n_slices, f, k0);
+    uint32_t bits = 0u;
+    if (f < a.n_frames && k0 < a.K) {
+      bits = (__ldg(a.frames + (uint64_t)f * a.stride + (k0 >> 5)) >> (k0 & 31u)) & 0xFFFFu;
+      if (a.K - k0 < 16u) bits &= (1u << (a.K - k0)) - 1u;
     }
-#pragma unroll
-    for (uint32_t q = 0; q < 4u; ++q) {
-      const uint32_t gw = gw0 + q * warps;
-      const uint32_t bits = __ballot_sync(kFull, on[q]);
-      if (lane == 0 && gw < total) conn[gw] = bits;
-    }
+    *reinterpret_cast<uint4*>(a.aimg + g * 16u) =
+        make_uint4(fp8_nibble(bits & 15u), fp8_nibble((bits >> 4) & 15u),
+                   fp8_nibble((bits >> 8) & 15u), fp8_nibble(bits >> 12));
   }
 }
 
 }  // namespace
 
-cudaError_t launch_conn_pack(const DenseArgs* args, uint32_t n, uint32_t max_C,
-                             uint32_t max_conn_words, cudaStream_t stream) {
-  const uint32_t words = max_C * max_conn_words;  // 8 warps per CTA, 16 words per warp-round
-  const dim3 grid(std::max<uint32_t>(1u, std::min<uint32_t>((words + 127u) / 128u, 64u)), n, 1);
+size_t dense_bimg_bytes(uint32_t C, uint32_t K) {
+  return (size_t)((C + kTN - 1) / kTN) * kTN * ((K + kTK - 1) / kTK) * kTK;
+}
+
+size_t dense_aimg_bytes(uint32_t n_frames, uint32_t K) {
+  return (size_t)((n_frames + kTM - 1) / kTM) * kTM * ((K + kTK - 1) / kTK) * kTK;
+}
+
+uint32_t dense_slices(uint32_t K) { return (K + kTK - 1) / kTK; }
+
+namespace {
+
+// A grid-stride launch over `units` 16-byte units: at most 8 CTAs of 256
+// threads per SM in all.
+dim3 image_grid(uint64_t units, uint32_t n) {
+  const uint64_t want = (units + 255u) / 256u;
+  const uint32_t cap = std::max<uint32_t>(1u, 152u * 8u / std::max<uint32_t>(1u, n));
+  return dim3((uint32_t)std::max<uint64_t>(1u, std::min<uint64_t>(want, cap)), n, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_conn_image(const DenseArgs* args, uint32_t n, uint32_t max_C, uint32_t max_K,
+                              cudaStream_t stream) {
   DenseLaunch L{args, DenseArgs{}};
-  sp_conn_pack_kernel<<<grid, 256, 0, stream>>>(L);
+  sp_conn_image_kernel<<<image_grid(dense_bimg_bytes(max_C, max_K) / 16u, n), 256, 0, stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
-cudaError_t launch_conn_pack_one(const DenseArgs& a, cudaStream_t stream) {
-  const uint32_t words = a.C * a.conn_words;
+cudaError_t launch_conn_image_one(const DenseArgs& a, cudaStream_t stream) {
   DenseLaunch L{nullptr, a};
-  sp_conn_pack_kernel<<<std::max<uint32_t>(1u, std::min<uint32_t>((words + 127u) / 128u, 608u)), 256, 0, stream>>>(L);
+  sp_conn_image_kernel<<<image_grid(dense_bimg_bytes(a.C, a.K) / 16u, 1u), 256, 0, stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
-// Two stages of 48 KB operand tiles and a 48 KB slab of packed bits: one CTA
-// per SM, so its 256-column accumulator never waits for tensor memory.
-size_t dense_smem_bytes() { return 2u * (kABytes + kBBytes) + kBitsBytes; }
+cudaError_t launch_frame_image(const DenseArgs* args, uint32_t n, uint32_t max_frames,
+                               uint32_t max_K, cudaStream_t stream) {
+  DenseLaunch L{args, DenseArgs{}};
+  sp_frame_image_kernel<<<image_grid(dense_aimg_bytes(max_frames, max_K) / 16u, n), 256, 0,
+                          stream>>>(L);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_image_one(const DenseArgs& a, cudaStream_t stream) {
+  DenseLaunch L{nullptr, a};
+  sp_frame_image_kernel<<<image_grid(dense_aimg_bytes(a.n_frames, a.K) / 16u, 1u), 256, 0,
+                          stream>>>(L);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+// Four stages of 48 KB: one CTA per SM, so its 256-column accumulator never
+// waits for tensor memory.
+size_t dense_smem_bytes() { return kStages * (kABytes + kBBytes); }
 
 cudaError_t dense_init() {
   return cudaFuncSetAttribute(sp_dense_overlap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -525,17 +712,39 @@ cudaError_t frame_inhibit_init() {
                               (int)frame_inhibit_smem_limit());
 }
 
+namespace {
+
+// Warp-per-frame select: global inhibition over at most 2048 columns.
+cudaError_t launch_select_warp(const InhibitLaunch& L, uint32_t max_C, uint32_t max_frames,
+                               uint32_t n, cudaStream_t stream) {
+  const dim3 grid((max_frames + kSelectWarps - 1) / kSelectWarps, n, 1);
+  if (max_C <= 1024u)
+    sp_frame_select_warp_kernel<32><<<grid, kSelectWarps * 32, 0, stream>>>(L);
+  else
+    sp_frame_select_warp_kernel<64><<<grid, kSelectWarps * 32, 0, stream>>>(L);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+bool select_warp_fits(uint32_t max_C) { return max_C <= 2048u; }
+
+}  // namespace
+
 cudaError_t launch_frame_inhibit(const FrameInhibitArgs& a, cudaStream_t stream) {
   InhibitLaunch L{nullptr, a};
+  if (a.inhibition == 0u && select_warp_fits(a.C))
+    return launch_select_warp(L, a.C, a.n_frames, 1u, stream);
   sp_frame_inhibit_kernel<<<a.n_frames, kStepThreads, frame_inhibit_smem(a.C, a.unit_S), stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_frame_inhibit_many(const FrameInhibitArgs* args, uint32_t n, uint32_t max_C,
-                                      uint32_t max_unit_S, uint32_t max_frames,
+                                      uint32_t max_unit_S, uint32_t max_frames, bool all_global,
                                       cudaStream_t stream) {
   InhibitLaunch L{args, FrameInhibitArgs{}};
+  if (all_global && select_warp_fits(max_C))
+    return launch_select_warp(L, max_C, max_frames, n, stream);
   const dim3 grid(max_frames, n, 1);
   sp_frame_inhibit_kernel<<<grid, kStepThreads, frame_inhibit_smem(max_C, max_unit_S), stream>>>(L);
   g_launches.fetch_add(1, std::memory_order_relaxed);

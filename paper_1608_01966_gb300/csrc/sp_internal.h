@@ -166,8 +166,10 @@ struct sp_handle {
   uint32_t* d_cwide = nullptr;
   uint32_t* d_xspan = nullptr;      // [2][xspan_ctas] input-word span of each batch CTA
   uint32_t xspan_ctas = 0;
-  uint32_t* d_conn = nullptr;       // [C][conn_words] connected bits of a dense run
-  uint32_t conn_words = 0;
+  uint8_t* d_bimg = nullptr;        // e4m3 connection image of a dense SP (tensor-core layout)
+  uint8_t* d_aimg = nullptr;        // e4m3 frame image of a dense run
+  size_t aimg_cap = 0;              // bytes of d_aimg
+  bool bimg_stale = true;           // the permanences may have changed since d_bimg was built
   bool unit_boost = true;
   uint32_t* h_result = nullptr;  // pinned [1 + C]
   cudaStream_t own_stream = nullptr;

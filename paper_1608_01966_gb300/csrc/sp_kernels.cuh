@@ -189,11 +189,17 @@ cudaError_t seq_max_active_clusters(uint32_t Q, size_t smem_bytes, int* out);
 cudaError_t launch_seq(const SeqArgs& a, uint32_t Q, size_t smem_bytes, cudaStream_t stream);
 
 // Dense pools on the tensor cores (sp_dense_tc.cu): the raw overlaps of a run
-// of frames without learning as one {0,1} matrix product.
+// of frames without learning as one {0,1} matrix product.  Both operands are
+// e4m3 images laid out block by block as the tensor core reads them from
+// shared memory: block (tile, slice) covers rows tile * R .. + R - 1 (R = 256
+// columns for the connection image, 128 frames for the frame image) and
+// inputs slice * 128 .. + 127, zero past the ends.
 struct DenseArgs {
   const float* perm;        // [C][K]
-  const uint32_t* conn;     // [C][conn_words] connected bits (perm >= thr), LSB first
-  uint32_t conn_words;      // words per column row (even)
+  uint8_t* bimg;            // connection image, dense_bimg_bytes(C, K)
+  uint8_t* aimg;            // frame image, dense_aimg_bytes(n_frames, K)
+  uint32_t n_slices;        // dense_slices(K)
+  uint32_t pack;            // 1: rebuild bimg from perm (the permanences changed)
   const float* boost;       // [C]
   const uint32_t* frames;   // frame f at frames + f * stride
   uint64_t stride;
@@ -218,12 +224,18 @@ struct FrameInhibitArgs {
 
 size_t dense_smem_bytes();
 cudaError_t dense_init();
+size_t dense_bimg_bytes(uint32_t C, uint32_t K);
+size_t dense_aimg_bytes(uint32_t n_frames, uint32_t K);
+uint32_t dense_slices(uint32_t K);
+// Connection images of the SPs whose pack flag is set / frame images of the
+// run (args: a device array of n entries, or one SP by value).
+cudaError_t launch_conn_image(const DenseArgs* args, uint32_t n, uint32_t max_C, uint32_t max_K,
+                              cudaStream_t stream);
+cudaError_t launch_conn_image_one(const DenseArgs& a, cudaStream_t stream);
+cudaError_t launch_frame_image(const DenseArgs* args, uint32_t n, uint32_t max_frames,
+                               uint32_t max_K, cudaStream_t stream);
+cudaError_t launch_frame_image_one(const DenseArgs& a, cudaStream_t stream);
 cudaError_t launch_dense_overlap(const DenseArgs& a, cudaStream_t stream);
-// Pack the connected bits of every dense SP of a launch (conn written in place
-// of the args' conn pointers; one thread per 32 synapses).
-cudaError_t launch_conn_pack(const DenseArgs* args, uint32_t n, uint32_t max_C,
-                             uint32_t max_conn_words, cudaStream_t stream);
-cudaError_t launch_conn_pack_one(const DenseArgs& a, cudaStream_t stream);
 // Several SPs in one launch: args is a device array of n entries; every SP
 // covers at most max_C columns and max_frames frames.
 cudaError_t launch_dense_overlap_many(const DenseArgs* args, uint32_t n, uint32_t max_C,
@@ -232,8 +244,10 @@ cudaError_t frame_inhibit_init();
 size_t frame_inhibit_smem(uint32_t C, uint32_t unit_S);
 size_t frame_inhibit_smem_limit();
 cudaError_t launch_frame_inhibit(const FrameInhibitArgs& a, cudaStream_t stream);
+// all_global: every member inhibits globally (one warp per frame then
+// selects the winners when max_C <= 2048).
 cudaError_t launch_frame_inhibit_many(const FrameInhibitArgs* args, uint32_t n, uint32_t max_C,
-                                      uint32_t max_unit_S, uint32_t max_frames,
+                                      uint32_t max_unit_S, uint32_t max_frames, bool all_global,
                                       cudaStream_t stream);
 cudaError_t launch_duty_run(const uint32_t* masks, uint32_t n_frames, uint32_t mask_words,
                             uint32_t C, float* duty, float period, cudaStream_t stream);

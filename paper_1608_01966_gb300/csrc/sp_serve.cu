@@ -193,6 +193,7 @@ sp_status start_launch(sp_server* s, LaunchSlot& L, const LaunchSlot& other) {
     chained = chained || S.in_flight > 0u;
     S.in_flight += 1;
     S.pending = r.learn;
+    if (r.learn) S.h->bimg_stale = true;
     S.cur ^= 1;
     L.members.emplace_back(i, r);
     ++count;

@@ -117,7 +117,9 @@ def test_dense_run_after_learning_uses_learned_state():
 
 def test_batch_of_dense_sps_infers_in_two_launches():
     """Dense SPs of different shapes in one batch: all overlaps in one
-    tensor-core launch, Alg. 2 for every frame and SP in one more."""
+    tensor-core launch, Alg. 2 for every frame and SP in one more (plus the
+    operand images: the frames' every run, the connections' only when the
+    permanences changed)."""
     shapes = [(1024, 1024), (300, 500), (700, 2048), (257, 999), (1024, 1024)]
     cases = [_dense_case(C, n, 50 + i, k=max(1, (2 * C + 50) // 100))
              for i, (C, n) in enumerate(shapes)]
@@ -135,7 +137,13 @@ def test_batch_of_dense_sps_infers_in_two_launches():
     before = spg.sp_kernel_launch_count()
     spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
     spg.sp_batch_sync(b)
-    assert spg.sp_kernel_launch_count() - before == 3  # pack, GEMM, inhibition
+    # connection images, frame images, GEMM, inhibition
+    assert spg.sp_kernel_launch_count() - before == 4
+    dm.zero_()
+    before = spg.sp_kernel_launch_count()
+    spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
+    spg.sp_batch_sync(b)
+    assert spg.sp_kernel_launch_count() - before == 3  # the connection images are kept
     masks = dm.cpu().numpy().view(np.uint32)
     spg.sp_batch_destroy(b)
     for i, c in enumerate(cases):
@@ -143,4 +151,122 @@ def test_batch_of_dense_sps_infers_in_two_launches():
         got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
         assert first_diff(got, act) is None, f"member {i}"
         np.testing.assert_array_equal(spg.sp_get_overlaps(hs[i]), ov[-1])
+        spg.sp_destroy(hs[i])
+
+
+@pytest.mark.parametrize("C,k,m,p,unit", [
+    (2000, 40, 4, 0.2, True),    # two mask words per lane of the warp select
+    (2000, 25, 1, 0.3, False),   # fp32 patterns (non-unit boosts), two words per lane
+    (2049, 40, 4, 0.2, True),    # wider than the warp select: one CTA per frame
+    (96, 0, 1, 0.3, True),       # k = 0: no column wins
+    (64, 64, 1, 0.3, True),      # k = C: every nonzero column wins
+    (333, 50, 36, 0.1, True),    # frames with fewer than k nonzero overlaps, and with more
+])
+def test_dense_global_select_edge_cases(C, k, m, p, unit):
+    """Alg. 2 with global inhibition over a dense run at the extremes of the
+    per-frame select (one warp per frame up to 2048 columns)."""
+    boost = None if unit else synth.perm_uniform(C + 3, (C,), 0.5, 2.0)
+    case = _dense_case(C, 512, 70 + C % 97, k=k, m=m, boost=boost)
+    frames = _frames(37, 512, p, 71 + k)
+    act, _, ov = oracle_run(case, frames, False, want_ov=True)
+    if C == 333:
+        nz = (ov > 0).sum(axis=1)
+        assert ((nz > 0) & (nz < k)).any() and (nz >= k).any()  # the case is what it says
+    got, gov, lst, _, _ = _run(case, frames)
+    assert first_diff(got, act) is None
+    np.testing.assert_array_equal(gov, ov[-1])
+    np.testing.assert_array_equal(lst, np.flatnonzero(act[-1]))
+    if k == 0:
+        assert act.sum() == 0
+
+
+def test_dense_batch_with_a_local_member_uses_the_cta_select():
+    """A batch whose members mix global and local inhibition: every member's
+    winners still match the oracle (the per-frame CTA kernel runs them all)."""
+    cases = [_dense_case(512, 512, 80, k=12, m=2),
+             _dense_case(256, 512, 81, k=3, m=2, inhibition=1, gw=16, gh=16, radius=2),
+             _dense_case(1500, 512, 82, k=30, m=2)]
+    F = 20
+    frames = [_frames(F, 512, 0.25, 90 + i) for i in range(len(cases))]
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    dm = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
+    spg.sp_batch_sync(b)
+    masks = dm.cpu().numpy().view(np.uint32)
+    spg.sp_batch_destroy(b)
+    for i, c in enumerate(cases):
+        act, _, ov = oracle_run(c, frames[i], False, want_ov=True)
+        got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+        assert first_diff(got, act) is None, f"member {i}"
+        np.testing.assert_array_equal(spg.sp_active_columns(hs[i]), np.flatnonzero(act[-1]))
+        spg.sp_destroy(hs[i])
+
+
+def test_dense_connection_image_follows_learning():
+    """An inference run builds the connection image; learning frames in
+    between change the permanences, so the next run must rebuild it."""
+    case = _dense_case(512, 512, 49, k=10, m=2)
+    frames = _frames(70, 512, 0.3, 50)
+    packed = wl.pack(frames)
+    h = spg.sp_create_from_state(case.config(), case.idx, case.perm, case.boost)
+    stream = torch.cuda.current_stream()
+    d = torch.from_numpy(packed.view(np.int32)).cuda()
+    dm = torch.zeros((70, 16), dtype=torch.int32, device="cuda")
+    spg.sp_compute_frames_device(h, d[:30], 30, packed.shape[1], False, dm[:30], stream)
+    for t in range(30, 38):
+        spg.sp_compute(h, packed[t], True)
+    spg.sp_compute_frames_device(h, d[38:], 32, packed.shape[1], False, dm[38:], stream)
+    spg.sp_sync(h)
+    act0, _, _ = oracle_run(case, frames[:30], False)
+    _, perm, _ = oracle_run(case, frames[30:38], True)
+    act1, _, _ = oracle_run(case, frames[38:], False, perm=perm)
+    got = dense(dm.cpu().numpy().view(np.uint32), 512)
+    assert first_diff(got[:30], act0) is None
+    assert first_diff(got[38:], act1) is None
+    np.testing.assert_array_equal(spg.sp_get_permanences(h), perm)
+    spg.sp_destroy(h)
+
+
+def test_dense_batch_connection_image_follows_batch_learning():
+    """Batch inference, then learning frames through the batch, then
+    inference again: the second inference sees the learned permanences."""
+    cases = [_dense_case(256, 512, 100 + i, k=8, m=2) for i in range(3)]
+    F = 24
+    frames = [_frames(2 * F + 4, 512, 0.3, 110 + i) for i in range(3)]
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    mw = info["mask_words"]
+    stream = torch.cuda.current_stream()
+
+    def frames_dev(lo, hi):
+        bf = wl.batch_frames([wl.pack(f[lo:hi]) for f in frames], fo, fw)
+        return torch.from_numpy(bf.view(np.int32)).cuda()
+
+    dm0 = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_infer_device(b, frames_dev(0, F), F, fw, dm0, mw, stream)
+    dl = torch.zeros((4, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_compute_device(b, frames_dev(F, F + 4), 4, fw, True, dl, mw, stream)
+    dm1 = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_infer_device(b, frames_dev(F + 4, 2 * F + 4), F, fw, dm1, mw, stream)
+    spg.sp_batch_sync(b)
+    m0 = dm0.cpu().numpy().view(np.uint32)
+    m1 = dm1.cpu().numpy().view(np.uint32)
+    spg.sp_batch_destroy(b)
+    for i, c in enumerate(cases):
+        sl = slice(int(mo[i]), int(mo[i]) + (c.C + 31) // 32)
+        a0, _, _ = oracle_run(c, frames[i][:F], False)
+        _, perm, _ = oracle_run(c, frames[i][F:F + 4], True)
+        a1, _, _ = oracle_run(c, frames[i][F + 4:], False, perm=perm)
+        assert first_diff(dense(m0[:, sl], c.C), a0) is None, f"member {i} before"
+        assert first_diff(dense(m1[:, sl], c.C), a1) is None, f"member {i} after"
         spg.sp_destroy(hs[i])
