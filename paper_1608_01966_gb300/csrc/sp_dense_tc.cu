@@ -38,6 +38,7 @@
 // issued, frees its tensor memory and returns.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 
 #include "../../include/sp.h"
 #include "sp_device.cuh"
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
   __shared__ uint32_t s_taddr;
   __shared__ volatile uint32_t s_fail;
   __shared__ uint32_t s_issued, s_consumed;
+  __shared__ __align__(16) float s_boost[kTN];
   DenseArgs a;  // kept in registers
   if (L.many)
     a = L.many[blockIdx.z];
@@ -199,7 +201,10 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
     a = L.one;
   const uint32_t t = threadIdx.x, warp = t >> 5, lane = t & 31u;
   const uint32_t f0 = blockIdx.y * kTM, c0 = blockIdx.x * kTN;
+  // the per-frame selection may be scheduled now: it waits for this grid
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   if (f0 >= a.n_frames || c0 >= a.C) return;  // a smaller SP of the launch
+  s_boost[t] = c0 + t < a.C ? __ldg(a.boost + c0 + t) : 0.0f;  // kThreads == kTN
 
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -222,6 +227,8 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
+  // the frame image (and everything before it) is complete from here on
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   const uint32_t taddr = s_taddr;
   const uint32_t n = a.n_slices;
   const uint8_t* ablk = a.aimg + (uint64_t)blockIdx.y * n * kABytes;
@@ -279,32 +286,41 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
   if (!ok) {
     if (t == 0) atomicExch(a.err, 1u);
   } else {
-    // ---- epilogue: warp w reads accumulator lanes 32(w % 4) .. + 31 (frames)
-    // and columns 128(w / 4) .. + 127; each 32 x 32 block goes through shared
-    // memory (the stages are free now) so that every store writes 32
-    // consecutive columns of one frame
-    float* tr = reinterpret_cast<float*>(smem) + warp * 32u * 33u;
+    // ---- epilogue: warp w reads accumulator lanes 32(w % 4) .. + 31 (lane i:
+    // frame f0 + 32(w % 4) + i) and columns 128(w / 4) .. + 127, 32 at a time
+    // (register j: column cb + j); each lane writes its frame's 32 overlaps as
+    // eight 16-byte stores.  The raw counts are exact integers in fp32, so
+    // the comparison with min_overlap (counts never reach 2^24) and the one
+    // multiply by the boost are Alg. 1's tail as written.
     const uint32_t q = warp & 3u, h = warp >> 2;
+    const uint32_t f = f0 + q * 32u + lane;
+    const float m = (float)min(a.min_overlap, 1u << 24);
+    const bool vec = (a.C & 3u) == 0u;
+    float* row = a.ov + (uint64_t)f * a.C;
 #pragma unroll 1
     for (uint32_t cb = h * 128u; cb < h * 128u + 128u; cb += 32u) {
       uint32_t r[32];
       tmem_ld32(taddr + ((q * 32u) << 16) + cb, r);
+      float v[32];
 #pragma unroll
-      for (uint32_t j = 0; j < 32; ++j) tr[lane * 33u + j] = __uint_as_float(r[j]);
-      __syncwarp();
-      const uint32_t c = c0 + cb + lane;
-      const bool col_ok = c < a.C;
-      const float b = col_ok ? __ldg(a.boost + c) : 0.0f;
-      const uint32_t fr0 = f0 + q * 32u;
-      float* out = a.ov + (uint64_t)fr0 * a.C + c;
-#pragma unroll 4
-      for (uint32_t i = 0; i < 32u; ++i) {
-        if (fr0 + i < a.n_frames && col_ok) {
-          const uint32_t raw = (uint32_t)tr[i * 33u + lane];
-          out[(uint64_t)i * a.C] = dev::boosted(raw, a.min_overlap, b);
+      for (uint32_t j = 0; j < 32u; ++j) {
+        const float raw = __uint_as_float(r[j]);
+        v[j] = raw < m ? 0.0f : __fmul_rn(raw, s_boost[cb + j]);
+      }
+      const uint32_t c = c0 + cb;
+      if (f < a.n_frames) {
+        if (vec && c + 32u <= a.C) {
+#pragma unroll
+          for (uint32_t j = 0; j < 32u; j += 4u)
+            *reinterpret_cast<float4*>(row + c + j) =
+                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+#pragma unroll
+          for (uint32_t j = 0; j < 32u; ++j)
+            if (c + j < a.C) row[c + j] = v[j];
         }
       }
-      __syncwarp();
+      __syncwarp();  // converged again before the next tcgen05.ld
     }
   }
   fence_before_sync();
@@ -394,7 +410,7 @@ __global__ void __launch_bounds__(kStepThreads) sp_frame_inhibit_kernel(const In
 constexpr uint32_t kSelectWarps = 4;  // frames per CTA
 
 template <int V>  // overlaps per lane: at most 32 * V columns
-__global__ void __launch_bounds__(kSelectWarps * 32, V <= 32 ? 8 : 4) sp_frame_select_warp_kernel(
+__global__ void __launch_bounds__(kSelectWarps * 32, V <= 32 ? 7 : 3) sp_frame_select_warp_kernel(
     const InhibitLaunch L) {
   constexpr int Q = (V + 31) / 32;  // mask words per lane
   FrameInhibitArgs a;  // kept in registers
@@ -402,6 +418,11 @@ __global__ void __launch_bounds__(kSelectWarps * 32, V <= 32 ? 8 : 4) sp_frame_s
     a = L.many[blockIdx.y];
   else
     a = L.one;
+  __shared__ uint32_t s_hist[kSelectWarps][64];
+  // the overlaps are the previous kernel's output; the next run's frame
+  // image may be prepared once this run's overlaps are final
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t f = blockIdx.x * kSelectWarps + (threadIdx.x >> 5);
   if (f >= a.n_frames) return;
@@ -430,6 +451,27 @@ __global__ void __launch_bounds__(kSelectWarps * 32, V <= 32 ? 8 : 4) sp_frame_s
     }
     if (lo == vmax) {
       T = vmax;
+    } else if (a.unit_S && k <= 32u && vmax - lo < 64u) {
+      // integer overlaps in a short range [lo, vmax]: count them per value
+      // (only those >= lo) and take T as the largest value with at least k
+      // overlaps at or above it; lane l holds values lo + 2l and lo + 2l + 1
+      uint32_t* hist = s_hist[threadIdx.x >> 5];
+      hist[lane] = 0u;
+      hist[lane + 32u] = 0u;
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (key[j] >= lo) atomicAdd(hist + (key[j] - lo), 1u);
+      __syncwarp();
+      const uint32_t h0 = hist[2u * lane], h1 = hist[2u * lane + 1u];
+      uint32_t suf = h0 + h1;  // becomes the count of overlaps >= lo + 2 lane
+#pragma unroll
+      for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(kFull, suf, o);
+        if (lane + o < 32u) suf += y;
+      }
+      const uint32_t best = suf - h0 >= k ? 2u * lane + 2u : (suf >= k ? 2u * lane + 1u : 0u);
+      T = lo + __reduce_max_sync(kFull, best) - 1u;  // count(>= lo) >= k: best >= 1 somewhere
     } else {
       const int d = 31 - __clz(lo ^ vmax);  // highest bit where the bounds differ
       T = d == 31 ? 0u : vmax & ~((2u << d) - 1u);
@@ -596,6 +638,10 @@ __global__ void __launch_bounds__(256) sp_conn_image_kernel(const DenseLaunch L)
 // X[f][i] = bit i of frame f as e4m3 {0, 1}; bits at or past K are zero
 // whatever the frame's unused high bits hold.
 __global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L) {
+  // the product may be scheduled now (it waits for this grid); the image is
+  // written only once the previous run has finished with it
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   DenseArgs a;
   if (L.many)
     a = L.many[blockIdx.y];
@@ -616,6 +662,36 @@ __global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L
         make_uint4(fp8_nibble(bits & 15u), fp8_nibble((bits >> 4) & 15u),
                    fp8_nibble((bits >> 8) & 15u), fp8_nibble(bits >> 12));
   }
+}
+
+}  // namespace
+
+namespace {
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel on the stream finishes; it orders itself with
+// griddepcontrol.wait where it reads that kernel's output (SP_DISABLE_PDL=1:
+// plain stream order).
+template <typename Arg>
+cudaError_t launch_pdl(void (*kernel)(Arg), dim3 grid, uint32_t threads, size_t smem,
+                       cudaStream_t stream, const Arg& arg) {
+  static const bool pdl = [] {
+    const char* e = std::getenv("SP_DISABLE_PDL");
+    return !(e && e[0] == '1');
+  }();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, arg);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -659,19 +735,15 @@ cudaError_t launch_conn_image_one(const DenseArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_frame_image(const DenseArgs* args, uint32_t n, uint32_t max_frames,
                                uint32_t max_K, cudaStream_t stream) {
-  DenseLaunch L{args, DenseArgs{}};
-  sp_frame_image_kernel<<<image_grid(dense_aimg_bytes(max_frames, max_K) / 16u, n), 256, 0,
-                          stream>>>(L);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  const DenseLaunch L{args, DenseArgs{}};
+  return launch_pdl(sp_frame_image_kernel, image_grid(dense_aimg_bytes(max_frames, max_K) / 16u, n),
+                    256, 0, stream, L);
 }
 
 cudaError_t launch_frame_image_one(const DenseArgs& a, cudaStream_t stream) {
-  DenseLaunch L{nullptr, a};
-  sp_frame_image_kernel<<<image_grid(dense_aimg_bytes(a.n_frames, a.K) / 16u, 1u), 256, 0,
-                          stream>>>(L);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  const DenseLaunch L{nullptr, a};
+  return launch_pdl(sp_frame_image_kernel, image_grid(dense_aimg_bytes(a.n_frames, a.K) / 16u, 1u),
+                    256, 0, stream, L);
 }
 
 // Four stages of 48 KB: one CTA per SM, so its 256-column accumulator never
@@ -685,19 +757,15 @@ cudaError_t dense_init() {
 
 cudaError_t launch_dense_overlap(const DenseArgs& a, cudaStream_t stream) {
   const dim3 grid((a.C + kTN - 1) / kTN, (a.n_frames + kTM - 1) / kTM, 1);
-  DenseLaunch L{nullptr, a};
-  sp_dense_overlap_kernel<<<grid, kThreads, dense_smem_bytes(), stream>>>(L);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  const DenseLaunch L{nullptr, a};
+  return launch_pdl(sp_dense_overlap_kernel, grid, kThreads, dense_smem_bytes(), stream, L);
 }
 
 cudaError_t launch_dense_overlap_many(const DenseArgs* args, uint32_t n, uint32_t max_C,
                                       uint32_t max_frames, cudaStream_t stream) {
   const dim3 grid((max_C + kTN - 1) / kTN, (max_frames + kTM - 1) / kTM, n);
-  DenseLaunch L{args, DenseArgs{}};
-  sp_dense_overlap_kernel<<<grid, kThreads, dense_smem_bytes(), stream>>>(L);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  const DenseLaunch L{args, DenseArgs{}};
+  return launch_pdl(sp_dense_overlap_kernel, grid, kThreads, dense_smem_bytes(), stream, L);
 }
 
 size_t frame_inhibit_smem(uint32_t C, uint32_t unit_S) {
@@ -719,11 +787,8 @@ cudaError_t launch_select_warp(const InhibitLaunch& L, uint32_t max_C, uint32_t 
                                uint32_t n, cudaStream_t stream) {
   const dim3 grid((max_frames + kSelectWarps - 1) / kSelectWarps, n, 1);
   if (max_C <= 1024u)
-    sp_frame_select_warp_kernel<32><<<grid, kSelectWarps * 32, 0, stream>>>(L);
-  else
-    sp_frame_select_warp_kernel<64><<<grid, kSelectWarps * 32, 0, stream>>>(L);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+    return launch_pdl(sp_frame_select_warp_kernel<32>, grid, kSelectWarps * 32, 0, stream, L);
+  return launch_pdl(sp_frame_select_warp_kernel<64>, grid, kSelectWarps * 32, 0, stream, L);
 }
 
 bool select_warp_fits(uint32_t max_C) { return max_C <= 2048u; }
