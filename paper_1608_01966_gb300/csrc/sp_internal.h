@@ -93,10 +93,11 @@ struct GraphKey {
   bool pending;
   bool unit_boost;  // selects the histogram path baked into the recorded launches
   uint64_t mstride; // mask stride (batches)
+  uint64_t extra = 0;  // dense runs: launch shape and buffer generations baked into the launches
   bool operator==(const GraphKey& o) const {
     return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
            cur == o.cur && pending == o.pending && unit_boost == o.unit_boost &&
-           mstride == o.mstride;
+           mstride == o.mstride && extra == o.extra;
   }
 };
 
@@ -170,6 +171,7 @@ struct sp_handle {
   uint8_t* d_aimg = nullptr;        // e4m3 frame image of a dense run
   size_t aimg_cap = 0;              // bytes of d_aimg
   bool bimg_stale = true;           // the permanences may have changed since d_bimg was built
+  uint32_t run_gen = 0;             // bumped whenever d_run_ov / d_run_masks are reallocated
   bool unit_boost = true;
   uint32_t* h_result = nullptr;  // pinned [1 + C]
   cudaStream_t own_stream = nullptr;

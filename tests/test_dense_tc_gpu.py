@@ -270,3 +270,49 @@ def test_dense_batch_connection_image_follows_batch_learning():
         assert first_diff(dense(m0[:, sl], c.C), a0) is None, f"member {i} before"
         assert first_diff(dense(m1[:, sl], c.C), a1) is None, f"member {i} after"
         spg.sp_destroy(hs[i])
+
+
+def test_dense_batch_repeated_runs_replay_recorded_launches():
+    """Runs that repeat earlier frames, masks and buffer parity replay the
+    launches recorded for them; a longer run in between reallocates the run
+    buffers, which no replay may keep using.  Winners, last-frame lists and
+    duty cycles (tracked through the runs without caller masks too) against
+    the oracle (the last two read once the batch is gone)."""
+    import oracle
+    cases = [_dense_case(256, 512, 120 + i, k=6, m=2) for i in range(2)]
+    hs = [spg.sp_create_from_state(c.config(duty_period=20.0), c.idx, c.perm, c.boost)
+          for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    mw = info["mask_words"]
+    stream = torch.cuda.current_stream()
+    sizes = {"A": 16, "B": 16, "C": 40}
+    frames = {name: [_frames(F, 512, 0.25 + 0.05 * i, 130 + 10 * j + i) for i in range(2)]
+              for j, (name, F) in enumerate(sizes.items())}
+    dev = {name: torch.from_numpy(wl.batch_frames([wl.pack(f) for f in fr], fo, fw)
+                                  .view(np.int32)).cuda() for name, fr in frames.items()}
+    dm = torch.zeros((40, mw), dtype=torch.int32, device="cuda")
+    duty = [np.zeros(256, np.float32) for _ in cases]
+    last = [None] * len(cases)
+    for name, with_masks in [("A", True), ("B", False), ("A", True), ("B", False), ("C", False),
+                             ("A", True), ("B", False), ("A", True)]:
+        F = sizes[name]
+        dm.zero_()
+        spg.sp_batch_infer_device(b, dev[name], F, fw, dm[:F] if with_masks else None, mw, stream)
+        spg.sp_batch_sync(b)
+        masks = dm.cpu().numpy().view(np.uint32)
+        for i, c in enumerate(cases):
+            act, _, _ = oracle_run(c, frames[name][i], False)
+            for t in range(F):
+                oracle.duty_update(duty[i], act[t], 20.0)
+            if with_masks:
+                got = dense(masks[:F, int(mo[i]):int(mo[i]) + c.C // 32], c.C)
+                assert first_diff(got, act) is None, (name, i)
+            last[i] = act[-1]
+    spg.sp_batch_destroy(b)  # members answer queries again
+    for i in range(len(cases)):
+        np.testing.assert_array_equal(spg.sp_get_duty_cycles(hs[i]), duty[i])
+        np.testing.assert_array_equal(spg.sp_active_columns(hs[i]), np.flatnonzero(last[i]))
+        spg.sp_destroy(hs[i])
