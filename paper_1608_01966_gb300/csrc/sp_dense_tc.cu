@@ -282,21 +282,25 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
   }
   // every thread: the accumulator (and the stages' last readers) are done
   if (!mbar_wait_bounded(&done, 0u)) ok = false;
+  ok = __syncthreads_and(ok) != 0;  // one decision for the whole CTA (warp-wide loads below)
   fence_after_sync();
   if (!ok) {
     if (t == 0) atomicExch(a.err, 1u);
   } else {
     // ---- epilogue: warp w reads accumulator lanes 32(w % 4) .. + 31 (lane i:
     // frame f0 + 32(w % 4) + i) and columns 128(w / 4) .. + 127, 32 at a time
-    // (register j: column cb + j); each lane writes its frame's 32 overlaps as
-    // eight 16-byte stores.  The raw counts are exact integers in fp32, so
-    // the comparison with min_overlap (counts never reach 2^24) and the one
-    // multiply by the boost are Alg. 1's tail as written.
+    // (register j: column cb + j).  The raw counts are exact integers in
+    // fp32, so the comparison with min_overlap (counts never reach 2^24) and
+    // the one multiply by the boost are Alg. 1's tail as written.  Each 32 x
+    // 32 block goes through a 4 KB shared-memory tile (the stages are free
+    // now) whose 16-byte chunk j of row i sits at chunk j ^ (i % 8): lanes
+    // write their rows and read back 8 lanes per row without bank conflicts,
+    // and every store instruction then writes four whole 128-byte rows.
     const uint32_t q = warp & 3u, h = warp >> 2;
-    const uint32_t f = f0 + q * 32u + lane;
+    const uint32_t fr0 = f0 + q * 32u;
     const float m = (float)min(a.min_overlap, 1u << 24);
     const bool vec = (a.C & 3u) == 0u;
-    float* row = a.ov + (uint64_t)f * a.C;
+    float4* tile = reinterpret_cast<float4*>(smem) + warp * 256u;  // [32 rows][8 chunks]
 #pragma unroll 1
     for (uint32_t cb = h * 128u; cb < h * 128u + 128u; cb += 32u) {
       uint32_t r[32];
@@ -308,19 +312,27 @@ __global__ void __launch_bounds__(kThreads, 1) sp_dense_overlap_kernel(const Den
         v[j] = raw < m ? 0.0f : __fmul_rn(raw, s_boost[cb + j]);
       }
       const uint32_t c = c0 + cb;
-      if (f < a.n_frames) {
-        if (vec && c + 32u <= a.C) {
+      if (vec && c + 32u <= a.C) {
 #pragma unroll
-          for (uint32_t j = 0; j < 32u; j += 4u)
-            *reinterpret_cast<float4*>(row + c + j) =
-                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
+        for (uint32_t j = 0; j < 8u; ++j)
+          tile[lane * 8u + (j ^ (lane & 7u))] =
+              make_float4(v[4u * j], v[4u * j + 1u], v[4u * j + 2u], v[4u * j + 3u]);
+        __syncwarp();
+        const uint32_t chunk = lane & 7u;
 #pragma unroll
-          for (uint32_t j = 0; j < 32u; ++j)
-            if (c + j < a.C) row[c + j] = v[j];
+        for (uint32_t i = 0; i < 8u; ++i) {
+          const uint32_t row = 4u * i + (lane >> 3);
+          const float4 x = tile[row * 8u + (chunk ^ (row & 7u))];
+          if (fr0 + row < a.n_frames)
+            *reinterpret_cast<float4*>(a.ov + (uint64_t)(fr0 + row) * a.C + c + 4u * chunk) = x;
         }
+      } else if (fr0 + lane < a.n_frames) {
+        float* out = a.ov + (uint64_t)(fr0 + lane) * a.C;
+#pragma unroll
+        for (uint32_t j = 0; j < 32u; ++j)
+          if (c + j < a.C) out[c + j] = v[j];
       }
-      __syncwarp();  // converged again before the next tcgen05.ld
+      __syncwarp();  // tile reused; converged again before the next tcgen05.ld
     }
   }
   fence_before_sync();
