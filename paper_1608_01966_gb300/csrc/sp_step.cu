@@ -337,7 +337,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     c_step = nb * kStepWarps;
   }
   auto publish = [&](uint32_t c, uint32_t raw) {
-    a.ov[c] = dev::boosted(raw, a.min_overlap, __ldg(a.boost + c));
+    // a histogram is kept only when every boost is exactly 1, and then the
+    // product is the count itself: no load stalls the warp here
+    a.ov[c] = dev::boosted(raw, a.min_overlap, a.hist ? 1.0f : __ldg(a.boost + c));
     // unit boosts: the overlap is the count, histogrammed for the select
     if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
   };
