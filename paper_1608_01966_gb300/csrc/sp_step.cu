@@ -92,7 +92,7 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
 // never touch permanences.
 
 #ifndef SP_COMPACT_COLS
-#define SP_COMPACT_COLS 2
+#define SP_COMPACT_COLS 4
 #endif
 constexpr int kCompactCols = SP_COMPACT_COLS;
 
