@@ -272,13 +272,17 @@ def test_dense_batch_connection_image_follows_batch_learning():
         spg.sp_destroy(hs[i])
 
 
-def test_dense_batch_repeated_runs_replay_recorded_launches():
+@pytest.mark.parametrize("graphs", [True, False])
+def test_dense_batch_repeated_runs_replay_recorded_launches(monkeypatch, graphs):
     """Runs that repeat earlier frames, masks and buffer parity replay the
-    launches recorded for them; a longer run in between reallocates the run
-    buffers, which no replay may keep using.  Winners, last-frame lists and
+    launches recorded for them (or, with graphs off, launch them directly,
+    chained by programmatic dependent launch); a longer run in between
+    reallocates the run buffers, which no replay may keep using.  Winners, last-frame lists and
     duty cycles (tracked through the runs without caller masks too) against
     the oracle (the last two read once the batch is gone)."""
     import oracle
+    if not graphs:
+        monkeypatch.setenv("SP_DISABLE_GRAPHS", "1")
     cases = [_dense_case(256, 512, 120 + i, k=6, m=2) for i in range(2)]
     hs = [spg.sp_create_from_state(c.config(duty_period=20.0), c.idx, c.perm, c.boost)
           for c in cases]
