@@ -96,6 +96,14 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
 #endif
 constexpr int kCompactCols = SP_COMPACT_COLS;
 
+// Lane l of a column holds synapses l, l + L, ..., l + 7L (L = S / 8 lanes in
+// use): the 8 offsets at positions 8l .. 8l + 7 and connected bits in byte l,
+// so the k-th gather of all lanes reads 32 neighbouring synapses of the
+// sorted pool (SP_COMPACT_STRIDED=0: lane l holds synapses 8l .. 8l + 7).
+#ifndef SP_COMPACT_STRIDED
+#define SP_COMPACT_STRIDED 1
+#endif
+
 __device__ __forceinline__ uint32_t off16(const uint4& o, int k) {
   const uint32_t w = k < 2 ? o.x : (k < 4 ? o.y : (k < 6 ? o.z : o.w));
   return (k & 1) ? (w >> 16) : (w & 0xffffu);
@@ -115,6 +123,19 @@ __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx
   if (act) {
     const uint4 o = reinterpret_cast<const uint4*>(cidx + (uint64_t)c * S)[lane];
     const uint32_t base = cbase[c];
+#if SP_COMPACT_STRIDED
+    float* prow = perm + (uint64_t)c * S + lane;
+    const uint32_t L = S >> 3;
+    float q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = prow[k * L];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      q[k] = learn_one(q[k], input_bit(x_prev, base + off16(o, k)), inc, dec);
+      nb |= (q[k] >= thr ? 1u : 0u) << k;
+      prow[k * L] = q[k];
+    }
+#else
     float4* p4 = reinterpret_cast<float4*>(perm + (uint64_t)c * S) + 2 * lane;
     float4 q[2] = {p4[0], p4[1]};
 #pragma unroll
@@ -125,6 +146,7 @@ __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx
     }
     p4[0] = q[0];
     p4[1] = q[1];
+#endif
   }
   uint32_t word = nb << (8u * (lane & 3));
   word |= __shfl_xor_sync(kFull, word, 1);
@@ -798,11 +820,24 @@ __global__ void __launch_bounds__(256) sp_compact_kernel(const uint32_t* idx, co
     if (lane == 0) atomicOr(wide, 1u);
     return;
   }
+#if SP_COMPACT_STRIDED
+  const uint32_t L = S >> 3;  // lanes in use; synapse s sits with lane s % L, slot s / L
+  for (uint32_t s = lane; s < S; s += 32)
+    cidx[(uint64_t)c * S + (s % L) * 8u + s / L] = (uint16_t)(row[s] - lo);
+  uint8_t* cb8 = reinterpret_cast<uint8_t*>(conn + (uint64_t)c * (S >> 5));
+  for (uint32_t l = lane; l < L; l += 32) {
+    uint32_t byte = 0;
+    for (uint32_t k = 0; k < 8u; ++k)
+      byte |= (perm[(uint64_t)c * S + l + k * L] >= thr ? 1u : 0u) << k;
+    cb8[l] = (uint8_t)byte;
+  }
+#else
   for (uint32_t s = lane; s < S; s += 32) {
     cidx[(uint64_t)c * S + s] = (uint16_t)(row[s] - lo);
     const uint32_t bits = __ballot_sync(kFull, perm[(uint64_t)c * S + s] >= thr);
     if (lane == 0) conn[(uint64_t)c * (S >> 5) + (s >> 5)] = bits;
   }
+#endif
   if (lane == 0) cbase[c] = lo;
 }
 
