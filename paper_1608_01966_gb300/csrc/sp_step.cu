@@ -85,11 +85,11 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
 
 // ---- compact form: 16-bit pool offsets and connected bits -------------------
 //
-// A lane holds 8 consecutive synapses of a column: one 16-byte vector of
-// offsets and one byte of connected bits, so a warp keeps kCompactCols
-// columns in flight with a few registers each.  A column that learns reads and
-// writes its fp32 permanences and rewrites its connected bits; the others
-// never touch permanences.
+// A lane holds 8 synapses of a column: one 16-byte vector of offsets and one
+// byte of connected bits, so a warp keeps kCompactCols columns in flight with
+// a few registers each.  A column that learns reads and writes its fp32
+// permanences and rewrites its connected bits; the others never touch
+// permanences.
 
 #ifndef SP_COMPACT_COLS
 #define SP_COMPACT_COLS 4
@@ -109,8 +109,8 @@ __device__ __forceinline__ uint32_t off16(const uint4& o, int k) {
   return (k & 1) ? (w >> 16) : (w & 0xffffu);
 }
 
-// Apply the pending learning to column c (lane: synapses 8 lane .. 8 lane + 7)
-// and return the lane's new byte of connected bits; writes perm and conn.
+// Apply the pending learning to column c (the lane's 8 synapses, as laid out
+// above) and return the lane's new byte of connected bits; writes perm and conn.
 // Rare (winners of the previous frame only), so kept out of line with its
 // own loads to leave the common path's registers alone.
 __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx,
