@@ -588,18 +588,20 @@ __global__ void sp_duty_run_kernel(const uint32_t* masks, uint32_t n_frames, uin
 }
 
 // Image blocks of one dense SP.  Unit u of a block (16 bytes: one row, 16
-// consecutive inputs) sits at byte 16u of the block: u = 64 (r / 8) +
-// 8 (chunk) + r % 8 for row r and 16-input chunk of the slice, which is the
-// core-matrix layout; unit g of the whole image is block g / U, unit g % U
-// (U = rows per tile x 8), so consecutive threads write consecutive 16 bytes.
+// consecutive inputs) sits at byte 16u of the block: u = 8 Q (r / 8) +
+// 8 (chunk) + r % 8 for row r and 16-input chunk of the slice (Q = kTK / 16
+// chunks per row), which is the core-matrix layout; unit g of the whole image
+// is block g / U, unit g % U (U = rows per tile x Q), so consecutive threads
+// write consecutive 16 bytes.
 __device__ __forceinline__ void image_unit(uint64_t g, uint32_t rows, uint32_t n_slices,
                                            uint32_t& row, uint32_t& k0) {
-  const uint32_t per = rows * 8u;  // units per block
+  constexpr uint32_t kChunks = kTK / 16u;  // 16-input chunks per row of a slice
+  const uint32_t per = rows * kChunks;     // units per block
   const uint64_t blk = g / per;
   const uint32_t u = (uint32_t)(g - blk * per);
   const uint32_t tile = (uint32_t)(blk / n_slices), slice = (uint32_t)(blk % n_slices);
-  row = tile * rows + (u >> 6) * 8u + (u & 7u);
-  k0 = slice * kTK + ((u >> 3) & 7u) * 16u;
+  row = tile * rows + (u / (8u * kChunks)) * 8u + (u & 7u);
+  k0 = slice * kTK + ((u >> 3) % kChunks) * 16u;
 }
 
 // Conn[c][i] = [perm[c][i] >= thr] as e4m3 {0, 1}; only SPs whose pack flag
@@ -612,7 +614,7 @@ __global__ void __launch_bounds__(256) sp_conn_image_kernel(const DenseLaunch L)
     a = L.one;
   if (!a.pack) return;
   const uint32_t n_ct = (a.C + kTN - 1) / kTN;
-  const uint64_t units = (uint64_t)n_ct * a.n_slices * kTN * 8u;
+  const uint64_t units = (uint64_t)n_ct * a.n_slices * kTN * (kTK / 16u);  // 16-byte units
   const bool vec = (a.K & 3u) == 0u;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < units;
        g += (uint64_t)gridDim.x * blockDim.x) {
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L
   else
     a = L.one;
   const uint32_t n_ft = (a.n_frames + kTM - 1) / kTM;
-  const uint64_t units = (uint64_t)n_ft * a.n_slices * kTM * 8u;
+  const uint64_t units = (uint64_t)n_ft * a.n_slices * kTM * (kTK / 16u);  // 16-byte units
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < units;
        g += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t f, k0;
