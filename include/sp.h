@@ -173,10 +173,15 @@ SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int lea
                                    void* stream);
 
 /* n_frames frames on the device, frame t at d_frames + t * frame_stride_words
- * (stride >= input_words), in order, all with the same learn flag; one fused
- * kernel per frame.  If d_active_masks is not NULL, frame t's active set is
- * written there as mask_words words at d_active_masks + t * mask_words.
- * Asynchronous on `stream` (NULL = the handle's stream). */
+ * (stride >= input_words), in order, all with the same learn flag, with the
+ * results of n_frames single-frame calls.  Execution: inference runs of an SP
+ * with dense pools go through the tensor cores (as sp_batch_infer_device);
+ * otherwise one persistent launch of a thread-block cluster holding the SP's
+ * state runs the whole sequence when the state fits, else one fused kernel
+ * per frame (replayed as a recorded graph for repeated sequences).  If
+ * d_active_masks is not NULL, frame t's active set is written there as
+ * mask_words words at d_active_masks + t * mask_words.  Asynchronous on
+ * `stream` (NULL = the handle's stream). */
 SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames,
                                           uint32_t n_frames, uint64_t frame_stride_words,
                                           int learn, uint32_t* d_active_masks,
@@ -312,12 +317,15 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
 /* Inference (no learning) over n_frames batch frames for a batch whose
  * members all have dense pools (every column's pool is its whole input,
  * S = n_in): the overlaps of every member and frame are one {0,1} matrix
- * product per member on the tensor cores (tcgen05, bf16 operands, fp32
+ * product per member on the tensor cores (tcgen05, e4m3 operands, fp32
  * accumulation; exact), all members in one launch, then Alg. 2 for every
- * frame of every member in a second launch.  Results are those of
- * n_frames calls of sp_batch_compute_device with learn = 0.  Frame and mask
- * layout as sp_batch_compute_device.  SP_ENOTSUP if a member's pools are not
- * dense. */
+ * frame of every member in a second launch; the frames are first laid out
+ * as operands in one more launch, and a member's connection operand is
+ * rebuilt (one launch for all such members) only when its permanences may
+ * have changed since it was last built.  Learning pending from an earlier
+ * batch step is applied first.  Results are those of n_frames calls of
+ * sp_batch_compute_device with learn = 0.  Frame and mask layout as
+ * sp_batch_compute_device.  SP_ENOTSUP if a member's pools are not dense. */
 SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
                                        uint64_t frame_stride_words, uint32_t* d_masks,
                                        uint64_t mask_stride_words, void* stream);
