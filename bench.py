@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 INSTANCES = 256
+REGIONS = 5  # timed regions of --steps steps each; the median is reported
 FRAME_POOL = 64
 SEQ_FRAMES = 500
 WORKLOAD = ("paper-scale frame SP x 256 independent instances: 960x540 blobbed frames, "
@@ -136,6 +137,17 @@ def compact_form(case):
     if case.S % 32 or case.S > 256:
         return False
     return int((case.idx.max(axis=1) - case.idx.min(axis=1)).max()) <= 0xFFFF
+
+
+def form_of(case):
+    return "compact" if compact_form(case) else "full"
+
+
+def form_bytes_per_frame(case, learn=True):
+    """Algorithmic bytes of one SP frame in the form the batch runs it on."""
+    if form_of(case) == "compact":
+        return compact_bytes_per_frame(case, learn)
+    return algorithmic_bytes_per_frame(case, learn)
 
 
 def compact_bytes_per_frame(case, learn=True):
@@ -298,7 +310,7 @@ def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
     info = spg.sp_batch_get_info(b)
     fo, mo = spg.sp_batch_offsets(b)
     fw = (info["frame_words"] + 3) // 4 * 4
-    fr = [wl.pack(wl.bernoulli_frames(i, c.n_in, dens[i], frames)) for i, c in enumerate(cases)]
+    fr = [wl.pack(f) for f in wl.uneven_frames(cases, dens, frames)]
     d = torch.from_numpy(wl.batch_frames(fr, fo, fw).view(np.int32)).to(dev)
     mw = info["mask_words"]
     dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
@@ -317,11 +329,19 @@ def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
     for h in hs:
         spg.sp_destroy(h)
     upd = sum(c.C for c in cases)
+    peak, kind = read_peaks()
+    moved = sum(form_bytes_per_frame(c) for c in cases)
+    gbs = moved / (ms / 1000.0) / 1e9
     return {"workload": f"{members} uneven SPs (C 128..4096, S 16..256, inputs 256..16384 bits), "
                         f"learning on, {frames} frames per persistent launch, autotuned",
             "cols_per_warp": cpw, "us_per_batch_frame": ms * 1000.0,
             "frames_per_s": members / (ms / 1000.0),
-            "column_updates_per_s": upd / (ms / 1000.0)}
+            "column_updates_per_s": upd / (ms / 1000.0),
+            "roofline": {"bound": "hbm", "kernel": "sp_batch_run_kernel", "achieved": gbs,
+                         "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
+                         "form_bytes_per_batch_frame": moved,
+                         "forms": {f: sum(1 for c in cases if form_of(c) == f)
+                                   for f in sorted({form_of(c) for c in cases})}}}
 
 
 def run_reference(args):
@@ -411,18 +431,10 @@ def run_dense_tc(spg, torch, dev, stream, members=16, frames=256, steps=5):
     overlaps (16 x 256 x 1024 x 1024 multiply-adds of {0,1} e4m3 operands)
     and one Alg. 2 launch per run; the connection images are built once (the
     permanences do not change without learning)."""
-    from paper_1608_01966_gb300 import synth, workloads as wl
+    from paper_1608_01966_gb300 import workloads as wl
     n_in, C = 1024, 1024
-    cases, packed = [], []
-    for i in range(members):
-        sd = synth.derive_seed(wl.BASE_SEED + 4, synth.PURPOSE_INSTANCE, 1000 + i)
-        idx = synth.pool_dense(C, n_in)
-        perm = synth.perm_uniform(synth.derive_seed(sd, synth.PURPOSE_PERM, 0), (C, n_in), 0.1, 0.3)
-        cases.append(wl.Case("dense", n_in, 1, C, n_in, idx, perm, np.ones(C, np.float32), k=20))
-        p = 0.02 + 0.18 * i / max(1, members - 1)
-        fr = np.stack([synth.frame_bernoulli(synth.derive_seed(sd, synth.PURPOSE_FRAME, t), n_in, p)
-                       for t in range(frames)])
-        packed.append(wl.pack(fr))
+    cases, fr = wl.dense_cases(members, frames, C=C, n_in=n_in)
+    packed = [wl.pack(f) for f in fr]
     hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
     b = spg.sp_batch_create(hs)
     info = spg.sp_batch_get_info(b)
@@ -597,21 +609,35 @@ def main():
     spg.sp_batch_sync(b)
     torch.cuda.synchronize()
 
+    # REGIONS timed regions of exactly K steps each (CUDA events on the
+    # launching stream, barrier + synchronize on both sides); the line reports
+    # the median region, max over ranks
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    launches0 = spg.sp_kernel_launch_count()
-    start.record(stream)
-    steps(warm, args.steps)
-    end.record(stream)
-    torch.cuda.synchronize()
-    launches = spg.sp_kernel_launch_count() - launches0
-    ms_local = start.elapsed_time(end) / args.steps
+    # about a second of the same steps under the clock sampler before the
+    # regions, so the samples see the GPU under this load (untimed)
+    t_next = warm
+    t_end = time.perf_counter() + 1.0
+    while time.perf_counter() < t_end:
+        steps(t_next, args.steps)
+        t_next += args.steps
+        torch.cuda.synchronize()
+    region_ms, launches = [], 0
+    for _ in range(REGIONS):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = spg.sp_kernel_launch_count()
+        start.record(stream)
+        steps(t_next, args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        launches = spg.sp_kernel_launch_count() - launches0
+        t_next += args.steps
+        region_ms.append(reduce_max(start.elapsed_time(end) / args.steps, dev))
     clk = clocks.stop()
-    ms = reduce_max(ms_local, dev)
+    ms = statistics.median(region_ms)
     if world > 1:
         dist.barrier()
     value = world * n / (ms / 1000.0)
@@ -669,11 +695,12 @@ def main():
                                    saturate_seconds=3.0)
 
     peak, peak_kind = read_peaks()
-    per_launch = sum(algorithmic_bytes_per_frame(c) for c in cases)
-    achieved = per_launch / (ms / 1000.0) / 1e9  # bytes of one step / time of one step
+    canonical = sum(algorithmic_bytes_per_frame(c) for c in cases)
     compact = all(compact_form(c) for c in cases)
-    moved = sum(compact_bytes_per_frame(c) if compact_form(c) else algorithmic_bytes_per_frame(c)
-                for c in cases)
+    moved = sum(form_bytes_per_frame(c) for c in cases)
+    # the algorithmic bytes of the form the kernel runs on, per step, over
+    # the average time of a step
+    achieved = moved / (ms / 1000.0) / 1e9
     persistent = (not args.per_frame_calls and args.steps > 1
                   and os.environ.get("SP_DISABLE_PERSISTENT", "0") != "1")
     kernel_name = "sp_batch_run_kernel" if persistent else "sp_batch_step_kernel"
@@ -686,10 +713,13 @@ def main():
         cpu = {"value": fps_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} SP frames of the same workload (first 16 instances in step "
                          f"order), one thread, ~{args.cpu_seconds:.0f} s"}
-        threads = os.cpu_count() or 1
+        threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (
+            os.cpu_count() or 1)
         fps_all, done_all = oracle_sample_parallel(cases[:max(16, threads)], pool_u8,
                                                    args.cpu_seconds / 2, threads)
         cpu["all_cores"] = {"value": fps_all, "unit": "frames/s", "cores": threads,
+                            "cores_note": "the cores this process may run on (its affinity "
+                                          f"mask); the host reports {os.cpu_count()}",
                             "sample": f"{done_all} SP frames, instances split over {threads} "
                                       f"threads, ~{args.cpu_seconds / 2:.0f} s"}
 
@@ -711,13 +741,15 @@ def main():
             "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_step": per_launch,
+                         "algorithmic_bytes_per_step": moved,
                          "form": ("compact: 16-bit pool offsets + connected bits, fp32 "
                                   "permanences touched only by learning columns") if compact
                                  else "full: 32-bit pools + fp32 permanences",
-                         "form_bytes_per_step": moved,
-                         "form_frac": moved / (ms / 1000.0) / 1e9 / peak,
+                         "traffic_over_algorithmic": (traffic / moved) if traffic else None,
+                         "canonical_bytes_per_step": canonical,
+                         "canonical_equiv_frac": canonical / (ms / 1000.0) / 1e9 / peak,
                          "avg_us_per_step": ms * 1000.0,
+                         "region_us_per_step": [r * 1000.0 for r in region_ms],
                          "steps_per_launch": steps_per_launch},
             "e2e": {"value": e2e_value, "unit": "frames/s",
                     "h2d_bytes_per_step": int(info["frame_words"] * 4),

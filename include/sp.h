@@ -187,6 +187,19 @@ SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames
                                           int learn, uint32_t* d_active_masks,
                                           void* stream);
 
+/* sp_compute_frames_device that also records the boosted overlaps of every
+ * frame -- Alg. 1's output (Section 1.1) before inhibition, the values
+ * Alg. 2 ranks -- so that each frame's overlaps, not only the last one's
+ * (sp_get_overlaps), can be checked: frame t's C floats go to
+ * d_overlaps + t * C (device, 4-byte aligned, caller-owned, n_frames * C
+ * floats).  d_overlaps NULL records nothing; every other argument, the
+ * execution and the results are those of sp_compute_frames_device.
+ * SP_EINVAL for a misaligned pointer (nothing enqueued). */
+SP_API sp_status sp_compute_frames_overlaps_device(sp_handle* h, const uint32_t* d_frames,
+                                                   uint32_t n_frames, uint64_t frame_stride_words,
+                                                   int learn, uint32_t* d_active_masks,
+                                                   float* d_overlaps, void* stream);
+
 /* n_frames frames from host memory (frame t at h_frames + t * stride words)
  * with their active masks written to host memory h_active_masks
  * ([n_frames][mask_words], NULL = not returned).  Copies are staged in
@@ -307,6 +320,23 @@ SP_API sp_status sp_batch_compute_device(sp_batch* b, const uint32_t* d_frames, 
                                          uint64_t frame_stride_words, int learn, uint32_t* d_masks,
                                          uint64_t mask_stride_words, void* stream);
 
+/* Batch overlap records: one record holds every member's boosted overlaps of
+ * one batch frame (Alg. 1, Section 1.1), member i's C_i floats at
+ * ov_off[i] (the sum of the earlier members' column counts); *ov_words
+ * receives the record's length.  Either pointer may be NULL. */
+SP_API sp_status sp_batch_overlap_offsets(const sp_batch* b, uint64_t* ov_off, uint64_t* ov_words);
+
+/* sp_batch_compute_device that also writes batch frame t's overlap record to
+ * d_overlaps + t * ov_stride floats (ov_stride >= the record length;
+ * device, 4-byte aligned, caller-owned); NULL records nothing.  Execution and
+ * results are otherwise those of sp_batch_compute_device.  SP_EINVAL for a
+ * short stride or a misaligned pointer. */
+SP_API sp_status sp_batch_compute_overlaps_device(sp_batch* b, const uint32_t* d_frames,
+                                                  uint32_t n_frames, uint64_t frame_stride_words,
+                                                  int learn, uint32_t* d_masks,
+                                                  uint64_t mask_stride_words, float* d_overlaps,
+                                                  uint64_t ov_stride, void* stream);
+
 /* The same from host memory: batch frames copied in (pinned memory gives
  * overlapped copies), mask records copied back to h_masks (NULL = not
  * returned).  Synchronous: returns when the masks are in host memory. */
@@ -329,6 +359,16 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
 SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
                                        uint64_t frame_stride_words, uint32_t* d_masks,
                                        uint64_t mask_stride_words, void* stream);
+
+/* sp_batch_infer_device that also writes batch frame t's overlap record (as
+ * sp_batch_compute_overlaps_device) to d_overlaps + t * ov_stride: the
+ * tensor-core product's boosted overlaps of every member and frame.  NULL
+ * records nothing. */
+SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_frames,
+                                                uint32_t n_frames, uint64_t frame_stride_words,
+                                                uint32_t* d_masks, uint64_t mask_stride_words,
+                                                float* d_overlaps, uint64_t ov_stride,
+                                                void* stream);
 
 /* Wait (bounded) until the batch's enqueued work has finished. */
 SP_API sp_status sp_batch_sync(sp_batch* b);
@@ -530,8 +570,10 @@ SP_API sp_status sp_encode_compute(sp_encoder* e, sp_handle* h, const uint8_t* h
  * -- different streams, or different threads without ordering -- race and
  * give wrong results: order them, e.g. all on one stream.
  *
- * The first call on each device does a one-time set-up with that device
- * current (it looks up the array's device address); make that first call
+ * Every call looks up the array's device address in the current device's
+ * context (a lookup that allocates nothing), so a device reset between calls
+ * needs no extra step from the caller.  The first call on a device may also
+ * load the library's device code into that context; make that first call
  * before any stream capture on that device.
  *
  * Arguments (device pointers on the current device; caller-owned; the call
@@ -539,8 +581,10 @@ SP_API sp_status sp_encode_compute(sp_encoder* e, sp_handle* h, const uint8_t* h
  *   cfg            scalars of the SP (input_w * input_h bits, num_columns C
  *                  <= SP_NOALLOC_MAX_COLUMNS, synapses_per_column S,
  *                  connect_threshold, perm_inc, perm_dec, min_overlap,
- *                  winners_set_size, inhibition, column grid, local_radius);
- *                  pool_mode, rf_*, perm_init_* and seed are ignored;
+ *                  winners_set_size, inhibition, column grid, local_radius),
+ *                  checked as sp_create checks them; pool_mode, rf_*,
+ *                  perm_init_*, seed and duty_period are ignored (no duty
+ *                  cycles are kept);
  *   d_idx          [C][S] input indices, each < input_w * input_h (not
  *                  checked: out-of-range indices read out of bounds);
  *   d_perm         [C][S] permanences, updated in place when learn != 0;

@@ -116,6 +116,8 @@ def lib():
         L.sp_compute_device.argtypes = [vp, vp, ct.c_int, vp]
         L.sp_compute_frames_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, ct.c_int, vp, vp]
         L.sp_compute_frames.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p]
+        L.sp_compute_frames_overlaps_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64,
+                                                        ct.c_int, vp, vp, vp]
         L.sp_active_columns.argtypes = [vp, _u32p, ct.c_uint32, _u32p]
         L.sp_get_overlaps.argtypes = [vp, _f32p]
         L.sp_get_permanences.argtypes = [vp, _f32p]
@@ -138,6 +140,13 @@ def lib():
                                               ct.c_uint64, vp]
         L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
                                        ct.c_uint64]
+        L.sp_batch_overlap_offsets.argtypes = [vp, ct.POINTER(ct.c_uint64),
+                                               ct.POINTER(ct.c_uint64)]
+        L.sp_batch_compute_overlaps_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64,
+                                                       ct.c_int, vp, ct.c_uint64, vp,
+                                                       ct.c_uint64, vp]
+        L.sp_batch_infer_overlaps_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp,
+                                                     ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_batch_sync.argtypes = [vp]
         L.sp_batch_autotune.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, _u32p]
         L.sp_batch_infer_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
@@ -266,6 +275,14 @@ def sp_compute_frames_device(h, d_frames, n_frames, stride_words, learn, d_activ
                                           _stream(stream)), "sp_compute_frames_device")
 
 
+def sp_compute_frames_overlaps_device(h, d_frames, n_frames, stride_words, learn,
+                                      d_active_masks=None, d_overlaps=None, stream=None):
+    _check(lib().sp_compute_frames_overlaps_device(h, _addr(d_frames), n_frames, stride_words,
+                                                   1 if learn else 0, _addr(d_active_masks),
+                                                   _addr(d_overlaps), _stream(stream)),
+           "sp_compute_frames_overlaps_device")
+
+
 def sp_compute_frames(h, frames, learn, masks_out=None):
     """frames: uint32 [n][stride] host array (pinned memory overlaps the copies);
     masks_out: uint32 [n][mask_words] host array or None."""
@@ -375,6 +392,35 @@ def sp_batch_compute_device(b, d_frames, n_frames, stride_words, learn, d_masks=
     _check(lib().sp_batch_compute_device(b, _addr(d_frames), n_frames, stride_words,
                                          1 if learn else 0, _addr(d_masks), mask_stride_words,
                                          _stream(stream)), "sp_batch_compute_device")
+
+
+def sp_batch_overlap_offsets(b):
+    """Per-member float offsets inside a batch overlap record, and its length."""
+    n = sp_batch_get_info(b)["members"]
+    oo = np.zeros(n, np.uint64)
+    words = ct.c_uint64()
+    _check(lib().sp_batch_overlap_offsets(b, oo.ctypes.data_as(ct.POINTER(ct.c_uint64)),
+                                          ct.byref(words)), "sp_batch_overlap_offsets")
+    return oo, words.value
+
+
+def sp_batch_compute_overlaps_device(b, d_frames, n_frames, stride_words, learn, d_masks=None,
+                                     mask_stride_words=0, d_overlaps=None, ov_stride=0,
+                                     stream=None):
+    _check(lib().sp_batch_compute_overlaps_device(b, _addr(d_frames), n_frames, stride_words,
+                                                  1 if learn else 0, _addr(d_masks),
+                                                  mask_stride_words, _addr(d_overlaps),
+                                                  ov_stride, _stream(stream)),
+           "sp_batch_compute_overlaps_device")
+
+
+def sp_batch_infer_overlaps_device(b, d_frames, n_frames, stride_words, d_masks=None,
+                                   mask_stride_words=0, d_overlaps=None, ov_stride=0,
+                                   stream=None):
+    _check(lib().sp_batch_infer_overlaps_device(b, _addr(d_frames), n_frames, stride_words,
+                                                _addr(d_masks), mask_stride_words,
+                                                _addr(d_overlaps), ov_stride, _stream(stream)),
+           "sp_batch_infer_overlaps_device")
 
 
 def sp_batch_autotune(b, d_frames, n_frames, stride_words):

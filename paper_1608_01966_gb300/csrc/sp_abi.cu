@@ -45,7 +45,8 @@ void sp::set_last_error(const char* fmt, ...) {
 
 using namespace sp::rt;
 
-namespace {
+namespace sp {
+namespace rt {
 
 sp_status validate_config(const sp_config* c) {
   if (!c) return fail(SP_EINVAL, "config is NULL");
@@ -75,6 +76,11 @@ sp_status validate_config(const sp_config* c) {
     return fail(SP_EINVAL, "local inhibition needs a column grid");
   return SP_OK;
 }
+
+}  // namespace rt
+}  // namespace sp
+
+namespace {
 
 sp_status validate_seeded(const sp_config* c) {
   const uint64_t n_in = (uint64_t)c->input_w * c->input_h;
@@ -319,8 +325,9 @@ sp::StepArgs base_args(const sp_handle* h) {
 // frame's (used iff learning is pending); x_save, if set, receives a copy of
 // x for the next frame's learning.
 sp_status enqueue_frame(sp_handle* h, cudaStream_t st, const uint32_t* x, const uint32_t* x_prev,
-                        uint32_t* x_save, int learn, uint32_t* mask_copy) {
+                        uint32_t* x_save, int learn, uint32_t* mask_copy, float* ov_copy = nullptr) {
   sp::StepArgs a = base_args(h);
+  a.ov_copy = ov_copy;
   const int cur = h->cur;
   a.x = x;
   if (h->pending) {
@@ -359,13 +366,14 @@ sp_status flush_learning(sp_handle* h) {
 // current (parity, pending) state.  Within the call the previous frame is
 // read in place; the last frame is saved when learning, for the next call.
 sp_status enqueue_sequence(sp_handle* h, cudaStream_t st, const uint32_t* x_base, uint32_t n,
-                           uint64_t stride, int learn, uint32_t* masks) {
+                           uint64_t stride, int learn, uint32_t* masks, float* ovs) {
   for (uint32_t t = 0; t < n; ++t) {
     const uint32_t* x = x_base + (uint64_t)t * stride;
     const uint32_t* x_prev = t ? x - stride : h->d_xsave[h->cur ^ 1];
     uint32_t* x_save = (learn && t + 1 == n) ? h->d_xsave[h->cur] : nullptr;
     uint32_t* mc = masks ? masks + (uint64_t)t * h->mask_words : nullptr;
-    sp_status s = enqueue_frame(h, st, x, x_prev, x_save, learn, mc);
+    float* oc = ovs ? ovs + (uint64_t)t * h->C : nullptr;
+    sp_status s = enqueue_frame(h, st, x, x_prev, x_save, learn, mc, oc);
     if (s != SP_OK) return s;
   }
   return SP_OK;
@@ -426,7 +434,7 @@ sp::DenseArgs dense_args(sp_handle* h, const uint32_t* x_base, uint32_t n, uint6
 }
 
 sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
-                    uint32_t* masks) {
+                    uint32_t* masks, float* ovs) {
   sp_status s = flush_learning(h);
   if (s != SP_OK) return s;
   if ((s = ensure_dense_buffers(h, n)) != SP_OK) return s;
@@ -460,6 +468,9 @@ sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t s
   if (duty)
     SP_CUDA(sp::launch_duty_run(f.masks_out, n, h->mask_words, h->C, h->d_duty,
                                 h->cfg.duty_period, h->stream));
+  if (ovs)  // the run's overlaps, every frame, for the caller's record
+    SP_CUDA(cudaMemcpyAsync(ovs, h->d_run_ov, (size_t)n * h->C * 4, cudaMemcpyDeviceToDevice,
+                            h->stream));
   h->pending = false;
   h->cur ^= 1;
   h->frames += n;
@@ -467,10 +478,10 @@ sp_status run_dense(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t s
 }
 
 sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_t stride,
-                       int learn, uint32_t* masks) {
+                       int learn, uint32_t* masks, float* ovs = nullptr) {
   if (learn) h->bimg_stale = true;
   if (!learn && h->dense && n >= kDenseMinFrames && dense_enabled())
-    return run_dense(h, x_base, n, stride, masks);
+    return run_dense(h, x_base, n, stride, masks, ovs);
   if (h->seq_ok && n >= kSeqMinFrames && seq_enabled()) {
     sp::SeqArgs a{};
     a.idx = h->d_idx;
@@ -488,6 +499,7 @@ sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_
     a.mask_last = h->d_mask[h->cur];
     a.result = h->d_result;
     a.ov_out = h->d_ov;
+    a.ov_all = ovs;
     a.C = h->C;
     a.S = h->S;
     a.n_words = h->n_words;
@@ -515,8 +527,9 @@ sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_
     return SP_OK;
   }
   if (n < kGraphMinFrames || !graphs_enabled())
-    return enqueue_sequence(h, h->stream, x_base, n, stride, learn, masks);
-  const GraphKey key{x_base, n, stride, learn, masks, h->cur, h->pending, h->unit_boost, 0};
+    return enqueue_sequence(h, h->stream, x_base, n, stride, learn, masks, ovs);
+  const GraphKey key{x_base, n, stride, learn, masks, h->cur, h->pending, h->unit_boost, 0, 0,
+                     ovs};
   GraphEntry* e = nullptr;
   for (auto& g : h->graphs)
     if (g.key == key) e = &g;
@@ -526,7 +539,7 @@ sp_status run_sequence(sp_handle* h, const uint32_t* x_base, uint32_t n, uint64_
     const bool pending0 = h->pending;
     const uint64_t frames0 = h->frames;
     SP_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    sp_status s = enqueue_sequence(h, h->cap_stream, x_base, n, stride, learn, masks);
+    sp_status s = enqueue_sequence(h, h->cap_stream, x_base, n, stride, learn, masks, ovs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
     sp::g_launches.fetch_sub(n, std::memory_order_relaxed);  // recorded, not launched
@@ -811,19 +824,28 @@ SP_API sp_status sp_compute_device(sp_handle* h, const uint32_t* d_bits, int lea
                        learn ? h->d_xsave[h->cur] : nullptr, learn, nullptr);
 }
 
-SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames, uint32_t n_frames,
-                                          uint64_t stride, int learn, uint32_t* d_active_masks,
-                                          void* stream) {
+SP_API sp_status sp_compute_frames_overlaps_device(sp_handle* h, const uint32_t* d_frames,
+                                                   uint32_t n_frames, uint64_t stride, int learn,
+                                                   uint32_t* d_active_masks, float* d_overlaps,
+                                                   void* stream) {
   if (!h || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
   if (h->batch) return fail(SP_EBUSY, "the handle is a member of a batch");
   if (n_frames == 0) return SP_OK;
   if (stride < h->n_words) return fail(SP_EINVAL, "frame stride %llu < %u words", (unsigned long long)stride, h->n_words);
-  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_active_masks) % 4u)
+  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_active_masks) % 4u ||
+      reinterpret_cast<uintptr_t>(d_overlaps) % 4u)
     return fail(SP_EINVAL, "device pointers must be 4-byte aligned");
   DeviceGuard g(h->device);
   sp_status s = use_stream(h, static_cast<cudaStream_t>(stream));
   if (s != SP_OK) return s;
-  return run_sequence(h, d_frames, n_frames, stride, learn, d_active_masks);
+  return run_sequence(h, d_frames, n_frames, stride, learn, d_active_masks, d_overlaps);
+}
+
+SP_API sp_status sp_compute_frames_device(sp_handle* h, const uint32_t* d_frames, uint32_t n_frames,
+                                          uint64_t stride, int learn, uint32_t* d_active_masks,
+                                          void* stream) {
+  return sp_compute_frames_overlaps_device(h, d_frames, n_frames, stride, learn, d_active_masks,
+                                           nullptr, stream);
 }
 
 SP_API sp_status sp_compute_frames(sp_handle* h, const uint32_t* h_frames, uint32_t n_frames,
@@ -1086,8 +1108,8 @@ struct sp_batch {
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
   uint32_t* d_err = nullptr;
-  uint64_t frame_words = 0, mask_words = 0;
-  std::vector<uint64_t> frame_off, mask_off;
+  uint64_t frame_words = 0, mask_words = 0, ov_words = 0;
+  std::vector<uint64_t> frame_off, mask_off, ov_off;
   int cur = 0;
   bool pending = false;
   uint64_t frames = 0;
@@ -1238,7 +1260,8 @@ sp_status batch_use_stream(sp_batch* b, cudaStream_t s) {
 
 // Enqueue n batch frames on `st` from the batch's current (parity, pending).
 sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, uint32_t n,
-                        uint64_t stride, int learn, uint32_t* masks, uint64_t mstride) {
+                        uint64_t stride, int learn, uint32_t* masks, uint64_t mstride,
+                        float* ovs, uint64_t ovstride) {
   for (uint32_t t = 0; t < n; ++t) {
     sp::BatchArgs a{};
     a.desc = b->d_desc;
@@ -1246,6 +1269,7 @@ sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, ui
     a.frames = x_base + (uint64_t)t * stride;
     a.prev_frames = t ? x_base + (uint64_t)(t - 1) * stride : nullptr;
     a.masks_out = masks ? masks + (uint64_t)t * mstride : nullptr;
+    a.ov_out = ovs ? ovs + (uint64_t)t * ovstride : nullptr;
     a.cur = (uint32_t)b->cur;
     a.pending = b->pending ? 1u : 0u;
     a.learn = learn ? 1u : 0u;
@@ -1268,7 +1292,8 @@ bool persistent_enabled() {
 }
 
 sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t stride, int learn,
-                    uint32_t* masks, uint64_t mstride) {
+                    uint32_t* masks, uint64_t mstride, float* ovs = nullptr,
+                    uint64_t ovstride = 0) {
   if (learn)
     for (sp_handle* h : b->members) h->bimg_stale = true;
   if (n >= 2 && persistent_enabled()) {
@@ -1281,6 +1306,8 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.stride = stride;
     r.masks_out = masks;
     r.mstride = mstride;
+    r.ov_out = ovs;
+    r.ov_stride = ovstride;
     r.cur0 = (uint32_t)b->cur;
     r.pending0 = b->pending ? 1u : 0u;
     r.learn = learn ? 1u : 0u;
@@ -1301,11 +1328,13 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     return SP_OK;
   }
   if (n < kGraphMinFrames || !graphs_enabled()) {
-    sp_status s = batch_enqueue(b, b->stream, x_base, n, stride, learn, masks, mstride);
+    sp_status s = batch_enqueue(b, b->stream, x_base, n, stride, learn, masks, mstride, ovs,
+                                ovstride);
     if (s == SP_OK) b->frames += n;
     return s;
   }
-  const GraphKey key{x_base, n, stride, learn, masks, b->cur, b->pending, false, mstride};
+  const GraphKey key{x_base, n, stride, learn, masks, b->cur, b->pending, false, mstride, 0, ovs,
+                     ovstride};
   GraphEntry* e = nullptr;
   for (auto& g : b->graphs)
     if (g.key == key) e = &g;
@@ -1314,7 +1343,8 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     const int cur0 = b->cur;
     const bool pending0 = b->pending;
     SP_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    sp_status s = batch_enqueue(b, b->cap_stream, x_base, n, stride, learn, masks, mstride);
+    sp_status s = batch_enqueue(b, b->cap_stream, x_base, n, stride, learn, masks, mstride, ovs,
+                                ovstride);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
     sp::g_launches.fetch_sub(n, std::memory_order_relaxed);
@@ -1381,13 +1411,16 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   }
   std::vector<sp::BatchDesc> desc(n);
   std::vector<uint32_t> cta_inst;
-  uint64_t foff = 0, moff = 0;
+  uint64_t foff = 0, moff = 0, ooff = 0;
   for (uint32_t i = 0; i < n; ++i) {
     sp_handle* h = members[i];
     sp::BatchDesc& d = desc[i];
     fill_desc(h, &d);
     d.frame_off = foff;
     d.mask_off = moff;
+    d.ov_off = ooff;
+    b->ov_off.push_back(ooff);
+    ooff += h->C;
     d.cta_first = (uint32_t)cta_inst.size();
     for (uint32_t c = 0; c < d.n_ctas; ++c) cta_inst.push_back(i);
     b->frame_off.push_back(foff);
@@ -1401,6 +1434,7 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   b->xspan_cap = batch_xspan_cap();
   b->frame_words = foff;
   b->mask_words = moff;
+  b->ov_words = ooff;
   b->n_ctas = (uint32_t)cta_inst.size();
   b->h_desc = desc;
   const size_t desc_bytes = align256(sizeof(sp::BatchDesc) * n);
@@ -1465,20 +1499,41 @@ SP_API sp_status sp_batch_offsets(const sp_batch* b, uint64_t* frame_off, uint64
   return SP_OK;
 }
 
-SP_API sp_status sp_batch_compute_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
-                                         uint64_t stride, int learn, uint32_t* d_masks,
-                                         uint64_t mstride, void* stream) {
+SP_API sp_status sp_batch_overlap_offsets(const sp_batch* b, uint64_t* ov_off, uint64_t* ov_words) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (ov_off) ov_off[i] = b->ov_off[i];
+  if (ov_words) *ov_words = b->ov_words;
+  return SP_OK;
+}
+
+SP_API sp_status sp_batch_compute_overlaps_device(sp_batch* b, const uint32_t* d_frames,
+                                                  uint32_t n_frames, uint64_t stride, int learn,
+                                                  uint32_t* d_masks, uint64_t mstride,
+                                                  float* d_overlaps, uint64_t ov_stride,
+                                                  void* stream) {
   if (!b || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
   if (n_frames == 0) return SP_OK;
   if (stride < b->frame_words) return fail(SP_EINVAL, "frame stride %llu < %llu words", (unsigned long long)stride, (unsigned long long)b->frame_words);
   if (d_masks && mstride < b->mask_words) return fail(SP_EINVAL, "mask stride %llu < %llu words", (unsigned long long)mstride, (unsigned long long)b->mask_words);
+  if (d_overlaps && ov_stride < b->ov_words)
+    return fail(SP_EINVAL, "overlap stride %llu < %llu", (unsigned long long)ov_stride, (unsigned long long)b->ov_words);
   if (reinterpret_cast<uintptr_t>(d_frames) % 16u || reinterpret_cast<uintptr_t>(d_masks) % 4u ||
       (n_frames > 1 && stride % 4u))
     return fail(SP_EINVAL, "batch frames must be 16-byte aligned (stride a multiple of 4 words)");
+  if (reinterpret_cast<uintptr_t>(d_overlaps) % 4u)
+    return fail(SP_EINVAL, "d_overlaps not 4-byte aligned");
   DeviceGuard g(b->device);
   sp_status s = batch_use_stream(b, static_cast<cudaStream_t>(stream));
   if (s != SP_OK) return s;
-  return batch_run(b, d_frames, n_frames, stride, learn, d_masks, mstride);
+  return batch_run(b, d_frames, n_frames, stride, learn, d_masks, mstride, d_overlaps, ov_stride);
+}
+
+SP_API sp_status sp_batch_compute_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                         uint64_t stride, int learn, uint32_t* d_masks,
+                                         uint64_t mstride, void* stream) {
+  return sp_batch_compute_overlaps_device(b, d_frames, n_frames, stride, learn, d_masks, mstride,
+                                          nullptr, 0, stream);
 }
 
 SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_t n_frames,
@@ -1537,14 +1592,18 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
   return batch_wait(b);
 }
 
-SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
-                                       uint64_t stride, uint32_t* d_masks, uint64_t mstride,
-                                       void* stream) {
+SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_frames,
+                                                uint32_t n_frames, uint64_t stride,
+                                                uint32_t* d_masks, uint64_t mstride,
+                                                float* d_overlaps, uint64_t ov_stride,
+                                                void* stream) {
   if (!b || (!d_frames && n_frames)) return fail(SP_EINVAL, "NULL argument");
   if (n_frames == 0) return SP_OK;
   if (stride < b->frame_words) return fail(SP_EINVAL, "frame stride below frame_words");
   if (d_masks && mstride < b->mask_words) return fail(SP_EINVAL, "mask stride below mask_words");
-  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_masks) % 4u)
+  if (d_overlaps && ov_stride < b->ov_words) return fail(SP_EINVAL, "overlap stride below the record length");
+  if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_masks) % 4u ||
+      reinterpret_cast<uintptr_t>(d_overlaps) % 4u)
     return fail(SP_EINVAL, "device pointers must be 4-byte aligned");
   for (sp_handle* h : b->members)
     if (!h->dense) return fail(SP_ENOTSUP, "every member needs dense pools (S = n_in)");
@@ -1698,9 +1757,25 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
     SP_CUDA(cudaGraphLaunch(e->exec, b->stream));
     sp::g_launches.fetch_add(n_launch, std::memory_order_relaxed);
   }
+  if (d_overlaps) {
+    // each member's [n_frames][C] run overlaps into its columns of the record
+    for (uint32_t i = 0; i < n; ++i) {
+      sp_handle* h = b->members[i];
+      SP_CUDA(cudaMemcpy2DAsync(d_overlaps + b->ov_off[i], ov_stride * 4, h->d_run_ov,
+                                (size_t)h->C * 4, (size_t)h->C * 4, n_frames,
+                                cudaMemcpyDeviceToDevice, b->stream));
+    }
+  }
   b->cur ^= 1;
   b->frames += n_frames;
   return SP_OK;
+}
+
+SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
+                                       uint64_t stride, uint32_t* d_masks, uint64_t mstride,
+                                       void* stream) {
+  return sp_batch_infer_overlaps_device(b, d_frames, n_frames, stride, d_masks, mstride, nullptr,
+                                        0, stream);
 }
 
 namespace {

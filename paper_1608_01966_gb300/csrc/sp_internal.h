@@ -62,6 +62,10 @@ struct DeviceGuard {
 
 inline size_t align256(size_t x) { return (x + 255u) & ~size_t(255u); }
 
+// Checks every field of a configuration that the compute paths use (sizes,
+// finite parameters, inhibition mode, column grid, reserved fields); sets the
+// calling thread's message and returns SP_EINVAL on the first violation.
+sp_status validate_config(const sp_config* c);
 bool all_ones(const float* v, size_t n);
 sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
@@ -94,10 +98,12 @@ struct GraphKey {
   bool unit_boost;  // selects the histogram path baked into the recorded launches
   uint64_t mstride; // mask stride (batches)
   uint64_t extra = 0;  // dense runs: launch shape and buffer generations baked into the launches
+  const float* ovs = nullptr;  // the caller's per-frame overlap record, or nullptr
+  uint64_t ovstride = 0;
   bool operator==(const GraphKey& o) const {
     return x == o.x && n == o.n && stride == o.stride && learn == o.learn && masks == o.masks &&
            cur == o.cur && pending == o.pending && unit_boost == o.unit_boost &&
-           mstride == o.mstride && extra == o.extra;
+           mstride == o.mstride && extra == o.extra && ovs == o.ovs && ovstride == o.ovstride;
   }
 };
 

@@ -33,6 +33,8 @@ struct StepArgs {
                              // launches; used (global inhibition) when every boost
                              // is exactly 1, else nullptr (radix select instead)
   uint32_t* result_copy;     // optional second copy of result[0..n] (serving), or nullptr
+  float* ov_copy;            // optional copy of this frame's boosted overlaps [C] (a
+                             // caller's per-frame overlap record), or nullptr
   float* duty;               // [C] active-duty cycles updated each frame, or nullptr
   float duty_period;
   const uint32_t* xspan;     // per CTA: [lo, hi) input words its columns read, or nullptr
@@ -66,6 +68,7 @@ struct BatchDesc {
   uint32_t* conn;
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
+  uint64_t ov_off;      // floats: this SP's overlaps inside one batch overlap record
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k, inhibition, gw, gh, radius;
@@ -82,6 +85,8 @@ struct BatchRunArgs {
   uint64_t stride;
   uint32_t* masks_out;          // batch mask record t at masks_out + t * mstride (nullable)
   uint64_t mstride;
+  float* ov_out;                // batch overlap record t at ov_out + t * ov_stride (nullable)
+  uint64_t ov_stride;
   uint32_t cur0, pending0, learn;  // parity and pending learning before frame 0
   uint32_t epoch;               // base of the done values (0: flags cleared per launch)
   unsigned long long* work;     // item counter, 0 at launch
@@ -110,6 +115,7 @@ struct BatchArgs {
   const uint32_t* frames;       // one batch frame (members at their frame_off)
   const uint32_t* prev_frames;  // the previous batch frame, or nullptr (saved copies)
   uint32_t* masks_out;          // one batch mask record, or nullptr
+  float* ov_out;                // one batch overlap record, or nullptr
   uint32_t cur, pending, learn;
   uint32_t save;                // copy each member's frame for next-call learning
   const TickMember* tick;       // if set: per-SP frame/state (indexed like desc); the
@@ -172,6 +178,7 @@ struct SeqArgs {
   uint32_t* mask_last;        // last frame's mask [mask_words]
   uint32_t* result;           // last frame: [0] count, [1..] ascending winners
   float* ov_out;              // last frame's boosted overlaps [C]
+  float* ov_all;              // [n_frames][C] boosted overlaps of every frame, or nullptr
   uint32_t C, S, n_words, mask_words;
   uint32_t Cq;                // columns per CTA (multiple of 32)
   uint32_t band_max;          // words of the largest per-CTA input band (multiple of 4)

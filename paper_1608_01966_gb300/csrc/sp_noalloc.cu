@@ -17,10 +17,8 @@
 // holds it until the process exits) and is shared by every call.
 #include <cuda_runtime.h>
 
-#include <cmath>
-#include <mutex>
-
 #include "../../include/sp.h"
+#include "sp_internal.h"
 #include "sp_kernels.cuh"
 
 namespace {
@@ -30,33 +28,29 @@ namespace {
 constexpr uint32_t kScratchWords = SP_NOALLOC_MAX_COLUMNS + 64u;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-uint32_t* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
-
 sp_status noalloc_fail(sp_status s, const char* msg) {
   sp::set_last_error("sp_step_noalloc: %s", msg);
   return s;
 }
 
-// Once per device, with that device current: the device address of the
-// scratch array.  In host code g_noalloc_scratch names a host-side stand-in,
-// never a device address, so it is not passed to a kernel directly.
-sp_status scratch_address(int dev, uint32_t** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      sp::set_last_error("sp_step_noalloc: cudaGetSymbolAddress failed: %s",
-                         cudaGetErrorString(e));
-      return SP_ECUDA;
-    }
-    if (sp::kernels_init() != cudaSuccess)
-      return noalloc_fail(SP_ECUDA, "kernel attribute set-up failed");
-    g_scratch_addr[dev] = static_cast<uint32_t*>(p);
+// The device address of the scratch array in the current device's context.
+// In host code g_noalloc_scratch names a host-side stand-in, never a device
+// address, so it is not passed to a kernel directly.  The address is looked
+// up on every call (a lookup, no allocation): a context that was destroyed
+// and created again -- a device reset between calls -- loads the library's
+// device code again, possibly at another address, so a remembered address
+// could be stale.  The kernels' attributes are set again for the same reason.
+sp_status scratch_address(uint32_t** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    sp::set_last_error("sp_step_noalloc: cudaGetSymbolAddress failed: %s",
+                       cudaGetErrorString(e));
+    return SP_ECUDA;
   }
-  *out = g_scratch_addr[dev];
+  if (sp::kernels_init() != cudaSuccess)
+    return noalloc_fail(SP_ECUDA, "kernel attribute set-up failed");
+  *out = static_cast<uint32_t*>(p);
   return SP_OK;
 }
 
@@ -72,31 +66,19 @@ SP_API sp_status sp_step_noalloc(const sp_config* cfg, const uint32_t* d_idx, fl
                                  void* stream) {
   if (!cfg || !d_idx || !d_perm || !d_boost || !d_input || !d_active_mask || !d_active_list)
     return noalloc_fail(SP_EINVAL, "NULL argument");
-  if (cfg->abi_version != SP_ABI_VERSION) return noalloc_fail(SP_EINVAL, "abi_version mismatch");
+  if (cfg->num_columns > SP_NOALLOC_MAX_COLUMNS)
+    return noalloc_fail(SP_EINVAL, "num_columns must be in [1, SP_NOALLOC_MAX_COLUMNS]");
+  // the same configuration checks as sp_create (the message names the field)
+  if (sp::rt::validate_config(cfg) != SP_OK) return SP_EINVAL;
   const uint64_t n_in = (uint64_t)cfg->input_w * cfg->input_h;
   const uint32_t C = cfg->num_columns, S = cfg->synapses_per_column;
-  if (C == 0 || C > SP_NOALLOC_MAX_COLUMNS)
-    return noalloc_fail(SP_EINVAL, "num_columns must be in [1, SP_NOALLOC_MAX_COLUMNS]");
-  if (S == 0 || S > SP_MAX_SYNAPSES) return noalloc_fail(SP_EINVAL, "synapses_per_column out of range");
-  if (n_in == 0 || n_in > SP_MAX_INPUT_BITS) return noalloc_fail(SP_EINVAL, "input size out of range");
-  if ((uint64_t)C * S > (1ull << 31)) return noalloc_fail(SP_EINVAL, "C*S too large");
-  if (!std::isfinite(cfg->connect_threshold) || !(cfg->perm_inc >= 0.0f) ||
-      !(cfg->perm_dec >= 0.0f) || !std::isfinite(cfg->perm_inc) || !std::isfinite(cfg->perm_dec))
-    return noalloc_fail(SP_EINVAL, "threshold / perm_inc / perm_dec invalid");
-  if (cfg->inhibition > SP_INHIBIT_PAPER_LITERAL) return noalloc_fail(SP_EINVAL, "inhibition mode");
-  if (cfg->inhibition == SP_INHIBIT_LOCAL &&
-      ((uint64_t)cfg->col_grid_w * cfg->col_grid_h != C || cfg->col_grid_w == 0))
-    return noalloc_fail(SP_EINVAL, "local inhibition needs col_grid_w * col_grid_h == num_columns");
   const bool vec = S % 4u == 0u;
   if (!aligned(d_idx, vec ? 16 : 4) || !aligned(d_perm, vec ? 16 : 4) || !aligned(d_boost, 4) ||
       !aligned(d_input, 4) || !aligned(d_active_mask, 4) || !aligned(d_active_list, 4))
     return noalloc_fail(SP_EINVAL, "device pointers misaligned (16 bytes for idx/perm when S % 4 == 0)");
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return noalloc_fail(SP_ECUDA, "no current CUDA device");
   uint32_t* scratch = nullptr;
-  sp_status s = scratch_address(dev, &scratch);
+  sp_status s = scratch_address(&scratch);
   if (s != SP_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* counter = scratch + SP_NOALLOC_MAX_COLUMNS;

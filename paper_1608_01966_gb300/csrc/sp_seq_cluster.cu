@@ -21,6 +21,9 @@
 //   5. learning (Section 1.1) of its winning columns in shared memory, with
 //      the frame band still resident.
 //
+// Outputs per frame: this CTA's words of the active mask and, when asked
+// for, its columns' boosted overlaps; the last frame's list and overlaps.
+//
 // The published overlaps are double-buffered by frame parity, so one
 // barrier per frame orders both the gather of frame t and the overwrite at
 // frame t+2.  Permanence rows that changed are written back at the end.
@@ -359,6 +362,9 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
     if (a.masks_out)
       for (uint32_t i = mw0 + t; i < mw1; i += kSeqThreads)
         a.masks_out[(uint64_t)f * a.mask_words + i] = s_mask[i];
+    if (a.ov_all)
+      for (uint32_t i = t; i < nc; i += kSeqThreads)
+        a.ov_all[(uint64_t)f * C + c0 + i] = fast ? __uint2float_rn(s_raw[i]) : ov_pub[i];
     if (last) {
       for (uint32_t i = mw0 + t; i < mw1; i += kSeqThreads) a.mask_last[i] = s_mask[i];
       for (uint32_t i = t; i < nc; i += kSeqThreads)

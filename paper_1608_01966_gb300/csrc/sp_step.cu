@@ -361,7 +361,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
   auto publish = [&](uint32_t c, uint32_t raw) {
     // a histogram is kept only when every boost is exactly 1, and then the
     // product is the count itself: no load stalls the warp here
-    a.ov[c] = dev::boosted(raw, a.min_overlap, a.hist ? 1.0f : __ldg(a.boost + c));
+    const float v = dev::boosted(raw, a.min_overlap, a.hist ? 1.0f : __ldg(a.boost + c));
+    a.ov[c] = v;
+    if (a.ov_copy) a.ov_copy[c] = v;
     // unit boosts: the overlap is the count, histogrammed for the select
     if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
   };
@@ -628,6 +630,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.x_save = (learn && save) ? (cur ? d.xsave1 : d.xsave0) : nullptr;
   a.mask_out = cur ? d.mask1 : d.mask0;
   a.mask_copy = (ba.masks_out && !ba.tick) ? ba.masks_out + d.mask_off : nullptr;
+  a.ov_copy = (ba.ov_out && !ba.tick) ? ba.ov_out + d.ov_off : nullptr;
   a.result = d.result;
   a.counter = d.counter;
   a.hist = d.hist;
@@ -753,6 +756,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
     a.x_save = (r.learn && save) ? (cur ? d.xsave1 : d.xsave0) : nullptr;
     a.mask_out = cur ? d.mask1 : d.mask0;
     a.mask_copy = r.masks_out ? r.masks_out + (uint64_t)t * r.mstride + d.mask_off : nullptr;
+    a.ov_copy = r.ov_out ? r.ov_out + (uint64_t)t * r.ov_stride + d.ov_off : nullptr;
     a.result = d.result;
     a.counter = d.counter;
     a.hist = d.hist;

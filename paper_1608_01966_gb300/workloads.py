@@ -134,6 +134,53 @@ def bernoulli_frames(case_index, n_in, p, n, seed=BASE_SEED + 4, start=0):
                      for t in range(start, start + n)])
 
 
+def uneven_frames(cases, dens, n, seed=BASE_SEED + 4, start=0):
+    """Frames of the uneven SPs: member i sees Bernoulli(dens[i]) frames drawn
+    from its own instance seed."""
+    return [bernoulli_frames(i, c.n_in, dens[i], n, seed=seed, start=start)
+            for i, c in enumerate(cases)]
+
+
+def dense_cases(members=16, frames=256, C=1024, n_in=1024, k=20, seed=BASE_SEED + 4):
+    """SPs with dense potential pools (every column sees the whole input,
+    S = n_in) for the tensor-core path: perms U[0.1,0.3], threshold 0.2,
+    min_overlap 4, global inhibition with k winners; member i's frames are
+    Bernoulli(p_i) with p_i spread evenly over [2%, 20%].  Returns (cases,
+    frames uint8 [members][frames][n_in])."""
+    cases, fr = [], []
+    for i in range(members):
+        sd = synth.derive_seed(seed, synth.PURPOSE_INSTANCE, 1000 + i)
+        idx = synth.pool_dense(C, n_in)
+        perm = synth.perm_uniform(synth.derive_seed(sd, synth.PURPOSE_PERM, 0), (C, n_in),
+                                  0.1, 0.3)
+        cases.append(Case(f"dense{i}", n_in, 1, C, n_in, idx, perm, np.ones(C, np.float32), k=k))
+        p = 0.02 + 0.18 * i / max(1, members - 1)
+        fr.append(np.stack([synth.frame_bernoulli(synth.derive_seed(sd, synth.PURPOSE_FRAME, t),
+                                                  n_in, p) for t in range(frames)]))
+    return cases, fr
+
+
+SERVE_RESOLUTIONS = ((320, 180), (640, 360), (960, 540))
+
+
+def serve_cases(streams=32, seed=BASE_SEED + 5):
+    """The serving workload's streams: stream i at resolution i mod 3 of
+    320x180 / 640x360 / 960x540, each with its own SP of 1024 columns on a
+    32x32 grid x 256 synapses from 64x64 windows (k 40, min_overlap 4)."""
+    cases = []
+    for i in range(streams):
+        W, H = SERVE_RESOLUTIONS[i % 3]
+        cases.append(grid_case(f"stream{i}", 1024, 256, synth.derive_seed(seed, synth.PURPOSE_INSTANCE, i),
+                               W=W, H=H))
+    return cases
+
+
+def serve_frames(case_index, W, H, n, seed=BASE_SEED + 5, start=0):
+    """Blobbed frames of serving stream case_index."""
+    return blob_frames(n, W=W, H=H, seed=synth.derive_seed(seed, synth.PURPOSE_FRAME, case_index),
+                       start=start)
+
+
 def batch_frames(per_member_packed, frame_off, frame_words):
     """Assemble batch frames: per_member_packed[i] is uint32 [n][words_i];
     returns uint32 [n][frame_words] with member i at word offset frame_off[i]."""

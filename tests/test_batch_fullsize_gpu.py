@@ -2,7 +2,8 @@
 SPs (1024 columns x 256 synapses from 64x64 windows of 960x540 blobbed
 frames, k = 40, learning on), autotuned, stepped by persistent launches over
 several frames and by single-frame launches.  The oracle checks sampled
-members frame by frame (winners) and their final permanences: bit-exact."""
+members frame by frame (every boosted overlap and the winners) and their
+final permanences: bit-exact."""
 import concurrent.futures as cf
 
 import numpy as np
@@ -40,19 +41,25 @@ def test_full_size_batch_sampled_against_oracle():
             batch[t, int(fo[i]):int(fo[i]) + packed.shape[1]] = packed[(7 * i + t) % 8]
     d = torch.from_numpy(batch.view(np.int32)).cuda()
     mw = info["mask_words"]
+    oo, ow = spg.sp_batch_overlap_offsets(b)
     dm = torch.zeros((n_frames, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((n_frames, ow), -1.0, dtype=torch.float32, device="cuda")
     spg.sp_batch_autotune(b, d, 2, fw)
     st = torch.cuda.current_stream()
-    spg.sp_batch_compute_device(b, d[0], 4, fw, True, dm[0], mw, st)   # one persistent launch
-    spg.sp_batch_compute_device(b, d[4], 1, fw, True, dm[4], mw, st)   # single-frame launch
-    spg.sp_batch_compute_device(b, d[5], 1, fw, True, dm[5], mw, st)
+    # one persistent launch, then two single-frame launches
+    spg.sp_batch_compute_overlaps_device(b, d[0], 4, fw, True, dm[0], mw, dov[0], ow, st)
+    spg.sp_batch_compute_overlaps_device(b, d[4], 1, fw, True, dm[4], mw, dov[4], ow, st)
+    spg.sp_batch_compute_overlaps_device(b, d[5], 1, fw, True, dm[5], mw, dov[5], ow, st)
     spg.sp_batch_sync(b)
     masks = dm.cpu().numpy().view(np.uint32)
+    ovr = dov.cpu().numpy()
     spg.sp_batch_destroy(b)
     for i in SAMPLED:
         c = cases[i]
         frames = np.stack([pool[(7 * i + t) % 8] for t in range(n_frames)])
-        want, perm, _ = oracle_run(c, frames, True)
+        want, perm, ov = oracle_run(c, frames, True, want_ov=True)
+        d = first_diff(ovr[:, int(oo[i]):int(oo[i]) + c.C], ov)
+        assert d is None, f"member {i}: overlap (frame, column) {d}"
         got = dense(masks[:, int(mo[i]):int(mo[i]) + 32], c.C)
         assert first_diff(got, want) is None, f"member {i}: {first_diff(got, want)}"
         assert got.sum(axis=1).max() <= c.k

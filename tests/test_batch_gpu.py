@@ -12,6 +12,8 @@ from helpers import dense, first_diff, oracle_run  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+SWEEP_FRAMES = 200  # learning frames per combination of the sweep workload
+
 
 def _member_frames(cases, dens, n):
     return [wl.bernoulli_frames(i, c.n_in, dens[i], n) for i, c in enumerate(cases)]
@@ -19,11 +21,14 @@ def _member_frames(cases, dens, n):
 
 def _run_batch(cases, frames_u8, learn, calls, boosts=None):
     """Create handles + batch, run the batch frames split into `calls` (list of
-    frame counts), return per-member active [n][C] and final perms."""
+    frame counts) through sp_batch_compute_overlaps_device, return per-member
+    active [n][C], final perms, and overlaps of every frame [n][C]."""
     hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
     b = spg.sp_batch_create(hs)
     info = spg.sp_batch_get_info(b)
     fo, mo = spg.sp_batch_offsets(b)
+    oo, ow = spg.sp_batch_overlap_offsets(b)
+    assert ow == sum(c.C for c in cases)
     n = frames_u8[0].shape[0]
     fw = (info["frame_words"] + 3) // 4 * 4
     bf = wl.batch_frames([wl.pack(f) for f in frames_u8], fo, fw)
@@ -31,29 +36,46 @@ def _run_batch(cases, frames_u8, learn, calls, boosts=None):
     stream = torch.cuda.current_stream()
     d = torch.from_numpy(bf.view(np.int32)).cuda()
     dm = torch.zeros((n, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((n, ow), -1.0, dtype=torch.float32, device="cuda")
     t0 = 0
     for k in calls:
-        spg.sp_batch_compute_device(b, d[t0], k, fw, learn, dm[t0], mw, stream)
+        spg.sp_batch_compute_overlaps_device(b, d[t0], k, fw, learn, dm[t0], mw, dov[t0], ow,
+                                             stream)
         t0 += k
     assert t0 == n
     spg.sp_batch_sync(b)
     masks = dm.cpu().numpy().view(np.uint32)
+    ovr = dov.cpu().numpy()
     spg.sp_batch_destroy(b)
     acts = [dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
             for i, c in enumerate(cases)]
     perms = [spg.sp_get_permanences(h) for h in hs]
-    ovs = [spg.sp_get_overlaps(h) for h in hs]
+    ovs = [ovr[:, int(oo[i]):int(oo[i]) + c.C] for i, c in enumerate(cases)]
+    last = [spg.sp_get_overlaps(h) for h in hs]
+    for i in range(len(cases)):
+        np.testing.assert_array_equal(last[i], ovs[i][-1], err_msg=f"member {i} last overlaps")
     for h in hs:
         spg.sp_destroy(h)
     return acts, perms, ovs
 
 
+def _oracle_all(cases, frames_u8, learn):
+    """The oracle on every member (host threads: the oracle's C code runs
+    without the GIL)."""
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        return list(ex.map(lambda i: oracle_run(cases[i], frames_u8[i], learn, want_ov=True),
+                           range(len(cases))))
+
+
 def _check(cases, frames_u8, learn, acts, perms, ovs, label):
-    for i, c in enumerate(cases):
-        act, perm, ov = oracle_run(c, frames_u8[i], learn, want_ov=True)
+    """Every member, every frame: overlaps element by element, active sets,
+    and the final permanences."""
+    for i, (act, perm, ov) in enumerate(_oracle_all(cases, frames_u8, learn)):
+        d = first_diff(ovs[i], ov)
+        assert d is None, f"{label} member {i}: first differing overlap (frame, column) {d}"
         assert first_diff(acts[i], act) is None, f"{label} member {i}: frame/column {first_diff(acts[i], act)}"
         np.testing.assert_array_equal(perms[i], perm, err_msg=f"{label} member {i} perms")
-        np.testing.assert_array_equal(ovs[i], ov[-1], err_msg=f"{label} member {i} overlaps")
 
 
 def test_batch_of_identical_shapes():
@@ -257,11 +279,13 @@ def test_batch_long_sequence_in_one_call(monkeypatch, persistent):
 
 @pytest.mark.parametrize("C", [256, 1024, 4096])
 def test_batch_parameter_sweep(C):
-    """The 54 synapse x min_overlap x k x {global, 9x9 local} combinations of
-    the sweep workload for one column count, as members of one batch (compact
-    form for S = 64 and 256, full form for S = 16), 8 learning frames in one
-    persistent launch, every member against the oracle."""
-    frames1 = wl.blob_frames(8, seed=wl.BASE_SEED + 3)
+    """The sweep workload at its stated length: the 54 synapse x min_overlap x
+    k x {global, 9x9 local} combinations for one column count, as members of
+    one batch (compact form for S = 64 and 256, full form for S = 16), 200
+    learning frames of 960x540 blobbed input in one persistent launch; every
+    member's overlaps and winners of every frame, and its final permanences,
+    against the oracle."""
+    frames1 = wl.blob_frames(SWEEP_FRAMES, seed=wl.BASE_SEED + 3)
     cases, frames = [], []
     for S in (16, 64, 256):
         for m in (2, 4, 8):
@@ -270,5 +294,5 @@ def test_batch_parameter_sweep(C):
                     cases.append(wl.grid_case("sweep", C, S, wl.BASE_SEED + 3 + C + S,
                                               min_overlap=m, k=k, inhibition=inh, radius=4))
                     frames.append(frames1)
-    acts, perms, ovs = _run_batch(cases, frames, True, [8])
+    acts, perms, ovs = _run_batch(cases, frames, True, [SWEEP_FRAMES])
     _check(cases, frames, True, acts, perms, ovs, f"sweep C{C}")

@@ -1,0 +1,185 @@
+"""The workloads at their stated sizes, in the launch configurations the
+benchmark times, against the CPU oracle frame by frame.  Bar: bit-exact --
+every frame's boosted overlaps element by element, every frame's winners,
+and the final permanences.
+
+  uneven     64 independent SPs of uneven shapes (columns 128..4096, synapses
+             16..256, inputs 256..16384 bits at 2-20 % density, k = 2 % of
+             the columns), learning on, autotuned, in persistent launches of
+             16 frames -- exactly the benchmark's members and frames;
+  dense      16 SPs with dense pools (1024 inputs x 1024 columns) inferring
+             256 frames on the tensor cores;
+  serving    32 video streams at 320x180 / 640x360 / 960x540 through the
+             library's continuous-batching server, learning on, frames
+             submitted by several producer threads.
+"""
+import concurrent.futures as cf
+import threading
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1608_01966_gb300 as spg  # noqa: E402
+from paper_1608_01966_gb300 import workloads as wl  # noqa: E402
+from helpers import dense, first_diff, oracle_params, oracle_run  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_members(cases, frames, learn):
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        return list(ex.map(lambda i: oracle_run(cases[i], frames[i], learn, want_ov=True),
+                           range(len(cases))))
+
+
+def _compare(cases, frames, learn, acts, ovs, perms, label):
+    for i, (act, perm, ov) in enumerate(_oracle_members(cases, frames, learn)):
+        c = cases[i]
+        d = first_diff(ovs[i], ov)
+        assert d is None, f"{label} member {i} (C {c.C}, S {c.S}, n_in {c.n_in}): overlap {d}"
+        d = first_diff(acts[i], act)
+        assert d is None, f"{label} member {i}: winners differ at (frame, column) {d}"
+        if perms is not None:
+            np.testing.assert_array_equal(perms[i], perm, err_msg=f"{label} member {i} perms")
+
+
+def _batch(cases):
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    oo, ow = spg.sp_batch_overlap_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    return hs, b, info, fo, mo, oo, ow, fw
+
+
+def _split(cases, masks, ovr, mo, oo):
+    acts = [dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+            for i, c in enumerate(cases)]
+    ovs = [ovr[:, int(oo[i]):int(oo[i]) + c.C] for i, c in enumerate(cases)]
+    return acts, ovs
+
+
+def test_uneven_batch_as_benchmarked():
+    """The benchmark's uneven batch: wl.uneven_cases(64), autotuned, learning,
+    runs of 16 frames per persistent launch (two runs: the second continues the
+    learning the first left pending); all 64 members compared."""
+    cases, dens = wl.uneven_cases(64)
+    F, runs = 16, 2
+    frames = wl.uneven_frames(cases, dens, F * runs)
+    assert max(c.C for c in cases) > 3500 and max(c.n_in for c in cases) > 15000
+    hs, b, info, fo, mo, oo, ow, fw = _batch(cases)
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    dm = torch.zeros((F * runs, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((F * runs, ow), -1.0, dtype=torch.float32, device="cuda")
+    tune = torch.from_numpy(wl.batch_frames(
+        [wl.pack(f) for f in wl.uneven_frames(cases, dens, 4, start=500)], fo, fw).view(np.int32)).cuda()
+    spg.sp_batch_autotune(b, tune, 4, fw)
+    st = torch.cuda.current_stream()
+    for r in range(runs):
+        spg.sp_batch_compute_overlaps_device(b, d[r * F], F, fw, True, dm[r * F], mw,
+                                             dov[r * F], ow, st)
+    spg.sp_batch_sync(b)
+    acts, ovs = _split(cases, dm.cpu().numpy().view(np.uint32), dov.cpu().numpy(), mo, oo)
+    spg.sp_batch_destroy(b)
+    perms = [spg.sp_get_permanences(h) for h in hs]
+    for h in hs:
+        spg.sp_destroy(h)
+    _compare(cases, frames, True, acts, ovs, perms, "uneven64")
+
+
+def test_dense_members_as_benchmarked():
+    """16 dense SPs (1024 x 1024) x 256 frames of inference in one batch call
+    on the tensor cores, run twice (the second run reuses the connection
+    images and replays the recorded launches): every overlap of every frame
+    and member."""
+    cases, frames = wl.dense_cases(16, 256)
+    hs, b, info, fo, mo, oo, ow, fw = _batch(cases)
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    st = torch.cuda.current_stream()
+    results = []
+    for _ in range(2):
+        dm = torch.zeros((256, mw), dtype=torch.int32, device="cuda")
+        dov = torch.full((256, ow), -1.0, dtype=torch.float32, device="cuda")
+        spg.sp_batch_infer_overlaps_device(b, d, 256, fw, dm, mw, dov, ow, st)
+        spg.sp_batch_sync(b)
+        results.append(_split(cases, dm.cpu().numpy().view(np.uint32), dov.cpu().numpy(), mo, oo))
+    spg.sp_batch_destroy(b)
+    for h in hs:
+        spg.sp_destroy(h)
+    for r, (acts, ovs) in enumerate(results):
+        _compare(cases, frames, False, acts, ovs, None, f"dense run {r}")
+
+
+def test_serving_32_streams_three_resolutions():
+    """32 streams (320x180 / 640x360 / 960x540 round-robin, 1024 x 256 SPs with
+    learning and duty cycles) served by the library's worker from 4 producer
+    threads: each stream's winners of every frame and its final permanences
+    equal the oracle's."""
+    n, F = 32, 24
+    cases = wl.serve_cases(n)
+    frames = [wl.serve_frames(i, c.W, c.H, F) for i, c in enumerate(cases)]
+    packed = [wl.pack(f) for f in frames]
+    words = max(p.shape[1] for p in packed)
+    srv = spg.sp_server_create(max_streams=n, queue_depth=4, max_input_words=words,
+                               device_budget_bytes=8 << 30, max_active=64)
+    sids = [spg.sp_server_open_stream(srv, c.config(duty_period=1000.0),
+                                      state=(c.idx, c.perm, c.boost)) for c in cases]
+    got = {i: {} for i in range(n)}
+    errors = []
+
+    def producer(members):
+        try:
+            for t in range(F):
+                for i in members:
+                    while True:
+                        try:
+                            spg.sp_server_submit(srv, sids[i], packed[i][t], True)
+                            break
+                        except spg.SpError as e:
+                            if e.status != 5:  # SP_EBUSY: queue full, offer again
+                                raise
+                            time.sleep(0.0002)
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+
+    threads = [threading.Thread(target=producer, args=(list(range(j, n, 4)),)) for j in range(4)]
+    for th in threads:
+        th.start()
+    done, deadline = 0, time.time() + 120
+    while done < n * F and time.time() < deadline:
+        for r, act in spg.sp_server_poll(srv, max_results=512, wait_ms=20):
+            assert r["status"] == 0
+            got[sids.index(r["stream_id"])][r["frame_seq"]] = act
+            done += 1
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    assert done == n * F
+    st = spg.sp_server_get_stats(srv)
+    assert st["frames_in_launches"] == n * F
+    perms = [spg.sp_server_get_permanences(srv, sids[i], (c.C, c.S)) for i, c in enumerate(cases)]
+    for sid in sids:
+        spg.sp_server_close_stream(srv, sid)
+    spg.sp_server_destroy(srv)
+
+    def check(i):
+        c = cases[i]
+        p = oracle_params(c)
+        perm = c.perm.copy()
+        for t in range(F):
+            a = oracle.run(p, c.idx, perm, c.boost, frames[i][t:t + 1], True)[0]
+            np.testing.assert_array_equal(got[i][t], np.flatnonzero(a),
+                                          err_msg=f"stream {i} ({c.W}x{c.H}) frame {t}")
+        np.testing.assert_array_equal(perms[i], perm, err_msg=f"stream {i} perms")
+
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        list(ex.map(check, range(n)))

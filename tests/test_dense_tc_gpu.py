@@ -1,7 +1,7 @@
 """Dense potential pools (every column sees the whole input) computed without
-learning on the tensor cores (tcgen05, bf16 {0,1} operands, fp32
+learning on the tensor cores (tcgen05 kind::f8f6f4, e4m3 {0,1} operands, fp32
 accumulation: exact), against the CPU oracle and against the per-frame
-kernel.  Bar: bit-exact."""
+kernel.  Bar: bit-exact, on every frame's overlaps and winners."""
 import numpy as np
 import pytest
 
@@ -33,16 +33,19 @@ def _run(case, frames, cfg_extra=None):
     h = spg.sp_create_from_state(cfg, case.idx, case.perm, case.boost)
     d = torch.from_numpy(packed.view(np.int32)).cuda()
     dm = torch.zeros((F, (case.C + 31) // 32), dtype=torch.int32, device="cuda")
+    dov = torch.full((F, case.C), -1.0, dtype=torch.float32, device="cuda")
     before = spg.sp_kernel_launch_count()
-    spg.sp_compute_frames_device(h, d, F, packed.shape[1], False, dm, torch.cuda.current_stream())
+    spg.sp_compute_frames_overlaps_device(h, d, F, packed.shape[1], False, dm, dov,
+                                          torch.cuda.current_stream())
     spg.sp_sync(h)
     launches = spg.sp_kernel_launch_count() - before
     out = dense(dm.cpu().numpy().view(np.uint32), case.C)
+    ovs = dov.cpu().numpy()
     ov = spg.sp_get_overlaps(h)
     lst = spg.sp_active_columns(h)
     duty = spg.sp_get_duty_cycles(h) if (cfg_extra or {}).get("duty_period") else None
     spg.sp_destroy(h)
-    return out, ov, lst, launches, duty
+    return out, ov, lst, launches, duty, ovs
 
 
 def test_dense_pools_on_tensor_cores_match_oracle():
@@ -51,8 +54,9 @@ def test_dense_pools_on_tensor_cores_match_oracle():
     case = _dense_case(1024, 1024, 41, k=40)
     frames = _frames(256, 1024, 0.2, 42)
     act, _, ov = oracle_run(case, frames, False, want_ov=True)
-    got, gov, lst, launches, _ = _run(case, frames)
+    got, gov, lst, launches, _, ovs = _run(case, frames)
     assert launches <= 4  # pack, GEMM, per-frame inhibition: not 256 launches
+    assert first_diff(ovs, ov) is None  # every overlap of every frame
     assert first_diff(got, act) is None
     np.testing.assert_array_equal(gov, ov[-1])
     np.testing.assert_array_equal(lst, np.flatnonzero(act[-1]))
@@ -81,7 +85,7 @@ def test_dense_local_inhibition_and_duty(monkeypatch):
     case = _dense_case(256, 512, 45, k=3, m=2, inhibition=1, gw=16, gh=16, radius=2)
     frames = _frames(40, 512, 0.3, 46)
     act, _, _ = oracle_run(case, frames, False)
-    got, _, _, _, duty = _run(case, frames, {"duty_period": 10.0})
+    got, _, _, _, duty, _ = _run(case, frames, {"duty_period": 10.0})
     assert first_diff(got, act) is None
     import oracle
     d = np.zeros(256, np.float32)
@@ -90,7 +94,7 @@ def test_dense_local_inhibition_and_duty(monkeypatch):
     np.testing.assert_array_equal(duty, d)
     # the per-frame kernel gives the same
     monkeypatch.setenv("SP_DISABLE_TENSOR_CORES", "1")
-    got2, _, _, launches, _ = _run(case, frames)
+    got2, _, _, launches, _, _ = _run(case, frames)
     assert launches >= 40 or launches == 1  # per-frame kernels (or one recorded graph)
     np.testing.assert_array_equal(got2, got)
 
@@ -133,6 +137,7 @@ def test_batch_of_dense_sps_infers_in_two_launches():
     bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
     d = torch.from_numpy(bf.view(np.int32)).cuda()
     mw = info["mask_words"]
+    oo, ow = spg.sp_batch_overlap_offsets(b)
     dm = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
     before = spg.sp_kernel_launch_count()
     spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
@@ -140,14 +145,17 @@ def test_batch_of_dense_sps_infers_in_two_launches():
     # connection images, frame images, GEMM, inhibition
     assert spg.sp_kernel_launch_count() - before == 4
     dm.zero_()
+    dov = torch.full((F, ow), -1.0, dtype=torch.float32, device="cuda")
     before = spg.sp_kernel_launch_count()
-    spg.sp_batch_infer_device(b, d, F, fw, dm, mw, torch.cuda.current_stream())
+    spg.sp_batch_infer_overlaps_device(b, d, F, fw, dm, mw, dov, ow, torch.cuda.current_stream())
     spg.sp_batch_sync(b)
     assert spg.sp_kernel_launch_count() - before == 3  # the connection images are kept
     masks = dm.cpu().numpy().view(np.uint32)
+    ovr = dov.cpu().numpy()
     spg.sp_batch_destroy(b)
     for i, c in enumerate(cases):
         act, _, ov = oracle_run(c, frames[i], False, want_ov=True)
+        assert first_diff(ovr[:, int(oo[i]):int(oo[i]) + c.C], ov) is None, f"member {i} overlaps"
         got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
         assert first_diff(got, act) is None, f"member {i}"
         np.testing.assert_array_equal(spg.sp_get_overlaps(hs[i]), ov[-1])
@@ -172,7 +180,8 @@ def test_dense_global_select_edge_cases(C, k, m, p, unit):
     if C == 333:
         nz = (ov > 0).sum(axis=1)
         assert ((nz > 0) & (nz < k)).any() and (nz >= k).any()  # the case is what it says
-    got, gov, lst, _, _ = _run(case, frames)
+    got, gov, lst, _, _, ovs = _run(case, frames)
+    assert first_diff(ovs, ov) is None
     assert first_diff(got, act) is None
     np.testing.assert_array_equal(gov, ov[-1])
     np.testing.assert_array_equal(lst, np.flatnonzero(act[-1]))

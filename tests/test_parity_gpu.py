@@ -4,7 +4,9 @@ Bar: bit-exact.  Overlaps are integer counts times an fp32 boost (one
 rounding on both sides), the winner set is unique under (overlap desc, index
 asc), and learning is one fp32 add or subtract plus a clamp per synapse, so
 the oracle and the kernels must agree on every active mask, every overlap
-and every permanence, frame after frame.
+and every permanence, frame after frame: the sequence calls record every
+frame's boosted overlaps (sp_compute_frames_overlaps_device) and each one is
+compared element by element.
 """
 import json
 import os
@@ -27,8 +29,9 @@ def _dev(a_u32):
 
 
 def gpu_frames(case, frames_u8, learn, h=None, want=("masks", "perm", "ov")):
-    """Run frames through sp_compute_frames_device (one fused kernel per
-    frame, the launch configuration the benchmark times)."""
+    """Run frames through sp_compute_frames_overlaps_device (the cluster
+    sequence kernel, or one fused kernel per frame), recording every frame's
+    overlaps."""
     packed = wl.pack(frames_u8)
     n = packed.shape[0]
     mw = (case.C + 31) // 32
@@ -38,9 +41,11 @@ def gpu_frames(case, frames_u8, learn, h=None, want=("masks", "perm", "ov")):
     stream = torch.cuda.current_stream()
     d = _dev(packed)
     dm = torch.zeros((n, mw), dtype=torch.int32, device="cuda")
-    spg.sp_compute_frames_device(h, d, n, packed.shape[1], learn, dm, stream)
+    dov = torch.full((n, case.C), -1.0, dtype=torch.float32, device="cuda")
+    spg.sp_compute_frames_overlaps_device(h, d, n, packed.shape[1], learn, dm, dov, stream)
     spg.sp_sync(h)
-    out = {"masks": dense(dm.cpu().numpy().view(np.uint32), case.C)}
+    out = {"masks": dense(dm.cpu().numpy().view(np.uint32), case.C),
+           "ovs": dov.cpu().numpy()}
     if "perm" in want:
         out["perm"] = spg.sp_get_permanences(h)
     if "ov" in want:
@@ -53,6 +58,8 @@ def gpu_frames(case, frames_u8, learn, h=None, want=("masks", "perm", "ov")):
 def assert_same(case, frames_u8, learn, label=""):
     act, perm, ov = oracle_run(case, frames_u8, learn, want_ov=True)
     g = gpu_frames(case, frames_u8, learn)
+    d = first_diff(g["ovs"], ov)
+    assert d is None, f"{label}: first differing overlap (frame, column) {d}"
     d = first_diff(g["masks"], act)
     assert d is None, f"{label}: first differing (frame, column) {d}"
     np.testing.assert_array_equal(g["ov"], ov[-1], err_msg=f"{label}: last-frame overlaps")
@@ -94,6 +101,8 @@ def test_small_config_inference_then_learning():
     g1 = gpu_frames(case, frames[:100], False, h=h)
     g2 = gpu_frames(case, frames[100:], True, h=h)
     spg.sp_destroy(h)
+    assert first_diff(g1["ovs"], ov_i) is None
+    assert first_diff(g2["ovs"], ov_l) is None
     assert first_diff(g1["masks"], act_i) is None
     np.testing.assert_array_equal(g1["perm"], case.perm)
     assert first_diff(g2["masks"], act_l) is None
@@ -313,6 +322,7 @@ def test_set_boost_changes_overlaps_exactly():
                      min_overlap=3)
     act, perm, ov = oracle_run(case_b, frames, True, want_ov=True)
     g = gpu_frames(case_b, frames, True, h=h)
+    assert first_diff(g["ovs"], ov) is None
     assert first_diff(g["masks"], act) is None
     np.testing.assert_array_equal(g["ov"], ov[-1])
     np.testing.assert_array_equal(g["perm"], perm)

@@ -83,9 +83,37 @@ def test_noalloc_matches_handle_path_two_calls_local_ragged():
     assert min(sizes) > 0
 
 
+def test_noalloc_matches_handle_path_paper_literal_k_at_least_c():
+    """The word-for-word Alg. 2 mode with winners_set_size >= C (the floor of
+    1 alone decides), then with k < C and boundary ties."""
+    C, S, n = 300, 12, 512
+    idx = synth.pool_uniform(synth.derive_seed(9, 1, 0), C, S, n)
+    perm = np.full((C, S), 0.2, np.float32)
+    frames = np.stack([synth.frame_bernoulli(synth.derive_seed(9, 3, t), n, 0.35)
+                       for t in range(2)])
+    for k in (C, C + 50, 40):
+        case = wl.Case("literal", n, 1, C, S, idx, perm, np.ones(C, np.float32), k=k,
+                       min_overlap=1, inhibition=2)
+        sizes = _two_calls_against_handle(case, frames, True)
+        assert min(sizes) > 0
+
+
+def test_noalloc_matches_handle_path_non_unit_boosts():
+    """Boosts that are not 1 (the radix select over fp32 products), learning."""
+    C, S, n = 700, 32, 2048
+    idx = synth.pool_uniform(synth.derive_seed(11, 1, 0), C, S, n)
+    perm = synth.perm_uniform(synth.derive_seed(11, 2, 0), (C, S), 0.1, 0.3)
+    boost = synth.perm_uniform(synth.derive_seed(11, 4, 0), (C,), 0.5, 2.0)
+    case = wl.Case("boosted", n, 1, C, S, idx, perm, boost, k=21, min_overlap=2)
+    frames = np.stack([synth.frame_bernoulli(synth.derive_seed(11, 3, t), n, 0.3)
+                       for t in range(2)])
+    sizes = _two_calls_against_handle(case, frames, True)
+    assert sizes == [21, 21]
+
+
 def test_noalloc_allocates_nothing_after_setup():
-    """After the first call on the device (its one-time set-up), further calls
-    leave the device's free memory unchanged."""
+    """After the first call on the device (which may load the library's device
+    code), further calls leave the device's free memory unchanged."""
     case = wl.small_case()
     packed = wl.pack(wl.small_frames(6))
     cfg = case.config()
@@ -112,3 +140,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         spg.sp_step_noalloc(cfg, t, t, t, t, False, t, t)
     assert e.value.status == 1
     assert "SP_NOALLOC_MAX_COLUMNS" in spg.sp_last_error()
+
+
+@pytest.mark.parametrize("bad", [dict(reserved=1), dict(duty_period=float("nan")),
+                                 dict(col_grid_w=7, col_grid_h=7)])
+def test_noalloc_rejects_what_sp_create_rejects(bad):
+    """The configuration checks are sp_create's: a non-zero reserved field, a
+    NaN duty period, a column grid that does not match num_columns."""
+    cfg = spg.sp_config_init(input_w=1024, input_h=1, num_columns=256, synapses_per_column=16,
+                             **bad)
+    t = torch.zeros(256 * 16, dtype=torch.int32, device="cuda")
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_step_noalloc(cfg, t, t, t, t, False, t, t)
+    assert e.value.status == 1
+    with pytest.raises(spg.SpError):
+        spg.sp_create(cfg)
