@@ -129,6 +129,8 @@ void free_handle(sp_handle* h) {
   if (h->d_aimg) cudaFree(h->d_aimg);
   if (h->d_xspan) cudaFree(h->d_xspan);
   if (h->d_compact) cudaFree(h->d_compact);
+  if (h->d_window) cudaFree(h->d_window);
+  if (h->d_wband) cudaFree(h->d_wband);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -655,7 +657,110 @@ bool handle_compact(sp_handle* h) {
   return wide == 0;
 }
 
-void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp) {
+// Shared memory a batch launch may give a window-form CTA for its frame
+// rows (SP_BATCH_WINDOW_KB, 0..96; 0 turns the window form off).  An SP whose
+// band would need more runs on the compact form: the whole launch takes the
+// largest member's figure, so a wide band would cost every CTA occupancy.
+uint32_t window_cap_bytes() {
+  uint32_t kb = 24u;
+  if (const char* e = std::getenv("SP_BATCH_WINDOW_KB")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 0 && v <= 96) kb = (uint32_t)v;
+  }
+  return kb << 10;
+}
+
+// Frame bands of the handle's window form for an n_ctas split; the shared
+// memory the widest needs, or 0 if they cannot be had.
+uint32_t window_bands(sp_handle* h, uint32_t n_ctas) {
+  if (h->wband_ctas != n_ctas) {
+    if (h->d_wband) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->d_wband);
+      h->d_wband = nullptr;
+      h->wband_ctas = 0;
+    }
+    if (device_malloc((void**)&h->d_wband, (size_t)n_ctas * 8) != cudaSuccess) {
+      h->d_wband = nullptr;
+      return 0u;
+    }
+    h->wband_ctas = n_ctas;
+  }
+  std::vector<uint32_t> band((size_t)n_ctas * 2);
+  if (sp::launch_window_bands(h->d_worg, h->C, h->cfg.input_h, n_ctas, h->d_wband, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(band.data(), h->d_wband, band.size() * 4, cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return 0u;
+  uint32_t rows = 0;
+  for (uint32_t b = 0; b < n_ctas; ++b) rows = std::max(rows, band[2 * b + 1]);
+  return sp::window_smem_bytes(rows, (h->cfg.input_w / 32u) | 1u);
+}
+
+// Derive the window form of the handle's pools and connectivity from its
+// current state (every pool inside a 64 x 64 box of a frame whose width is a
+// multiple of 32) and the frame bands of an n_ctas split; false if the SP
+// does not qualify, the bands exceed the cap or the form cannot be had.
+// SP_BATCH_WINDOW_KB=0 turns it off.
+bool handle_window(sp_handle* h, uint32_t n_ctas, uint32_t* win_bytes) {
+  const uint32_t cap = window_cap_bytes();
+  if (cap == 0u || h->window_geom == 0) return false;
+  // a column streams 516 bytes in the window form; it pays only where the
+  // other forms stream about as much (large pools), since a small pool is
+  // cheaper as offsets (2 bytes and a bit per synapse) or indices and
+  // permanences (8 bytes per synapse)
+  const bool compact_shape = h->S % 32u == 0u && h->S <= 256u;
+  const double other = compact_shape ? 2.125 * h->S + 4.0 : 8.0 * h->S;
+  if (516.0 > 1.1 * other) return false;
+  const uint32_t W = h->cfg.input_w;
+  if (W % 32u != 0u || h->S > 4096u) {
+    h->window_geom = 0;
+    return false;
+  }
+  DeviceGuard g(h->device);
+  if (!h->d_window) {
+    const size_t b_org = align256((size_t)h->C * 4), b_bits = align256((size_t)h->C * 512);
+    if (device_malloc(&h->d_window, b_org + b_bits + 256) != cudaSuccess) {
+      h->d_window = nullptr;
+      return false;
+    }
+    char* p = static_cast<char*>(h->d_window);
+    h->d_worg = reinterpret_cast<uint32_t*>(p);
+    h->d_wbits = reinterpret_cast<uint32_t*>(p + b_org);
+    h->d_wbad = reinterpret_cast<uint32_t*>(p + b_org + b_bits);
+  }
+  uint32_t bad = 1;
+  if (cudaMemsetAsync(h->d_wbad, 0, 4, h->stream) != cudaSuccess ||
+      sp::launch_window(h->d_idx, h->d_perm, h->C, h->S, W, h->cfg.connect_threshold, h->d_worg,
+                        h->d_wbits, h->d_wbad, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&bad, h->d_wbad, 4, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return false;
+  h->window_geom = bad ? 0 : 1;
+  if (bad) return false;
+  const uint32_t need = window_bands(h, n_ctas);
+  if (need == 0u || need > cap) return false;
+  if (win_bytes) *win_bytes = need;
+  return true;
+}
+
+bool window_rebands(sp_handle* h, sp::BatchDesc* d, uint32_t* win_bytes) {
+  if (!d->worg) return false;
+  DeviceGuard g(h->device);
+  const uint32_t need = window_bands(h, d->n_ctas);
+  if (need == 0u || need > window_cap_bytes()) {
+    d->worg = nullptr;
+    d->wbits = nullptr;
+    d->wband = nullptr;
+    return false;
+  }
+  d->wband = h->d_wband;
+  if (win_bytes) *win_bytes = need;
+  return true;
+}
+
+void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp, uint32_t* win_bytes) {
   *d = sp::BatchDesc{};
   d->idx = h->d_idx;
   d->perm = h->d_perm;
@@ -685,7 +790,15 @@ void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp) {
   d->radius = h->cfg.local_radius;
   d->n_ctas = batch_ctas(h->C, h->S, cols_per_warp);
   d->xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d->n_ctas) : nullptr;
-  if (handle_compact(h)) {
+  if (win_bytes) *win_bytes = 0u;
+  if (handle_window(h, d->n_ctas, win_bytes)) {
+    d->worg = h->d_worg;
+    d->wbits = h->d_wbits;
+    d->wband = h->d_wband;
+    d->wpr = h->cfg.input_w / 32u;
+    d->wps = d->wpr | 1u;  // an odd row stride: the 32 rows a warp reads hit 32 banks
+    d->win_w = h->cfg.input_w;
+  } else if (handle_compact(h)) {
     d->cidx = h->d_cidx;
     d->cbase = h->d_cbase;
     d->conn = h->d_cconn;
@@ -1106,6 +1219,7 @@ struct sp_batch {
   uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
+  uint32_t win_cap = 0;               // shared memory of the widest window-form CTA
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
   uint32_t* d_err = nullptr;
   uint64_t frame_words = 0, mask_words = 0, ov_words = 0;
@@ -1276,6 +1390,7 @@ sp_status batch_enqueue(sp_batch* b, cudaStream_t st, const uint32_t* x_base, ui
     a.save = (t + 1 == n) ? 1u : 0u;
     a.stage_cap = b->stage_cap;
     a.xspan_cap = b->xspan_cap;
+    a.win_cap = b->win_cap;
     a.err = b->d_err;
     SP_CUDA(sp::launch_batch_step(a, b->n_ctas, b->max_C, st));
     b->pending = learn != 0;
@@ -1318,6 +1433,7 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.err = b->d_err;
     r.stage_cap = b->stage_cap;
     r.xspan_cap = b->xspan_cap;
+    r.win_cap = b->win_cap;
     // counter, abort word and done flags start at 0 in every launch, so a
     // launch recorded into a graph and replayed sees no stale flags
     SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
@@ -1415,7 +1531,9 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
   for (uint32_t i = 0; i < n; ++i) {
     sp_handle* h = members[i];
     sp::BatchDesc& d = desc[i];
-    fill_desc(h, &d);
+    uint32_t wb = 0;
+    fill_desc(h, &d, 0, &wb);
+    b->win_cap = std::max(b->win_cap, wb);
     d.frame_off = foff;
     d.mask_off = moff;
     d.ov_off = ooff;
@@ -1785,12 +1903,22 @@ namespace {
 // be idle.
 sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
   std::vector<uint32_t> cta_inst;
+  uint32_t win_cap = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {
     sp_handle* h = b->members[i];
     sp::BatchDesc& d = b->h_desc[i];
     d.n_ctas = batch_ctas(h->C, h->S, cols_per_warp);
     d.cta_first = (uint32_t)cta_inst.size();
     d.xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d.n_ctas) : nullptr;
+    uint32_t wb = 0;
+    if (d.worg && !window_rebands(h, &d, &wb) && handle_compact(h)) {
+      // the bands of this split do not fit: the compact form, derived from
+      // the permanences as they are now (the window form kept them current)
+      d.cidx = h->d_cidx;
+      d.cbase = h->d_cbase;
+      d.conn = h->d_cconn;
+    }
+    win_cap = std::max(win_cap, wb);
     for (uint32_t c = 0; c < d.n_ctas; ++c) cta_inst.push_back((uint32_t)i);
   }
   const size_t n = b->members.size();
@@ -1810,6 +1938,7 @@ sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
   SP_CUDA(cudaStreamSynchronize(b->stream));
   b->n_ctas = (uint32_t)cta_inst.size();
   b->cols_per_warp = cols_per_warp;
+  b->win_cap = win_cap;
   for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);  // recorded with the old grid
   b->graphs.clear();
   return SP_OK;
@@ -1874,6 +2003,7 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         r.err = b->d_err;
         r.stage_cap = b->stage_cap;
         r.xspan_cap = b->xspan_cap;
+        r.win_cap = b->win_cap;
         e = cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream);
         if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->stream);
       } else {
@@ -1885,6 +2015,7 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
           a.cur = (uint32_t)b->cur;  // inference with nothing pending: parity unchanged
           a.stage_cap = b->stage_cap;
           a.xspan_cap = b->xspan_cap;
+          a.win_cap = b->win_cap;
           a.err = b->d_err;
           e = sp::launch_batch_step(a, b->n_ctas, b->max_C, b->stream);
         }

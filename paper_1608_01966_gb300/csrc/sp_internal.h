@@ -71,7 +71,14 @@ sp_status handle_wait(sp_handle* h);
 sp_status handle_flush_learning(sp_handle* h);
 uint32_t batch_ctas(uint32_t C, uint32_t S, uint32_t cols_per_warp = 0);
 uint32_t batch_stage_cap(uint32_t need);
-void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp = 0);
+// The descriptor of one SP inside a multi-SP launch, in the best form it
+// qualifies for (window, compact, else full); *win_bytes (nullable) receives
+// the shared memory a CTA of this SP needs in the window form, 0 otherwise.
+void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp = 0,
+               uint32_t* win_bytes = nullptr);
+// Recompute the window form's per-CTA frame bands for a new CTA split; false
+// (the descriptor then leaves the window form) if they no longer fit.
+bool window_rebands(sp_handle* h, sp::BatchDesc* d, uint32_t* win_bytes);
 uint32_t batch_xspan_cap();
 
 constexpr uint32_t kChunkFrames = 32;  // frames per staged chunk in sp_compute_frames
@@ -171,6 +178,13 @@ struct sp_handle {
   uint32_t* d_cbase = nullptr;
   uint32_t* d_cconn = nullptr;
   uint32_t* d_cwide = nullptr;
+  void* d_window = nullptr;         // batch window form: worg [C] | wbits [C][128] | flag
+  uint32_t* d_worg = nullptr;
+  uint32_t* d_wbits = nullptr;
+  uint32_t* d_wbad = nullptr;
+  uint32_t* d_wband = nullptr;      // [2][wband_ctas] frame rows of each batch CTA
+  uint32_t wband_ctas = 0;
+  int window_geom = -1;             // pools fit 64 x 64 boxes: -1 unknown, 0 no, 1 yes
   uint32_t* d_xspan = nullptr;      // [2][xspan_ctas] input-word span of each batch CTA
   uint32_t xspan_ctas = 0;
   uint8_t* d_bimg = nullptr;        // e4m3 connection image of a dense SP (tensor-core layout)

@@ -43,6 +43,15 @@ struct StepArgs {
   const uint16_t* cidx;
   const uint32_t* cbase;
   uint32_t* conn;
+  // window form (batches; nullptr = not used), laid out as described at
+  // launch_window: per column the origin of a 64 x 64 box holding its pool
+  // and a bitmap of its connected synapses inside the box
+  const uint32_t* worg;
+  uint32_t* wbits;
+  const uint32_t* wband;  // per CTA: first frame row and row count its columns read
+  uint32_t wpr;           // frame words per row (input_w / 32)
+  uint32_t wps;           // shared-memory words per staged row
+  uint32_t win_w;         // input_w
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
   uint32_t min_overlap, k;
@@ -66,6 +75,10 @@ struct BatchDesc {
   const uint16_t* cidx;   // compact form (nullable), as in StepArgs
   const uint32_t* cbase;
   uint32_t* conn;
+  const uint32_t* worg;   // window form (nullable), as in StepArgs
+  uint32_t* wbits;
+  const uint32_t* wband;
+  uint32_t wpr, wps, win_w;
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
   uint64_t ov_off;      // floats: this SP's overlaps inside one batch overlap record
@@ -94,6 +107,7 @@ struct BatchRunArgs {
   uint32_t* done;               // per SP: epoch + t + 1 once frame t is complete
   uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
   uint32_t stage_cap, xspan_cap;
+  uint32_t win_cap;             // bytes of shared memory for a window-form CTA's band
 };
 
 // Per-launch entry of one SP when a launch steps a chosen subset of SPs,
@@ -123,6 +137,7 @@ struct BatchArgs {
   uint32_t* results_out;        // with tick: per-SP [count, ascending list]
   uint32_t stage_cap;           // bytes of dynamic shared memory for staging state (0: none)
   uint32_t xspan_cap;           // bytes of shared memory for a CTA's input span (0: none)
+  uint32_t win_cap;             // bytes of shared memory for a window-form CTA's band
   uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
 };
 
@@ -138,6 +153,26 @@ cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t
 cudaError_t launch_compact(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
                            float thr, uint16_t* cidx, uint32_t* cbase, uint32_t* conn,
                            uint32_t* wide, cudaStream_t stream);
+
+// Window form of an SP whose input is W pixels wide (W % 32 == 0): for every
+// column, worg[c] = (oy << 16) | ox, the smallest row and column of its pool's
+// pixels, and wbits[c][128] the connected synapses (perm >= thr) as a 64 x 64
+// bitmap of the box starting there -- row r, pixel ox + j is bit j % 32 of
+// word 2r + j / 32 of the row pair, stored so that lane l of a warp loads one
+// 16-byte vector {row l low, row l high, row l + 32 low, row l + 32 high} at
+// word 4l.  *bad is set to 1 if a pool does not fit a 64 x 64 box (or the
+// box origin does not fit 16 bits); the form is unusable then.
+cudaError_t launch_window(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
+                          uint32_t W, float thr, uint32_t* worg, uint32_t* wbits, uint32_t* bad,
+                          cudaStream_t stream);
+// The frame rows each of n_ctas blocks of consecutive columns reads in the
+// window form: out[2b] = first row, out[2b + 1] = row count (0 for an empty
+// block); rows past H - 1 are never read.
+cudaError_t launch_window_bands(const uint32_t* worg, uint32_t C, uint32_t H, uint32_t n_ctas,
+                                uint32_t* out, cudaStream_t stream);
+// Shared memory of a window-form CTA: `rows` staged frame rows of wps words,
+// two words of padding, and a 512-byte learning scratch per warp.
+uint32_t window_smem_bytes(uint32_t rows, uint32_t wps);
 
 // Per-CTA input-word spans of an SP split into n_ctas blocks of consecutive
 // columns: out[2b], out[2b+1] = lowest and one past the highest input word

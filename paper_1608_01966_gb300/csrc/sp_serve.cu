@@ -59,6 +59,7 @@ struct Stream {
   uint64_t launch_seq = 0;     // the request that may launch next
   uint32_t n_ctas = 0, max_active = 0, input_words = 0;
   uint32_t stage_bytes = 0;    // shared memory to stage its CTAs' state
+  uint32_t win_bytes = 0;      // shared memory of its CTAs in the window form (0: other forms)
 };
 
 struct Done {
@@ -221,13 +222,15 @@ sp_status start_launch(sp_server* s, LaunchSlot& L, const LaunchSlot& other) {
   a.cta_inst = L.d_cta;
   a.tick = L.d_table;
   a.results_out = L.d_results;
-  uint32_t max_C = 1, stage = 0;
+  uint32_t max_C = 1, stage = 0, win = 0;
   for (auto& m : L.members) {
     max_C = std::max(max_C, s->streams[m.first].h->C);
     stage = std::max(stage, s->streams[m.first].stage_bytes);
+    win = std::max(win, s->streams[m.first].win_bytes);
   }
   a.stage_cap = batch_stage_cap(stage);
   a.xspan_cap = batch_xspan_cap();
+  a.win_cap = win;
   a.err = L.d_err;
   SP_CUDA(sp::launch_batch_step(a, ctas, max_C, L.st));
   SP_CUDA(cudaMemcpyAsync(L.h_results, L.d_results, (size_t)count * row * 4,
@@ -364,7 +367,7 @@ sp_status admit(sp_server* s, sp_handle* h, uint32_t* stream_id) {
   sp::BatchDesc d;
   // a launch carries one frame of a few tens of streams: small CTAs (16
   // columns) keep every SM busy and the latency low
-  fill_desc(h, &d, kServeColsPerWarp);
+  fill_desc(h, &d, kServeColsPerWarp, &S.win_bytes);
   S.n_ctas = d.n_ctas;
   S.stage_bytes = sp::batch_stage_bytes(h->C, h->S, d.n_ctas);
   const size_t ring_bytes = (size_t)s->cfg.queue_depth * info.input_words * 4;

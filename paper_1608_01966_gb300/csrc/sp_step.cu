@@ -164,6 +164,69 @@ __device__ __forceinline__ uint32_t compact_count(const uint32_t* x, uint32_t ba
   return n;
 }
 
+// ---- window form: a 64 x 64 bitmap of connected synapses per column ---------
+//
+// Pools drawn from a receptive-field window fit a 64 x 64 box of the frame.
+// A column then needs only the box origin and a 512-byte bitmap of its
+// connected synapses inside the box: lane l of the column's warp holds rows l
+// and l + 32 (one 16-byte load), and counts its rows against the frame rows
+// staged in shared memory -- a funnel shift aligns each 64-pixel row segment
+// to the box, an AND with the bitmap row and a population count give the
+// row's share of Alg. 1's count.  No gather leaves shared memory.  A column
+// that learns reads and writes its fp32 permanences (the full form stays
+// authoritative) and rewrites its bitmap.
+
+#ifndef SP_WINDOW_COLS
+#define SP_WINDOW_COLS 4
+#endif
+constexpr int kWinCols = SP_WINDOW_COLS;  // columns per warp in flight
+constexpr uint32_t kWinWords = 128;        // bitmap words per column
+
+__device__ __forceinline__ uint32_t window_row(const uint32_t* p, uint32_t sh, uint32_t lo,
+                                               uint32_t hi) {
+  if ((lo | hi) == 0u) return 0u;  // empty row: nothing is read
+  const uint32_t a0 = p[0], a1 = p[1], a2 = p[2];
+  return __popc(__funnelshift_r(a0, a1, sh) & lo) + __popc(__funnelshift_r(a1, a2, sh) & hi);
+}
+
+// This lane's share of the raw overlap of a column with bitmap rows bm and
+// origin org, against frame rows y0.. staged in `band` at ps words a row.
+__device__ __forceinline__ uint32_t window_count(const uint32_t* band, const uint4& bm,
+                                                 uint32_t org, uint32_t y0, uint32_t ps,
+                                                 int lane) {
+  const uint32_t ox = org & 0xffffu, oy = org >> 16;
+  const uint32_t* p = band + (oy + (uint32_t)lane - y0) * ps + (ox >> 5);
+  return window_row(p, ox & 31u, bm.x, bm.y) + window_row(p + 32u * ps, ox & 31u, bm.z, bm.w);
+}
+
+// Apply the pending learning to column c: writes its permanences and its
+// new bitmap (each lane its own 16 bytes, which the same lane reads back for
+// the count).  scr: this warp's 128-word scratch.
+__device__ __forceinline__ void window_learn(float* perm, const uint32_t* idx, uint32_t* wbits,
+                                           uint32_t* scr, const uint32_t* x_prev, uint32_t c,
+                                           uint32_t S, uint32_t W, uint32_t org, float thr,
+                                           float inc, float dec) {
+  const int lane = threadIdx.x & 31;
+  reinterpret_cast<uint4*>(scr)[lane] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  const uint32_t ox = org & 0xffffu, oy = org >> 16;
+  const uint64_t row = (uint64_t)c * S;
+  for (uint32_t s = lane; s < S; s += 32) {
+    const uint32_t id = __ldg(idx + row + s);
+    const float p = learn_one(perm[row + s], input_bit(x_prev, id), inc, dec);
+    perm[row + s] = p;
+    if (p >= thr) {
+      const uint32_t y = id / W, x = id - y * W;
+      const uint32_t j = x - ox;
+      atomicOr(scr + 2u * (y - oy) + (j >> 5), 1u << (j & 31u));
+    }
+  }
+  __syncwarp();
+  reinterpret_cast<uint4*>(wbits + (uint64_t)c * kWinWords)[lane] =
+      make_uint4(scr[2 * lane], scr[2 * lane + 1], scr[2 * lane + 64], scr[2 * lane + 65]);
+  __syncwarp();  // every lane has read the scratch before it is reused
+}
+
 // Raw overlap of column c (Alg. 1), computed by one warp.  When learn_now,
 // the previous frame's learning is applied first and written back.  With
 // VEC = 4 every lane loads two 16-byte vectors of indices and permanences
@@ -370,7 +433,65 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
-  if (STAGE && a.cidx) {
+  if (STAGE && a.worg) {
+    // window form: the frame rows the CTA's boxes cover are copied to shared
+    // memory first (cp.async, overlapping the first group's bitmap loads);
+    // then kWinCols columns per warp in flight, each counted against them
+    const uint32_t y0 = __ldg(a.wband + 2u * bid), nr = __ldg(a.wband + 2u * bid + 1u);
+    const uint32_t ps = a.wps;
+    uint32_t* band = dyn_smem;
+    uint32_t* scr = dyn_smem + ((nr * ps + 2u + 3u) & ~3u) + (uint32_t)warp * kWinWords;
+    for (uint32_t r = (uint32_t)warp; r < nr; r += kStepWarps) {
+      const uint32_t* src = a.x + (uint64_t)(y0 + r) * a.wpr;
+      for (uint32_t w = (uint32_t)lane; w < a.wpr; w += 32)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(band + r * ps + w)),
+                     "l"(src + w)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (a.mask_prev) {
+      // the previous frame's winners among this warp's columns learn first
+      // (rare), so the counting loop below carries no learning path
+      for (uint32_t base = c_first; base < c_end; base += 32u * c_step) {
+        const uint32_t c = base + (uint32_t)lane * c_step;
+        uint32_t m = __ballot_sync(kFull, c < c_end && learning(c));
+        while (m) {
+          const uint32_t cl = base + (uint32_t)(__ffs(m) - 1) * c_step;
+          m &= m - 1u;
+          window_learn(a.perm, a.idx, a.wbits, scr, a.x_prev, cl, a.S, a.win_w, __ldg(a.worg + cl),
+                       a.thr, a.inc, a.dec);
+        }
+      }
+    }
+    uint4 bm[kWinCols];
+    uint32_t org[kWinCols];
+    auto load_group = [&](uint32_t c0) {
+#pragma unroll
+      for (int j = 0; j < kWinCols; ++j) {
+        const uint32_t c = c0 + j * c_step;
+        const bool ok = c < c_end;
+        bm[j] = ok ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)c * kWinWords) + lane)
+                   : make_uint4(0u, 0u, 0u, 0u);
+        org[j] = ok ? __ldg(a.worg + c) : 0u;
+      }
+    };
+    load_group(c_first);  // in flight while the band lands
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    for (uint32_t c0 = c_first; c0 < c_end; c0 += kWinCols * c_step) {
+      if (c0 != c_first) load_group(c0);
+      uint32_t cnt[kWinCols];
+#pragma unroll
+      for (int j = 0; j < kWinCols; ++j) cnt[j] = window_count(band, bm[j], org[j], y0, ps, lane);
+#pragma unroll
+      for (int j = 0; j < kWinCols; ++j) {
+        const uint32_t c = c0 + j * c_step;
+        const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
+        if (c < c_end && lane == 0) publish(c, r);
+      }
+    }
+    __syncthreads();  // the band becomes the last CTA's working memory
+  } else if (STAGE && a.cidx) {
     // compact form: kCompactCols columns per warp in flight; the input words
     // the CTA's pools index are first copied to shared memory when they fit
     // (the copy overlaps the first group's loads), so the bit gathers read
@@ -640,6 +761,12 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.cidx = d.cidx;
   a.cbase = d.cbase;
   a.conn = d.conn;
+  a.worg = d.worg;
+  a.wbits = d.wbits;
+  a.wband = d.wband;
+  a.wpr = d.wpr;
+  a.wps = d.wps;
+  a.win_w = d.win_w;
   if (!ba.tick) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   a.C = d.C;
   a.S = d.S;
@@ -766,6 +893,12 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
     a.cidx = d.cidx;
     a.cbase = d.cbase;
     a.conn = d.conn;
+    a.worg = d.worg;
+    a.wbits = d.wbits;
+    a.wband = d.wband;
+    a.wpr = d.wpr;
+    a.wps = d.wps;
+    a.win_w = d.win_w;
     a.C = d.C;
     a.S = d.S;
     a.n_words = d.n_words;
@@ -854,6 +987,86 @@ cudaError_t launch_compact(const uint32_t* idx, const float* perm, uint32_t C, u
   return cudaGetLastError();
 }
 
+// One warp per column: the pool's bounding box, then its connected synapses
+// as bits of a 64 x 64 bitmap (built in shared memory, written lane-wise).
+__global__ void __launch_bounds__(256) sp_window_kernel(const uint32_t* idx, const float* perm,
+                                                        uint32_t C, uint32_t S, uint32_t W,
+                                                        float thr, uint32_t* worg,
+                                                        uint32_t* wbits, uint32_t* bad) {
+  __shared__ uint32_t s_bits[8][kWinWords];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t c = blockIdx.x * 8u + warp;
+  if (c >= C) return;
+  const uint64_t row = (uint64_t)c * S;
+  uint32_t x0 = 0xffffffffu, x1 = 0u, y0 = 0xffffffffu, y1 = 0u;
+  for (uint32_t s = lane; s < S; s += 32) {
+    const uint32_t id = idx[row + s], y = id / W, x = id - y * W;
+    x0 = min(x0, x);
+    x1 = max(x1, x);
+    y0 = min(y0, y);
+    y1 = max(y1, y);
+  }
+  x0 = __reduce_min_sync(kFull, x0);
+  x1 = __reduce_max_sync(kFull, x1);
+  y0 = __reduce_min_sync(kFull, y0);
+  y1 = __reduce_max_sync(kFull, y1);
+  if (x1 - x0 >= 64u || y1 - y0 >= 64u || x0 > 0xffffu || y0 > 0xffffu) {
+    if (lane == 0) atomicOr(bad, 1u);
+    return;
+  }
+  uint32_t* sb = s_bits[warp];
+  reinterpret_cast<uint4*>(sb)[lane] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  for (uint32_t s = lane; s < S; s += 32) {
+    if (perm[row + s] >= thr) {
+      const uint32_t id = idx[row + s], y = id / W, x = id - y * W;
+      const uint32_t j = x - x0;
+      atomicOr(sb + 2u * (y - y0) + (j >> 5), 1u << (j & 31u));
+    }
+  }
+  __syncwarp();
+  reinterpret_cast<uint4*>(wbits + (uint64_t)c * kWinWords)[lane] =
+      make_uint4(sb[2 * lane], sb[2 * lane + 1], sb[2 * lane + 64], sb[2 * lane + 65]);
+  if (lane == 0) worg[c] = (y0 << 16) | x0;
+}
+
+cudaError_t launch_window(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
+                          uint32_t W, float thr, uint32_t* worg, uint32_t* wbits, uint32_t* bad,
+                          cudaStream_t stream) {
+  sp_window_kernel<<<(C + 7u) / 8u, 256, 0, stream>>>(idx, perm, C, S, W, thr, worg, wbits, bad);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+// Thread b: the frame rows block b of `per` consecutive columns reads.
+__global__ void __launch_bounds__(128) sp_window_band_kernel(const uint32_t* worg, uint32_t C,
+                                                             uint32_t H, uint32_t per,
+                                                             uint32_t n_ctas, uint32_t* out) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_ctas) return;
+  const uint32_t c0 = min(C, b * per), c1 = min(C, c0 + per);
+  uint32_t y0 = 0xffffffffu, y1 = 0u;
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t oy = worg[c] >> 16;
+    y0 = min(y0, oy);
+    y1 = max(y1, min(H - 1u, oy + 63u));
+  }
+  out[2u * b] = c0 < c1 ? y0 : 0u;
+  out[2u * b + 1u] = c0 < c1 ? y1 - y0 + 1u : 0u;
+}
+
+cudaError_t launch_window_bands(const uint32_t* worg, uint32_t C, uint32_t H, uint32_t n_ctas,
+                                uint32_t* out, cudaStream_t stream) {
+  const uint32_t per = (C + n_ctas - 1u) / n_ctas;
+  sp_window_band_kernel<<<(n_ctas + 127u) / 128u, 128, 0, stream>>>(worg, C, H, per, n_ctas, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+uint32_t window_smem_bytes(uint32_t rows, uint32_t wps) {
+  return (((rows * wps + 2u + 3u) & ~3u) + kStepWarps * kWinWords) * 4u;
+}
+
 // Block b of `per` consecutive columns: lowest and one past the highest input
 // word its pools index.
 __global__ void __launch_bounds__(256) sp_xspan_kernel(const uint32_t* idx, uint32_t C,
@@ -892,8 +1105,8 @@ cudaError_t launch_xspan(const uint32_t* idx, uint32_t C, uint32_t S, uint32_t n
 }
 
 cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream) {
-  const size_t smem =
-      std::max<size_t>(step_smem_bytes(max_C), std::max(r.stage_cap, r.xspan_cap));
+  const size_t smem = std::max<size_t>(step_smem_bytes(max_C),
+                                       std::max(std::max(r.stage_cap, r.xspan_cap), r.win_cap));
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -918,8 +1131,8 @@ uint32_t batch_stage_bytes(uint32_t C, uint32_t S, uint32_t n_ctas) {
 
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream) {
-  const size_t smem =
-      std::max<size_t>(step_smem_bytes(max_C), std::max(a.stage_cap, a.xspan_cap));
+  const size_t smem = std::max<size_t>(step_smem_bytes(max_C),
+                                       std::max(std::max(a.stage_cap, a.xspan_cap), a.win_cap));
   static const bool pdl = [] {
     const char* e = std::getenv("SP_DISABLE_PDL");
     return !(e && e[0] == '1');

@@ -123,16 +123,21 @@ def test_batch_staged_state(monkeypatch, cpw):
     _check(cases, frames, True, acts, perms, ovs, f"staged cpw={cpw}")
 
 
+@pytest.mark.parametrize("window_kb", ["24", "0"])
 @pytest.mark.parametrize("xspan_kb", ["0", "16"])
 @pytest.mark.parametrize("compact", ["1", "0"])
-def test_batch_compact_form(monkeypatch, compact, xspan_kb):
-    """Members whose synapse count is a multiple of 32 (<= 256) and whose pools
-    span at most 65536 inputs run on 16-bit offsets and connected bits; the
-    others (a pool spread over a 960x540 frame, S = 48) on the full form.
-    Both must equal the oracle, learning included, with the CTAs' input words
-    read from global memory or first copied to shared memory."""
+def test_batch_compact_form(monkeypatch, compact, xspan_kb, window_kb):
+    """Members whose pools fit 64 x 64 boxes of a frame 32k pixels wide run on
+    the window form (box origin + bitmap of connected synapses, frame rows
+    staged in shared memory) unless it is off; members whose synapse count is
+    a multiple of 32 (<= 256) and whose pools span at most 65536 inputs run on
+    16-bit offsets and connected bits; the others (a pool spread over a 960x540
+    frame, S = 48) on the full form.  Every form must
+    equal the oracle, learning included, with the CTAs' input words read from
+    global memory or first copied to shared memory."""
     monkeypatch.setenv("SP_BATCH_COMPACT", compact)
     monkeypatch.setenv("SP_BATCH_XSPAN_KB", xspan_kb)
+    monkeypatch.setenv("SP_BATCH_WINDOW_KB", window_kb)
     cases, frames = [], []
     for i, S in enumerate((32, 64, 128, 256)):
         c = wl.grid_case(f"win{S}", 256, S, wl.BASE_SEED + 400 + i, W=320, H=180, rf=32, k=6,
@@ -277,14 +282,18 @@ def test_batch_long_sequence_in_one_call(monkeypatch, persistent):
     _check(cases, frames, True, acts, perms, ovs, f"persistent={persistent}")
 
 
+@pytest.mark.parametrize("window_kb", ["24", "0"])
 @pytest.mark.parametrize("C", [256, 1024, 4096])
-def test_batch_parameter_sweep(C):
+def test_batch_parameter_sweep(C, window_kb, monkeypatch):
     """The sweep workload at its stated length: the 54 synapse x min_overlap x
     k x {global, 9x9 local} combinations for one column count, as members of
-    one batch (compact form for S = 64 and 256, full form for S = 16), 200
+    one batch (window form, else compact form for S = 64 and 256 and full form
+    for S = 16), 200
     learning frames of 960x540 blobbed input in one persistent launch; every
     member's overlaps and winners of every frame, and its final permanences,
-    against the oracle."""
+    against the oracle.  Window-shaped pools run on the window form, or with it
+    off on the compact form."""
+    monkeypatch.setenv("SP_BATCH_WINDOW_KB", window_kb)
     frames1 = wl.blob_frames(SWEEP_FRAMES, seed=wl.BASE_SEED + 3)
     cases, frames = [], []
     for S in (16, 64, 256):
