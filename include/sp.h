@@ -370,6 +370,16 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
                                                 float* d_overlaps, uint64_t ov_stride,
                                                 void* stream);
 
+/* Bound, in nanoseconds of the GPU's global timer, of the one wait inside a
+ * persistent batch launch: a CTA item of a member's frame t + 1 waits for
+ * that member's frame t, which CTAs already running compute, so the wait
+ * ends by itself; if it has not ended within the bound, the launch stops
+ * taking work and the next sp_batch_sync (or synchronous call) returns
+ * SP_ETIMEOUT.  The members then hold a partially computed run (frames of
+ * some members done, others not); the batch's per-launch counters are reset,
+ * so later calls run normally.  0 restores the default of 1 s. */
+SP_API sp_status sp_batch_set_device_wait_ns(sp_batch* b, uint64_t ns);
+
 /* Wait (bounded) until the batch's enqueued work has finished. */
 SP_API sp_status sp_batch_sync(sp_batch* b);
 

@@ -148,6 +148,7 @@ def lib():
         L.sp_batch_infer_overlaps_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp,
                                                      ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_batch_sync.argtypes = [vp]
+        L.sp_batch_set_device_wait_ns.argtypes = [vp, ct.c_uint64]
         L.sp_batch_autotune.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, _u32p]
         L.sp_batch_infer_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_server_create.argtypes = [ct.POINTER(SpServerConfig), ct.POINTER(vp)]
@@ -451,6 +452,10 @@ def sp_batch_infer_device(b, d_frames, n_frames, stride_words, d_masks=None,
     _check(lib().sp_batch_infer_device(b, _addr(d_frames), n_frames, stride_words,
                                        _addr(d_masks), mask_stride_words, _stream(stream)),
            "sp_batch_infer_device")
+
+
+def sp_batch_set_device_wait_ns(b, ns):
+    _check(lib().sp_batch_set_device_wait_ns(b, ns), "sp_batch_set_device_wait_ns")
 
 
 def sp_batch_sync(b):

@@ -1221,6 +1221,7 @@ struct sp_batch {
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
   uint32_t win_cap = 0;               // shared memory of the widest window-form CTA
   uint32_t* h_err = nullptr;          // mapped host word: a bounded wait expired
+  uint64_t wait_ns = kDeviceWaitNs;   // bound of a persistent launch's per-SP frame wait
   uint32_t* d_err = nullptr;
   uint64_t frame_words = 0, mask_words = 0, ov_words = 0;
   std::vector<uint64_t> frame_off, mask_off, ov_off;
@@ -1309,7 +1310,15 @@ sp_status batch_wait(sp_batch* b) {
     if (e == cudaSuccess) {
       if (b->h_err && *reinterpret_cast<volatile uint32_t*>(b->h_err)) {
         *b->h_err = 0u;
-        return fail(SP_ETIMEOUT, "a bulk copy of column state did not complete");
+        // a launch gave up part way: frames of some members stopped after
+        // some CTAs took their tickets and counted their histograms, so
+        // both are cleared for the next launch
+        for (sp_handle* h : b->members) {
+          SP_CUDA(cudaMemsetAsync(h->d_counter, 0, 4, b->stream));
+          if (h->d_hist) SP_CUDA(cudaMemsetAsync(h->d_hist, 0, ((size_t)h->S + 1) * 4, b->stream));
+        }
+        SP_CUDA(cudaStreamSynchronize(b->stream));
+        return fail(SP_ETIMEOUT, "a bounded device wait expired (the launch stopped early)");
       }
       return SP_OK;
     }
@@ -1434,6 +1443,7 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     r.stage_cap = b->stage_cap;
     r.xspan_cap = b->xspan_cap;
     r.win_cap = b->win_cap;
+    r.wait_ns = b->wait_ns;
     // counter, abort word and done flags start at 0 in every launch, so a
     // launch recorded into a graph and replayed sees no stale flags
     SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
@@ -2004,6 +2014,7 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         r.stage_cap = b->stage_cap;
         r.xspan_cap = b->xspan_cap;
         r.win_cap = b->win_cap;
+        r.wait_ns = b->wait_ns;
         e = cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream);
         if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->stream);
       } else {
@@ -2050,6 +2061,15 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
   cudaEventDestroy(e1);
   if (s == SP_OK && cols_per_warp) *cols_per_warp = best;
   return s;
+}
+
+SP_API sp_status sp_batch_set_device_wait_ns(sp_batch* b, uint64_t ns) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  b->wait_ns = ns ? ns : kDeviceWaitNs;
+  // recorded launches carry the old bound
+  for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);
+  b->graphs.clear();
+  return SP_OK;
 }
 
 SP_API sp_status sp_batch_sync(sp_batch* b) {

@@ -121,6 +121,7 @@ struct GraphEntry {
 };
 
 constexpr uint32_t kDenseMinFrames = 16;  // shorter inference runs use the per-frame kernel
+constexpr uint64_t kDeviceWaitNs = 1000000000ull;  // default bound of an in-kernel wait: 1 s
 
 inline bool dense_enabled() {
   const char* s = std::getenv("SP_DISABLE_TENSOR_CORES");

@@ -108,6 +108,7 @@ struct BatchRunArgs {
   uint32_t* err;                // set to 1 if a bounded wait expired (nullable)
   uint32_t stage_cap, xspan_cap;
   uint32_t win_cap;             // bytes of shared memory for a window-form CTA's band
+  uint64_t wait_ns;             // bound of an item's wait for its SP's previous frame
 };
 
 // Per-launch entry of one SP when a launch steps a chosen subset of SPs,

@@ -201,7 +201,11 @@ __device__ __forceinline__ uint32_t window_count(const uint32_t* band, const uin
 
 // Apply the pending learning to column c: writes its permanences and its
 // new bitmap (each lane its own 16 bytes, which the same lane reads back for
-// the count).  scr: this warp's 128-word scratch.
+// the count).  scr: this warp's 128-word scratch.  A lane's pool indices and
+// permanences of a pass are all loaded before the first input bit is
+// gathered, so a learning column costs about one memory latency per pass of
+// 32 x kWinLearnUnroll synapses.
+constexpr int kWinLearnUnroll = 8;
 __device__ __forceinline__ void window_learn(float* perm, const uint32_t* idx, uint32_t* wbits,
                                            uint32_t* scr, const uint32_t* x_prev, uint32_t c,
                                            uint32_t S, uint32_t W, uint32_t org, float thr,
@@ -211,14 +215,32 @@ __device__ __forceinline__ void window_learn(float* perm, const uint32_t* idx, u
   __syncwarp();
   const uint32_t ox = org & 0xffffu, oy = org >> 16;
   const uint64_t row = (uint64_t)c * S;
-  for (uint32_t s = lane; s < S; s += 32) {
-    const uint32_t id = __ldg(idx + row + s);
-    const float p = learn_one(perm[row + s], input_bit(x_prev, id), inc, dec);
-    perm[row + s] = p;
-    if (p >= thr) {
-      const uint32_t y = id / W, x = id - y * W;
-      const uint32_t j = x - ox;
-      atomicOr(scr + 2u * (y - oy) + (j >> 5), 1u << (j & 31u));
+  for (uint32_t s0 = 0; s0 < S; s0 += 32u * kWinLearnUnroll) {
+    uint32_t id[kWinLearnUnroll], bit[kWinLearnUnroll];
+    float p[kWinLearnUnroll];
+#pragma unroll
+    for (int k = 0; k < kWinLearnUnroll; ++k) {
+      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
+      id[k] = s < S ? __ldg(idx + row + s) : 0u;
+      p[k] = s < S ? __ldcg(perm + row + s) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kWinLearnUnroll; ++k) {
+      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
+      bit[k] = s < S ? input_bit(x_prev, id[k]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kWinLearnUnroll; ++k) {
+      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
+      if (s < S) {
+        const float q = learn_one(p[k], bit[k], inc, dec);
+        perm[row + s] = q;
+        if (q >= thr) {
+          const uint32_t y = id[k] / W, x = id[k] - y * W;
+          const uint32_t j = x - ox;
+          atomicOr(scr + 2u * (y - oy) + (j >> 5), 1u << (j & 31u));
+        }
+      }
     }
   }
   __syncwarp();
@@ -433,7 +455,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
-  if (STAGE && a.worg) {
+  if (STAGE && SP_CONTIG_COLUMNS && a.worg) {
     // window form: the frame rows the CTA's boxes cover are copied to shared
     // memory first (cp.async, overlapping the first group's bitmap loads);
     // then kWinCols columns per warp in flight, each counted against them
@@ -450,14 +472,18 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     if (a.mask_prev) {
-      // the previous frame's winners among this warp's columns learn first
-      // (rare), so the counting loop below carries no learning path
-      for (uint32_t base = c_first; base < c_end; base += 32u * c_step) {
-        const uint32_t c = base + (uint32_t)lane * c_step;
+      // the previous frame's winners among the CTA's columns learn first
+      // (rare), dealt round-robin to its warps, so the counting loop below
+      // carries no learning path; the CTA barrier after the band copy orders
+      // each rewritten bitmap before any warp loads it
+      const uint32_t lo = c_first - (SP_CONTIG_COLUMNS ? (uint32_t)warp : 0u);
+      uint32_t q = 0;
+      for (uint32_t base = lo; base < c_end; base += 32u) {
+        const uint32_t c = base + (uint32_t)lane;
         uint32_t m = __ballot_sync(kFull, c < c_end && learning(c));
-        while (m) {
-          const uint32_t cl = base + (uint32_t)(__ffs(m) - 1) * c_step;
-          m &= m - 1u;
+        for (; m; m &= m - 1u, ++q) {
+          if ((q % kStepWarps) != (uint32_t)warp) continue;
+          const uint32_t cl = base + (uint32_t)(__ffs(m) - 1);
           window_learn(a.perm, a.idx, a.wbits, scr, a.x_prev, cl, a.S, a.win_w, __ldg(a.worg + cl),
                        a.thr, a.inc, a.dec);
         }
@@ -475,9 +501,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
         org[j] = ok ? __ldg(a.worg + c) : 0u;
       }
     };
-    load_group(c_first);  // in flight while the band lands
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
+    load_group(c_first);
     for (uint32_t c0 = c_first; c0 < c_end; c0 += kWinCols * c_step) {
       if (c0 != c_first) load_group(c0);
       uint32_t cnt[kWinCols];
@@ -812,9 +838,9 @@ int step_grid(uint32_t C) { return (int)((C + kStepWarps - 1) / kStepWarps); }
 // (the SP's last CTA of that frame releases done[inst] = epoch + t).  The
 // items it waits for were taken earlier by CTAs that are running, so the
 // wait always ends; it is bounded all the same (1 s of %globaltimer, then
-// the launch is aborted and the error word set).  Frame t + 1 of one SP thus
-// overlaps frame t of the others instead of waiting for a whole grid.
-constexpr unsigned long long kDoneWaitNs = 1000000000ull;
+// the launch is aborted and the error word set; r.wait_ns sets the bound).
+// Frame t + 1 of one SP thus overlaps frame t of the others instead of
+// waiting for a whole grid.
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
@@ -851,7 +877,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
         uint32_t ok = 1u;
         for (uint32_t i = 0;; ++i) {
           if ((int32_t)(ld_acquire(r.done + inst) - target) >= 0) break;
-          if (ld_acquire(r.abort) != 0u || global_ns() - t0 > kDoneWaitNs) {
+          if (ld_acquire(r.abort) != 0u || global_ns() - t0 > r.wait_ns) {
             ok = 0u;
             break;
           }

@@ -102,3 +102,46 @@ def test_injected_allocation_failure(monkeypatch):
     spg.sp_compute(h, wl.pack(wl.small_frames(1))[0], True)
     assert spg.sp_active_columns(h).size <= 10
     spg.sp_destroy(h)
+
+
+def test_device_wait_expires_then_the_batch_runs_clean():
+    """The one wait inside a persistent batch launch (an item of a member's
+    frame t + 1 waiting for that member's frame t) given a bound of 1 ns: the
+    launch stops early and the batch reports SP_ETIMEOUT without hanging;
+    with the default bound restored, the same batch then computes a learning
+    run whose overlaps, winners and permanences equal the oracle's."""
+    cases = [wl.frame_case(seed=wl.BASE_SEED + 720 + i) for i in range(4)]
+    frames = [wl.blob_frames(12, seed=wl.BASE_SEED + 720 + i) for i in range(4)]
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    oo, ow = spg.sp_batch_overlap_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    d = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in frames], fo, fw).view(np.int32)).cuda()
+    st = torch.cuda.current_stream()
+    # 4 members x 8 CTAs per frame: every frame-1 item is taken while frame 0
+    # is still being computed, so it must wait, and a 1 ns bound expires
+    spg.sp_batch_set_device_wait_ns(b, 1)
+    spg.sp_batch_compute_device(b, d, 12, fw, False, None, 0, st)
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_batch_sync(b)
+    assert e.value.status == 4  # SP_ETIMEOUT
+    spg.sp_batch_set_device_wait_ns(b, 0)  # the default bound
+    mw = info["mask_words"]
+    dm = torch.zeros((12, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((12, ow), -1.0, dtype=torch.float32, device="cuda")
+    spg.sp_batch_compute_overlaps_device(b, d, 12, fw, True, dm, mw, dov, ow, st)
+    spg.sp_batch_sync(b)
+    masks = dm.cpu().numpy().view(np.uint32)
+    ovr = dov.cpu().numpy()
+    spg.sp_batch_destroy(b)
+    for i, c in enumerate(cases):
+        p = oracle_params(c)
+        perm = c.perm.copy()
+        act, ov = oracle.run(p, c.idx, perm, c.boost, frames[i], True, want_ov=True)
+        assert first_diff(ovr[:, int(oo[i]):int(oo[i]) + c.C], ov) is None, f"member {i} overlaps"
+        got = dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C)
+        assert first_diff(got, act) is None, f"member {i} winners"
+        np.testing.assert_array_equal(spg.sp_get_permanences(hs[i]), perm, err_msg=f"member {i}")
+        spg.sp_destroy(hs[i])
