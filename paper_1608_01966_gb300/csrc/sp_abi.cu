@@ -658,14 +658,15 @@ bool handle_compact(sp_handle* h) {
 }
 
 // Shared memory a batch launch may give a window-form CTA for its frame
-// rows (SP_BATCH_WINDOW_KB, 0..96; 0 turns the window form off).  An SP whose
-// band would need more runs on the compact form: the whole launch takes the
-// largest member's figure, so a wide band would cost every CTA occupancy.
+// rows, bitmap rings and learning scratch (SP_BATCH_WINDOW_KB, 0..160; 0
+// turns the window form off).  An SP whose CTAs would need more runs on the
+// compact form: the whole launch takes the largest member's figure, so a
+// wide band would cost every CTA occupancy.
 uint32_t window_cap_bytes() {
-  uint32_t kb = 24u;
+  uint32_t kb = 48u;
   if (const char* e = std::getenv("SP_BATCH_WINDOW_KB")) {
     const long v = std::strtol(e, nullptr, 10);
-    if (v >= 0 && v <= 96) kb = (uint32_t)v;
+    if (v >= 0 && v <= 160) kb = (uint32_t)v;
   }
   return kb << 10;
 }
@@ -695,7 +696,7 @@ uint32_t window_bands(sp_handle* h, uint32_t n_ctas) {
     return 0u;
   uint32_t rows = 0;
   for (uint32_t b = 0; b < n_ctas; ++b) rows = std::max(rows, band[2 * b + 1]);
-  return sp::window_smem_bytes(rows, (h->cfg.input_w / 32u) | 1u);
+  return sp::window_smem_bytes(rows, h->cfg.input_w / 32u);
 }
 
 // Derive the window form of the handle's pools and connectivity from its
@@ -718,6 +719,7 @@ bool handle_window(sp_handle* h, uint32_t n_ctas, uint32_t* win_bytes) {
     h->window_geom = 0;
     return false;
   }
+  if ((h->C + n_ctas - 1u) / n_ctas > 256u) return false;  // a CTA holds at most 256 columns
   DeviceGuard g(h->device);
   if (!h->d_window) {
     const size_t b_org = align256((size_t)h->C * 4), b_bits = align256((size_t)h->C * 512);
@@ -748,7 +750,7 @@ bool handle_window(sp_handle* h, uint32_t n_ctas, uint32_t* win_bytes) {
 bool window_rebands(sp_handle* h, sp::BatchDesc* d, uint32_t* win_bytes) {
   if (!d->worg) return false;
   DeviceGuard g(h->device);
-  const uint32_t need = window_bands(h, d->n_ctas);
+  const uint32_t need = (h->C + d->n_ctas - 1u) / d->n_ctas > 256u ? 0u : window_bands(h, d->n_ctas);
   if (need == 0u || need > window_cap_bytes()) {
     d->worg = nullptr;
     d->wbits = nullptr;
@@ -796,7 +798,6 @@ void fill_desc(sp_handle* h, sp::BatchDesc* d, uint32_t cols_per_warp, uint32_t*
     d->wbits = h->d_wbits;
     d->wband = h->d_wband;
     d->wpr = h->cfg.input_w / 32u;
-    d->wps = d->wpr | 1u;  // an odd row stride: the 32 rows a warp reads hit 32 banks
     d->win_w = h->cfg.input_w;
   } else if (handle_compact(h)) {
     d->cidx = h->d_cidx;

@@ -50,7 +50,6 @@ struct StepArgs {
   uint32_t* wbits;
   const uint32_t* wband;  // per CTA: first frame row and row count its columns read
   uint32_t wpr;           // frame words per row (input_w / 32)
-  uint32_t wps;           // shared-memory words per staged row
   uint32_t win_w;         // input_w
   uint32_t C, S, n_words, mask_words;
   float thr, inc, dec;
@@ -78,7 +77,7 @@ struct BatchDesc {
   const uint32_t* worg;   // window form (nullable), as in StepArgs
   uint32_t* wbits;
   const uint32_t* wband;
-  uint32_t wpr, wps, win_w;
+  uint32_t wpr, win_w;
   uint64_t frame_off;   // words: this SP's frame inside one batch frame
   uint64_t mask_off;    // words: this SP's mask inside one batch mask record
   uint64_t ov_off;      // floats: this SP's overlaps inside one batch overlap record
@@ -171,9 +170,10 @@ cudaError_t launch_window(const uint32_t* idx, const float* perm, uint32_t C, ui
 // block); rows past H - 1 are never read.
 cudaError_t launch_window_bands(const uint32_t* worg, uint32_t C, uint32_t H, uint32_t n_ctas,
                                 uint32_t* out, cudaStream_t stream);
-// Shared memory of a window-form CTA: `rows` staged frame rows of wps words,
-// two words of padding, and a 512-byte learning scratch per warp.
-uint32_t window_smem_bytes(uint32_t rows, uint32_t wps);
+// Shared memory of a window-form CTA: `rows` staged frame rows of wpr words
+// (input_w / 32), the per-warp rings of bitmap slots and the learning
+// scratch.
+uint32_t window_smem_bytes(uint32_t rows, uint32_t wpr);
 
 // Per-CTA input-word spans of an SP split into n_ctas blocks of consecutive
 // columns: out[2b], out[2b+1] = lowest and one past the highest input word

@@ -164,91 +164,6 @@ __device__ __forceinline__ uint32_t compact_count(const uint32_t* x, uint32_t ba
   return n;
 }
 
-// ---- window form: a 64 x 64 bitmap of connected synapses per column ---------
-//
-// Pools drawn from a receptive-field window fit a 64 x 64 box of the frame.
-// A column then needs only the box origin and a 512-byte bitmap of its
-// connected synapses inside the box: lane l of the column's warp holds rows l
-// and l + 32 (one 16-byte load), and counts its rows against the frame rows
-// staged in shared memory -- a funnel shift aligns each 64-pixel row segment
-// to the box, an AND with the bitmap row and a population count give the
-// row's share of Alg. 1's count.  No gather leaves shared memory.  A column
-// that learns reads and writes its fp32 permanences (the full form stays
-// authoritative) and rewrites its bitmap.
-
-#ifndef SP_WINDOW_COLS
-#define SP_WINDOW_COLS 4
-#endif
-constexpr int kWinCols = SP_WINDOW_COLS;  // columns per warp in flight
-constexpr uint32_t kWinWords = 128;        // bitmap words per column
-
-__device__ __forceinline__ uint32_t window_row(const uint32_t* p, uint32_t sh, uint32_t lo,
-                                               uint32_t hi) {
-  if ((lo | hi) == 0u) return 0u;  // empty row: nothing is read
-  const uint32_t a0 = p[0], a1 = p[1], a2 = p[2];
-  return __popc(__funnelshift_r(a0, a1, sh) & lo) + __popc(__funnelshift_r(a1, a2, sh) & hi);
-}
-
-// This lane's share of the raw overlap of a column with bitmap rows bm and
-// origin org, against frame rows y0.. staged in `band` at ps words a row.
-__device__ __forceinline__ uint32_t window_count(const uint32_t* band, const uint4& bm,
-                                                 uint32_t org, uint32_t y0, uint32_t ps,
-                                                 int lane) {
-  const uint32_t ox = org & 0xffffu, oy = org >> 16;
-  const uint32_t* p = band + (oy + (uint32_t)lane - y0) * ps + (ox >> 5);
-  return window_row(p, ox & 31u, bm.x, bm.y) + window_row(p + 32u * ps, ox & 31u, bm.z, bm.w);
-}
-
-// Apply the pending learning to column c: writes its permanences and its
-// new bitmap (each lane its own 16 bytes, which the same lane reads back for
-// the count).  scr: this warp's 128-word scratch.  A lane's pool indices and
-// permanences of a pass are all loaded before the first input bit is
-// gathered, so a learning column costs about one memory latency per pass of
-// 32 x kWinLearnUnroll synapses.
-constexpr int kWinLearnUnroll = 8;
-__device__ __forceinline__ void window_learn(float* perm, const uint32_t* idx, uint32_t* wbits,
-                                           uint32_t* scr, const uint32_t* x_prev, uint32_t c,
-                                           uint32_t S, uint32_t W, uint32_t org, float thr,
-                                           float inc, float dec) {
-  const int lane = threadIdx.x & 31;
-  reinterpret_cast<uint4*>(scr)[lane] = make_uint4(0u, 0u, 0u, 0u);
-  __syncwarp();
-  const uint32_t ox = org & 0xffffu, oy = org >> 16;
-  const uint64_t row = (uint64_t)c * S;
-  for (uint32_t s0 = 0; s0 < S; s0 += 32u * kWinLearnUnroll) {
-    uint32_t id[kWinLearnUnroll], bit[kWinLearnUnroll];
-    float p[kWinLearnUnroll];
-#pragma unroll
-    for (int k = 0; k < kWinLearnUnroll; ++k) {
-      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
-      id[k] = s < S ? __ldg(idx + row + s) : 0u;
-      p[k] = s < S ? __ldcg(perm + row + s) : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < kWinLearnUnroll; ++k) {
-      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
-      bit[k] = s < S ? input_bit(x_prev, id[k]) : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < kWinLearnUnroll; ++k) {
-      const uint32_t s = s0 + (uint32_t)lane + 32u * k;
-      if (s < S) {
-        const float q = learn_one(p[k], bit[k], inc, dec);
-        perm[row + s] = q;
-        if (q >= thr) {
-          const uint32_t y = id[k] / W, x = id[k] - y * W;
-          const uint32_t j = x - ox;
-          atomicOr(scr + 2u * (y - oy) + (j >> 5), 1u << (j & 31u));
-        }
-      }
-    }
-  }
-  __syncwarp();
-  reinterpret_cast<uint4*>(wbits + (uint64_t)c * kWinWords)[lane] =
-      make_uint4(scr[2 * lane], scr[2 * lane + 1], scr[2 * lane + 64], scr[2 * lane + 65]);
-  __syncwarp();  // every lane has read the scratch before it is reused
-}
-
 // Raw overlap of column c (Alg. 1), computed by one warp.  When learn_now,
 // the previous frame's learning is applied first and written back.  With
 // VEC = 4 every lane loads two 16-byte vectors of indices and permanences
@@ -417,6 +332,271 @@ __host__ __device__ __forceinline__ uint32_t stage_ring_bytes(uint32_t S) {
   return kRing * 2u * S * 4u;
 }
 
+// Alg. 1's tail for column c with raw count `raw` (one lane): the boosted
+// overlap to the SP's overlaps (and the caller's record), and, with unit
+// boosts, the count into the histogram the last CTA selects from.
+__device__ __forceinline__ void publish_overlap(const StepArgs& a, uint32_t c, uint32_t raw) {
+  // a histogram is kept only when every boost is exactly 1, and then the
+  // product is the count itself: no load stalls the warp here
+  const float v = dev::boosted(raw, a.min_overlap, a.hist ? 1.0f : __ldg(a.boost + c));
+  a.ov[c] = v;
+  if (a.ov_copy) a.ov_copy[c] = v;
+  if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
+}
+
+// ---- window form: a 64 x 64 bitmap of connected synapses per column ---------
+//
+// Pools drawn from a receptive-field window fit a 64 x 64 box of the frame.
+// A column then needs only the box origin and a 512-byte bitmap of its
+// connected synapses inside the box.  A CTA's columns are consecutive, so
+// their boxes cover a band of consecutive frame rows: the band is copied to
+// shared memory once per item (one bulk copy).  Every warp then counts its
+// columns kWinCols at a time, their bitmaps loaded into registers (16 bytes
+// per lane and column, one coalesced request per column) -- with
+// SP_WIN_PIPE the next group's loads are issued before the current group is
+// counted.  Lane l of a column's warp counts rows l and l + 32 of its box: a
+// funnel shift aligns each 64-pixel row segment of the band to the box, an
+// AND with the bitmap row and a population count give the row's share of
+// Alg. 1's count.  No gather leaves shared memory.
+//
+// Learning (the previous frame's winners, rare) runs first, CTA-wide: all
+// synapses of up to kWinLearn columns at once, a pass's indices and
+// permanences loaded before its first input bit is gathered.  The
+// permanences (the full form stays authoritative) and the new bitmaps go to
+// global memory; the first kWinLearn learners' bitmaps also stay in shared
+// memory, where the count reads them (the first group's loads are issued
+// before the update), and any further learner's is read back from global
+// memory.
+
+#ifndef SP_WINDOW_COLS
+#define SP_WINDOW_COLS 4
+#endif
+#ifndef SP_WIN_PIPE
+#define SP_WIN_PIPE 0
+#endif
+constexpr int kWinCols = SP_WINDOW_COLS;  // columns per warp in flight
+constexpr uint32_t kWinLearn = 8;         // learners kept in shared memory
+constexpr uint32_t kWinWords = 128;       // bitmap words per column
+constexpr uint32_t kWinMaxCols = 256;     // columns of one CTA (4 warps x 64)
+constexpr int kWinLearnUnroll = 4;
+
+__device__ __forceinline__ uint32_t window_row(const uint32_t* p, uint32_t sh, uint32_t lo,
+                                               uint32_t hi) {
+  const uint32_t a0 = p[0], a1 = p[1], a2 = p[2];
+  return __popc(__funnelshift_r(a0, a1, sh) & lo) + __popc(__funnelshift_r(a1, a2, sh) & hi);
+}
+
+// This lane's share of the raw overlap of a column with bitmap rows bm and
+// box origin org, against frame words staged in `band` (band[i] = frame word
+// base + i; wpr words per frame row).
+__device__ __forceinline__ uint32_t window_count(const uint32_t* band, const uint4& bm,
+                                                 uint32_t org, uint32_t base, uint32_t wpr,
+                                                 int lane) {
+  const uint32_t ox = org & 0xffffu, oy = org >> 16;
+  const uint32_t* p = band + ((oy + (uint32_t)lane) * wpr + (ox >> 5) - base);
+  return window_row(p, ox & 31u, bm.x, bm.y) + window_row(p + 32u * wpr, ox & 31u, bm.z, bm.w);
+}
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// A barrier initialized for one item is invalidated at its end, so that the
+// next item of a persistent CTA may initialize the same memory again.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// The window form's pass of one CTA over its columns [lo, hi), whose boxes
+// lie in frame rows [y0, y0 + nr) (see above).  If the band's copy does not
+// complete in time the error word is set, the copy is waited for (bounded)
+// and the columns publish 0.
+template <bool STREAM>
+__device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint32_t hi,
+                                            uint32_t y0, uint32_t nr, uint32_t* dyn_smem,
+                                            uint32_t* err) {
+  __shared__ uint32_t s_org[kWinMaxCols];
+  __shared__ uint8_t s_lmap[kWinMaxCols];  // 0, or 1 + the learner's scratch slot, or 255
+  __shared__ uint32_t s_lcol[kWinMaxCols];
+  __shared__ uint32_t s_nl;
+  __shared__ __align__(8) uint64_t s_bar_band;
+  const uint32_t t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31;
+  const uint32_t n = hi > lo ? hi - lo : 0u;
+  const uint32_t wpr = a.wpr;
+  // the band: whole frame rows (bit x of row y is bit y * W + x of the
+  // frame), 64 rows past the lowest box origin, so every row of every box is
+  // in it; rows past the frame's last are zero
+  const uint32_t H = a.n_words / wpr;
+  const uint32_t w_lo = y0 * wpr, w_hi = min(y0 + nr, H) * wpr, w_end = (y0 + nr) * wpr;
+  const bool bulk = (reinterpret_cast<uintptr_t>(a.x) & 15u) == 0u && (a.n_words & 3u) == 0u;
+  const uint32_t base = bulk ? (w_lo & ~3u) : w_lo;
+  const uint32_t copy_hi = bulk ? ((w_hi + 3u) & ~3u) : w_hi;  // <= n_words
+  const uint32_t band_words = (max(copy_hi, w_end) - base + 4u + 3u) & ~3u;
+  uint32_t* band = dyn_smem;
+  uint32_t* scr = dyn_smem + band_words;
+  const uint32_t c0 = lo + (uint32_t)warp;  // this warp's columns: c0, c0 + 4, ...
+
+  if (t == 0) {
+    mbar_init1(&s_bar_band);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_nl = 0u;
+  }
+  for (uint32_t i = t; i < n; i += kStepThreads) s_lmap[i] = 0u;
+  __syncthreads();
+  // the band (one bulk copy; it reads frames other work wrote with ordinary
+  // stores, hence the proxy fence) and the box origins
+  if (t == 0 && bulk && n) {
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    mbar_expect(&s_bar_band, (copy_hi - base) * 4u);
+    bulk_g2s(band, a.x + base, (copy_hi - base) * 4u, &s_bar_band);
+  }
+  for (uint32_t w = copy_hi - base + t; w < band_words; w += kStepThreads) band[w] = 0u;
+  if (!bulk)
+    for (uint32_t w = w_lo + t; w < w_hi; w += kStepThreads)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(band + (w - base))),
+                   "l"(a.x + w)
+                   : "memory");
+  for (uint32_t i = t; i < n; i += kStepThreads)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(s_org + i)),
+                 "l"(a.worg + lo + i)
+                 : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  uint4 bm[kWinCols];
+  auto load_group = [&](uint32_t c, uint4(&b)[kWinCols]) {
+#pragma unroll
+    for (int j = 0; j < kWinCols; ++j) {
+      const uint32_t cj = c + j * kStepWarps;
+      b[j] = cj < hi ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)cj * kWinWords) + lane)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  // ---- learning of the previous frame's winners ----------------------------
+  if (!a.mask_prev) {
+    load_group(c0, bm);  // in flight during the band copy
+  } else {
+    for (uint32_t i = t; i < n; i += kStepThreads) {
+      const uint32_t c = lo + i;
+      if ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u) {
+        const uint32_t j = atomicAdd(&s_nl, 1u);
+        s_lcol[j] = c;
+        s_lmap[i] = j < kWinLearn ? (uint8_t)(j + 1u) : (uint8_t)255u;
+      }
+    }
+    __syncthreads();
+    const uint32_t nl = s_nl;
+    // rounds of kWinLearn learners through the scratch, the first round last
+    // so that its bitmaps remain there for the count
+    const uint32_t rounds = (nl + kWinLearn - 1u) / kWinLearn;
+    for (uint32_t rr = rounds; rr-- > 0u;) {
+      const uint32_t j0 = rr * kWinLearn, m = min(kWinLearn, nl - j0);
+      for (uint32_t i = t; i < m * kWinWords; i += kStepThreads) scr[i] = 0u;
+      __syncthreads();
+      const uint32_t total = m * a.S;
+      for (uint32_t e0 = 0; e0 < total; e0 += kStepThreads * kWinLearnUnroll) {
+        uint32_t id[kWinLearnUnroll], at[kWinLearnUnroll], bits = 0u;
+        float p[kWinLearnUnroll];
+#pragma unroll
+        for (int k = 0; k < kWinLearnUnroll; ++k) {
+          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
+          const uint32_t j = e / a.S, s = e - j * a.S;
+          // C * S < 2^31 (configuration limit): a 32-bit element index
+          at[k] = e < total ? s_lcol[j0 + j] * a.S + s : 0u;
+          id[k] = e < total ? __ldg(a.idx + at[k]) : 0u;
+          p[k] = e < total ? __ldcg(a.perm + at[k]) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kWinLearnUnroll; ++k) {
+          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
+          bits |= (e < total ? input_bit(a.x_prev, id[k]) : 0u) << k;
+        }
+#pragma unroll
+        for (int k = 0; k < kWinLearnUnroll; ++k) {
+          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
+          if (e < total) {
+            const uint32_t j = e / a.S;
+            const float q = learn_one(p[k], (bits >> k) & 1u, a.inc, a.dec);
+            a.perm[at[k]] = q;
+            if (q >= a.thr) {
+              const uint32_t org = __ldg(a.worg + s_lcol[j0 + j]);
+              const uint32_t y = id[k] / a.win_w, x = id[k] - y * a.win_w;
+              const uint32_t jx = x - (org & 0xffffu);
+              atomicOr(scr + j * kWinWords + 2u * (y - (org >> 16)) + (jx >> 5), 1u << (jx & 31u));
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // the new bitmaps to global memory, in the lane layout of the form
+      for (uint32_t q = t; q < m * 32u; q += kStepThreads) {
+        const uint32_t j = q >> 5, l = q & 31u;
+        const uint32_t* b = scr + j * kWinWords;
+        reinterpret_cast<uint4*>(a.wbits + (uint64_t)s_lcol[j0 + j] * kWinWords)[l] =
+            make_uint4(b[2 * l], b[2 * l + 1], b[2 * l + 64], b[2 * l + 65]);
+      }
+      if (rr != 0u) __syncthreads();  // the scratch is reused by the next round
+    }
+    load_group(c0, bm);
+  }
+
+  // ---- band and origins in place ---------------------------------------------
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  bool ok = true;
+  if (bulk && n) ok = stage_wait(&s_bar_band, 0u);
+  if (!ok) {
+    if (t == 0 && err) atomicExch(err, 1u);
+    stage_wait(&s_bar_band, 0u);  // the copy, if still in flight (bounded)
+  }
+  __syncthreads();
+
+  // ---- the count: this warp's columns, kWinCols at a time --------------------
+  for (uint32_t c = c0; c < hi; c += kWinCols * kStepWarps) {
+#if SP_WIN_PIPE
+    uint4 nx[kWinCols];
+    load_group(c + kWinCols * kStepWarps, nx);
+#endif
+    uint32_t cnt[kWinCols];
+#pragma unroll
+    for (int j = 0; j < kWinCols; ++j) {
+      const uint32_t cj = c + j * kStepWarps;
+      const uint32_t li = cj < hi ? s_lmap[cj - lo] : 0u;
+      uint4 b = bm[j];
+      if (li != 0u) {  // a learner: its bitmap as rewritten above
+        if (li != 255u) {
+          const uint32_t* s = scr + (li - 1u) * kWinWords;
+          b = make_uint4(s[2 * lane], s[2 * lane + 1], s[2 * lane + 64], s[2 * lane + 65]);
+        } else {
+          b = __ldcg(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)cj * kWinWords) + lane);
+        }
+      }
+      cnt[j] = (ok && cj < hi) ? window_count(band, b, s_org[cj - lo], base, wpr, lane) : 0u;
+    }
+    // lane j publishes the group's column j
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int j = 0; j < kWinCols; ++j) {
+      const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
+      mine = lane == j ? r : mine;
+    }
+    if (lane < kWinCols && c + (uint32_t)lane * kStepWarps < hi)
+      publish_overlap(a, c + (uint32_t)lane * kStepWarps, mine);
+#if SP_WIN_PIPE
+#pragma unroll
+    for (int j = 0; j < kWinCols; ++j) bm[j] = nx[j];
+#else
+    load_group(c + kWinCols * kStepWarps, bm);
+#endif
+  }
+  __syncthreads();  // the band becomes the last CTA's working memory
+  if (t == 0) mbar_inval(&s_bar_band);
+}
+
 // One frame of one SP, run by nb CTAs of which this is number bid.  With
 // STAGE, a CTA whose columns' state fits in stage_cap bytes of dynamic
 // shared memory stages it there by bulk copy first.
@@ -443,80 +623,13 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     c_end = a.C;
     c_step = nb * kStepWarps;
   }
-  auto publish = [&](uint32_t c, uint32_t raw) {
-    // a histogram is kept only when every boost is exactly 1, and then the
-    // product is the count itself: no load stalls the warp here
-    const float v = dev::boosted(raw, a.min_overlap, a.hist ? 1.0f : __ldg(a.boost + c));
-    a.ov[c] = v;
-    if (a.ov_copy) a.ov_copy[c] = v;
-    // unit boosts: the overlap is the count, histogrammed for the select
-    if (a.hist && raw >= a.min_overlap && raw != 0u) atomicAdd(a.hist + raw, 1u);
-  };
+  auto publish = [&](uint32_t c, uint32_t raw) { publish_overlap(a, c, raw); };
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
   if (STAGE && SP_CONTIG_COLUMNS && a.worg) {
-    // window form: the frame rows the CTA's boxes cover are copied to shared
-    // memory first (cp.async, overlapping the first group's bitmap loads);
-    // then kWinCols columns per warp in flight, each counted against them
-    const uint32_t y0 = __ldg(a.wband + 2u * bid), nr = __ldg(a.wband + 2u * bid + 1u);
-    const uint32_t ps = a.wps;
-    uint32_t* band = dyn_smem;
-    uint32_t* scr = dyn_smem + ((nr * ps + 2u + 3u) & ~3u) + (uint32_t)warp * kWinWords;
-    for (uint32_t r = (uint32_t)warp; r < nr; r += kStepWarps) {
-      const uint32_t* src = a.x + (uint64_t)(y0 + r) * a.wpr;
-      for (uint32_t w = (uint32_t)lane; w < a.wpr; w += 32)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(band + r * ps + w)),
-                     "l"(src + w)
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    if (a.mask_prev) {
-      // the previous frame's winners among the CTA's columns learn first
-      // (rare), dealt round-robin to its warps, so the counting loop below
-      // carries no learning path; the CTA barrier after the band copy orders
-      // each rewritten bitmap before any warp loads it
-      const uint32_t lo = c_first - (SP_CONTIG_COLUMNS ? (uint32_t)warp : 0u);
-      uint32_t q = 0;
-      for (uint32_t base = lo; base < c_end; base += 32u) {
-        const uint32_t c = base + (uint32_t)lane;
-        uint32_t m = __ballot_sync(kFull, c < c_end && learning(c));
-        for (; m; m &= m - 1u, ++q) {
-          if ((q % kStepWarps) != (uint32_t)warp) continue;
-          const uint32_t cl = base + (uint32_t)(__ffs(m) - 1);
-          window_learn(a.perm, a.idx, a.wbits, scr, a.x_prev, cl, a.S, a.win_w, __ldg(a.worg + cl),
-                       a.thr, a.inc, a.dec);
-        }
-      }
-    }
-    uint4 bm[kWinCols];
-    uint32_t org[kWinCols];
-    auto load_group = [&](uint32_t c0) {
-#pragma unroll
-      for (int j = 0; j < kWinCols; ++j) {
-        const uint32_t c = c0 + j * c_step;
-        const bool ok = c < c_end;
-        bm[j] = ok ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)c * kWinWords) + lane)
-                   : make_uint4(0u, 0u, 0u, 0u);
-        org[j] = ok ? __ldg(a.worg + c) : 0u;
-      }
-    };
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
-    load_group(c_first);
-    for (uint32_t c0 = c_first; c0 < c_end; c0 += kWinCols * c_step) {
-      if (c0 != c_first) load_group(c0);
-      uint32_t cnt[kWinCols];
-#pragma unroll
-      for (int j = 0; j < kWinCols; ++j) cnt[j] = window_count(band, bm[j], org[j], y0, ps, lane);
-#pragma unroll
-      for (int j = 0; j < kWinCols; ++j) {
-        const uint32_t c = c0 + j * c_step;
-        const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
-        if (c < c_end && lane == 0) publish(c, r);
-      }
-    }
-    __syncthreads();  // the band becomes the last CTA's working memory
+    window_item<STREAM>(a, min(a.C, c_first - (uint32_t)warp), c_end, __ldg(a.wband + 2u * bid),
+                        __ldg(a.wband + 2u * bid + 1u), dyn_smem, err);
   } else if (STAGE && a.cidx) {
     // compact form: kCompactCols columns per warp in flight; the input words
     // the CTA's pools index are first copied to shared memory when they fit
@@ -664,6 +777,10 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
       for (uint32_t k = i; k < n_mine; ++k)
         if (lane == 0) publish(c_first + k * c_step, 0u);
     }
+    __syncwarp();
+    if (lane == 0)
+      for (uint32_t k = 0; k < kRing; ++k)
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(mb + k)) : "memory");
     __syncthreads();  // the rings become the last CTA's working memory
   } else {
     uint32_t xlo = 0u, xhi = 0u;
@@ -791,7 +908,6 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.wbits = d.wbits;
   a.wband = d.wband;
   a.wpr = d.wpr;
-  a.wps = d.wps;
   a.win_w = d.win_w;
   if (!ba.tick) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   a.C = d.C;
@@ -923,7 +1039,6 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
     a.wbits = d.wbits;
     a.wband = d.wband;
     a.wpr = d.wpr;
-    a.wps = d.wps;
     a.win_w = d.win_w;
     a.C = d.C;
     a.S = d.S;
@@ -1064,7 +1179,8 @@ cudaError_t launch_window(const uint32_t* idx, const float* perm, uint32_t C, ui
   return cudaGetLastError();
 }
 
-// Thread b: the frame rows block b of `per` consecutive columns reads.
+// Thread b: the frame rows block b of `per` consecutive columns reads: from
+// its lowest box origin to 64 rows past its highest.
 __global__ void __launch_bounds__(128) sp_window_band_kernel(const uint32_t* worg, uint32_t C,
                                                              uint32_t H, uint32_t per,
                                                              uint32_t n_ctas, uint32_t* out) {
@@ -1075,7 +1191,7 @@ __global__ void __launch_bounds__(128) sp_window_band_kernel(const uint32_t* wor
   for (uint32_t c = c0; c < c1; ++c) {
     const uint32_t oy = worg[c] >> 16;
     y0 = min(y0, oy);
-    y1 = max(y1, min(H - 1u, oy + 63u));
+    y1 = max(y1, oy + 63u);  // rows past the frame are staged as zeros
   }
   out[2u * b] = c0 < c1 ? y0 : 0u;
   out[2u * b + 1u] = c0 < c1 ? y1 - y0 + 1u : 0u;
@@ -1089,8 +1205,10 @@ cudaError_t launch_window_bands(const uint32_t* worg, uint32_t C, uint32_t H, ui
   return cudaGetLastError();
 }
 
-uint32_t window_smem_bytes(uint32_t rows, uint32_t wps) {
-  return (((rows * wps + 2u + 3u) & ~3u) + kStepWarps * kWinWords) * 4u;
+uint32_t window_smem_bytes(uint32_t rows, uint32_t wpr) {
+  // band (rounded out to 16-byte ends, plus slack for the last row's third
+  // word) and the learning scratch
+  return (((rows * wpr + 12u + 3u) & ~3u) + kWinLearn * kWinWords) * 4u;
 }
 
 // Block b of `per` consecutive columns: lowest and one past the highest input
