@@ -139,13 +139,33 @@ def compact_form(case):
     return int((case.idx.max(axis=1) - case.idx.min(axis=1)).max()) <= 0xFFFF
 
 
-def form_of(case):
-    return "compact" if compact_form(case) else "full"
+FORM_TEXT = {
+    "window": "window: per column a 64x64 bitmap of connected synapses + box origin, counted "
+              "against the CTA's frame rows in shared memory; fp32 permanences touched only by "
+              "learning columns",
+    "compact": "compact: 16-bit pool offsets + connected bits, fp32 permanences touched only by "
+               "learning columns",
+    "full": "full: 32-bit pools + fp32 permanences",
+}
 
 
-def form_bytes_per_frame(case, learn=True):
-    """Algorithmic bytes of one SP frame in the form the batch runs it on."""
-    if form_of(case) == "compact":
+def window_bytes_per_frame(case, learn=True):
+    """Bytes one SP frame moves on the window form: per column a 512-byte
+    bitmap of connected synapses and a box origin, the frame, the overlaps,
+    the winner list and, when learning, the winners' pool indices read,
+    permanences read and written, and bitmaps rewritten."""
+    b = case.C * 512 + case.C * 4 + case.n_words * 4 + case.C * 4 + case.k * 4
+    if learn:
+        b += case.k * (case.S * 4 * 3 + 512)
+    return b
+
+
+def form_bytes_per_frame(case, form, learn=True):
+    """Algorithmic bytes of one SP frame in the form the batch runs it on
+    (a name of FORM_NAMES, as sp_batch_forms reports it)."""
+    if form == "window":
+        return window_bytes_per_frame(case, learn)
+    if form == "compact":
         return compact_bytes_per_frame(case, learn)
     return algorithmic_bytes_per_frame(case, learn)
 
@@ -325,12 +345,14 @@ def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
     s1.record(stream)
     torch.cuda.synchronize()
     ms = s0.elapsed_time(s1) / (steps * frames)
+    forms_b = spg.sp_batch_forms(b)
     spg.sp_batch_destroy(b)
     for h in hs:
         spg.sp_destroy(h)
     upd = sum(c.C for c in cases)
     peak, kind = read_peaks()
-    moved = sum(form_bytes_per_frame(c) for c in cases)
+    forms = [spg.FORM_NAMES[int(f)] for f in forms_b]
+    moved = sum(form_bytes_per_frame(c, f) for c, f in zip(cases, forms))
     gbs = moved / (ms / 1000.0) / 1e9
     return {"workload": f"{members} uneven SPs (C 128..4096, S 16..256, inputs 256..16384 bits), "
                         f"learning on, {frames} frames per persistent launch, autotuned",
@@ -340,8 +362,7 @@ def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
             "roofline": {"bound": "hbm", "kernel": "sp_batch_run_kernel", "achieved": gbs,
                          "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
                          "form_bytes_per_batch_frame": moved,
-                         "forms": {f: sum(1 for c in cases if form_of(c) == f)
-                                   for f in sorted({form_of(c) for c in cases})}}}
+                         "forms": {f: forms.count(f) for f in sorted(set(forms))}}}
 
 
 def run_reference(args):
@@ -585,6 +606,7 @@ def main():
     if not args.no_autotune:  # set-up, outside the timed region
         cols_per_warp = spg.sp_batch_autotune(b, d_batch, 8, fw)
         info = spg.sp_batch_get_info(b)
+    forms = [spg.FORM_NAMES[int(f)] for f in spg.sp_batch_forms(b)]
 
     def step(t):
         r = t % FRAME_POOL
@@ -696,8 +718,7 @@ def main():
 
     peak, peak_kind = read_peaks()
     canonical = sum(algorithmic_bytes_per_frame(c) for c in cases)
-    compact = all(compact_form(c) for c in cases)
-    moved = sum(form_bytes_per_frame(c) for c in cases)
+    moved = sum(form_bytes_per_frame(c, f) for c, f in zip(cases, forms))
     # the algorithmic bytes of the form the kernel runs on, per step, over
     # the average time of a step
     achieved = moved / (ms / 1000.0) / 1e9
@@ -742,9 +763,8 @@ def main():
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_step": moved,
-                         "form": ("compact: 16-bit pool offsets + connected bits, fp32 "
-                                  "permanences touched only by learning columns") if compact
-                                 else "full: 32-bit pools + fp32 permanences",
+                         "form": FORM_TEXT[forms[0]] if len(set(forms)) == 1 else
+                                 {f: forms.count(f) for f in sorted(set(forms))},
                          "traffic_over_algorithmic": (traffic / moved) if traffic else None,
                          "canonical_bytes_per_step": canonical,
                          "canonical_equiv_frac": canonical / (ms / 1000.0) / 1e9 / peak,

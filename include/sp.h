@@ -337,6 +337,20 @@ SP_API sp_status sp_batch_compute_overlaps_device(sp_batch* b, const uint32_t* d
                                                   uint64_t mask_stride_words, float* d_overlaps,
                                                   uint64_t ov_stride, void* stream);
 
+/* The form each member's state takes in batch launches (one entry per
+ * member, in member order):
+ *   SP_FORM_FULL     the SP's own pools and permanences, 8 bytes a synapse;
+ *   SP_FORM_COMPACT  16-bit pool offsets and one connected bit a synapse
+ *                    (S a multiple of 32 up to 256, pools spanning at most
+ *                    65536 inputs);
+ *   SP_FORM_WINDOW   per column the origin of a 64 x 64 box of the frame
+ *                    holding its pool and a 512-byte bitmap of its connected
+ *                    synapses there (frames 32k pixels wide, large pools).
+ * The permanences stay authoritative in every form; learning rewrites the
+ * derived form of the columns it changes. */
+enum { SP_FORM_FULL = 0, SP_FORM_COMPACT = 1, SP_FORM_WINDOW = 2 };
+SP_API sp_status sp_batch_forms(const sp_batch* b, uint32_t* forms);
+
 /* The same from host memory: batch frames copied in (pinned memory gives
  * overlapped copies), mask records copied back to h_masks (NULL = not
  * returned).  Synchronous: returns when the masks are in host memory. */

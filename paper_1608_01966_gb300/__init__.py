@@ -10,7 +10,8 @@ from ._binding import (  # noqa: F401
     sp_active_columns, sp_batch_autotune, sp_batch_compute, sp_batch_compute_device,
     sp_batch_compute_overlaps_device, sp_batch_create, sp_batch_destroy, sp_batch_get_info,
     sp_batch_infer_device, sp_batch_infer_overlaps_device, sp_batch_offsets,
-    sp_batch_overlap_offsets, sp_batch_set_device_wait_ns, sp_batch_sync,
+    sp_batch_overlap_offsets, sp_batch_set_device_wait_ns, sp_batch_sync, sp_batch_forms,
+    SP_FORM_FULL, SP_FORM_COMPACT, SP_FORM_WINDOW, FORM_NAMES,
     sp_compute, sp_compute_device, sp_compute_frames, sp_compute_frames_device,
     sp_compute_frames_overlaps_device, sp_config_init, sp_create, sp_create_from_state,
     sp_destroy, sp_get_boost, sp_get_duty_cycles, sp_get_info, sp_get_overlaps,

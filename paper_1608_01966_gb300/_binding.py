@@ -140,6 +140,7 @@ def lib():
                                               ct.c_uint64, vp]
         L.sp_batch_compute.argtypes = [vp, _u32p, ct.c_uint32, ct.c_uint64, ct.c_int, _u32p,
                                        ct.c_uint64]
+        L.sp_batch_forms.argtypes = [vp, _u32p]
         L.sp_batch_overlap_offsets.argtypes = [vp, ct.POINTER(ct.c_uint64),
                                                ct.POINTER(ct.c_uint64)]
         L.sp_batch_compute_overlaps_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64,
@@ -393,6 +394,18 @@ def sp_batch_compute_device(b, d_frames, n_frames, stride_words, learn, d_masks=
     _check(lib().sp_batch_compute_device(b, _addr(d_frames), n_frames, stride_words,
                                          1 if learn else 0, _addr(d_masks), mask_stride_words,
                                          _stream(stream)), "sp_batch_compute_device")
+
+
+SP_FORM_FULL, SP_FORM_COMPACT, SP_FORM_WINDOW = 0, 1, 2
+FORM_NAMES = {SP_FORM_FULL: "full", SP_FORM_COMPACT: "compact", SP_FORM_WINDOW: "window"}
+
+
+def sp_batch_forms(b):
+    """Per-member form of the batch state (SP_FORM_*)."""
+    n = sp_batch_get_info(b)["members"]
+    out = np.zeros(n, np.uint32)
+    _check(lib().sp_batch_forms(b, out.ctypes.data_as(_u32p)), "sp_batch_forms")
+    return out
 
 
 def sp_batch_overlap_offsets(b):

@@ -1628,6 +1628,15 @@ SP_API sp_status sp_batch_offsets(const sp_batch* b, uint64_t* frame_off, uint64
   return SP_OK;
 }
 
+SP_API sp_status sp_batch_forms(const sp_batch* b, uint32_t* forms) {
+  if (!b || !forms) return fail(SP_EINVAL, "NULL argument");
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    const sp::BatchDesc& d = b->h_desc[i];
+    forms[i] = d.worg ? SP_FORM_WINDOW : (d.cidx ? SP_FORM_COMPACT : SP_FORM_FULL);
+  }
+  return SP_OK;
+}
+
 SP_API sp_status sp_batch_overlap_offsets(const sp_batch* b, uint64_t* ov_off, uint64_t* ov_words) {
   if (!b) return fail(SP_EINVAL, "NULL batch");
   for (size_t i = 0; i < b->members.size(); ++i)

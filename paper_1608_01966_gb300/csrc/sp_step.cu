@@ -378,7 +378,10 @@ constexpr int kWinCols = SP_WINDOW_COLS;  // columns per warp in flight
 constexpr uint32_t kWinLearn = 8;         // learners kept in shared memory
 constexpr uint32_t kWinWords = 128;       // bitmap words per column
 constexpr uint32_t kWinMaxCols = 256;     // columns of one CTA (4 warps x 64)
-constexpr int kWinLearnUnroll = 4;
+#ifndef SP_WIN_LEARN_UNROLL
+#define SP_WIN_LEARN_UNROLL 4
+#endif
+constexpr int kWinLearnUnroll = SP_WIN_LEARN_UNROLL;  // synapses per thread and pass
 
 __device__ __forceinline__ uint32_t window_row(const uint32_t* p, uint32_t sh, uint32_t lo,
                                                uint32_t hi) {
@@ -386,15 +389,14 @@ __device__ __forceinline__ uint32_t window_row(const uint32_t* p, uint32_t sh, u
   return __popc(__funnelshift_r(a0, a1, sh) & lo) + __popc(__funnelshift_r(a1, a2, sh) & hi);
 }
 
-// This lane's share of the raw overlap of a column with bitmap rows bm and
-// box origin org, against frame words staged in `band` (band[i] = frame word
-// base + i; wpr words per frame row).
+// This lane's share of the raw overlap of a column with bitmap rows bm,
+// against the staged band: `at` = (o << 5) | (ox & 31) with o the band word
+// holding the box's top-left pixel; lane_off = lane * wpr, row32 = 32 * wpr.
 __device__ __forceinline__ uint32_t window_count(const uint32_t* band, const uint4& bm,
-                                                 uint32_t org, uint32_t base, uint32_t wpr,
-                                                 int lane) {
-  const uint32_t ox = org & 0xffffu, oy = org >> 16;
-  const uint32_t* p = band + ((oy + (uint32_t)lane) * wpr + (ox >> 5) - base);
-  return window_row(p, ox & 31u, bm.x, bm.y) + window_row(p + 32u * wpr, ox & 31u, bm.z, bm.w);
+                                                 uint32_t at, uint32_t lane_off,
+                                                 uint32_t row32) {
+  const uint32_t* p = band + (at >> 5) + lane_off;
+  return window_row(p, at & 31u, bm.x, bm.y) + window_row(p + row32, at & 31u, bm.z, bm.w);
 }
 
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
@@ -463,11 +465,13 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(band + (w - base))),
                    "l"(a.x + w)
                    : "memory");
-  for (uint32_t i = t; i < n; i += kStepThreads)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(s_org + i)),
-                 "l"(a.worg + lo + i)
-                 : "memory");
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+  // each column's box as a band position: (word of its top-left pixel
+  // relative to the band) << 5 | its bit in that word
+  for (uint32_t i = t; i < n; i += kStepThreads) {
+    const uint32_t org = __ldg(a.worg + lo + i), ox = org & 0xffffu;
+    s_org[i] = (((org >> 16) * wpr + (ox >> 5) - base) << 5) | (ox & 31u);
+  }
   uint4 bm[kWinCols];
   auto load_group = [&](uint32_t c, uint4(&b)[kWinCols]) {
 #pragma unroll
@@ -499,35 +503,49 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
       for (uint32_t i = t; i < m * kWinWords; i += kStepThreads) scr[i] = 0u;
       __syncthreads();
       const uint32_t total = m * a.S;
+      // element e = j * S + s: synapse s of learner j0 + j; a thread's
+      // elements advance by kStepThreads, so (j, s) is stepped, not divided
+      uint32_t ej = t / a.S, es = t - ej * a.S;
+      const uint32_t dj = kStepThreads / a.S, ds = kStepThreads - dj * a.S;
+      auto step = [&]() {
+        ej += dj;
+        es += ds;
+        if (es >= a.S) {
+          es -= a.S;
+          ++ej;
+        }
+      };
+      const float inv_w = 1.0f / (float)a.win_w;
       for (uint32_t e0 = 0; e0 < total; e0 += kStepThreads * kWinLearnUnroll) {
-        uint32_t id[kWinLearnUnroll], at[kWinLearnUnroll], bits = 0u;
+        uint32_t id[kWinLearnUnroll], at[kWinLearnUnroll], jj[kWinLearnUnroll], bits = 0u;
         float p[kWinLearnUnroll];
 #pragma unroll
         for (int k = 0; k < kWinLearnUnroll; ++k) {
-          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
-          const uint32_t j = e / a.S, s = e - j * a.S;
+          const bool v = ej < m;
           // C * S < 2^31 (configuration limit): a 32-bit element index
-          at[k] = e < total ? s_lcol[j0 + j] * a.S + s : 0u;
-          id[k] = e < total ? __ldg(a.idx + at[k]) : 0u;
-          p[k] = e < total ? __ldcg(a.perm + at[k]) : 0.0f;
+          jj[k] = ej;
+          at[k] = v ? s_lcol[j0 + ej] * a.S + es : 0u;
+          id[k] = v ? __ldg(a.idx + at[k]) : 0u;
+          p[k] = v ? __ldcg(a.perm + at[k]) : 0.0f;
+          step();
         }
 #pragma unroll
-        for (int k = 0; k < kWinLearnUnroll; ++k) {
-          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
-          bits |= (e < total ? input_bit(a.x_prev, id[k]) : 0u) << k;
-        }
+        for (int k = 0; k < kWinLearnUnroll; ++k)
+          bits |= (jj[k] < m ? input_bit(a.x_prev, id[k]) : 0u) << k;
 #pragma unroll
         for (int k = 0; k < kWinLearnUnroll; ++k) {
-          const uint32_t e = e0 + t + kStepThreads * (uint32_t)k;
-          if (e < total) {
-            const uint32_t j = e / a.S;
+          if (jj[k] < m) {
             const float q = learn_one(p[k], (bits >> k) & 1u, a.inc, a.dec);
             a.perm[at[k]] = q;
             if (q >= a.thr) {
-              const uint32_t org = __ldg(a.worg + s_lcol[j0 + j]);
-              const uint32_t y = id[k] / a.win_w, x = id[k] - y * a.win_w;
-              const uint32_t jx = x - (org & 0xffffu);
-              atomicOr(scr + j * kWinWords + 2u * (y - (org >> 16)) + (jx >> 5), 1u << (jx & 31u));
+              const uint32_t org = __ldg(a.worg + s_lcol[j0 + jj[k]]);
+              // the pixel's row inside its box: (id - oy * W) / W < 64,
+              // from a float estimate corrected to the exact quotient
+              const uint32_t d = id[k] - (org >> 16) * a.win_w;
+              uint32_t r = __float2uint_rz(__uint2float_rz(d) * inv_w);
+              r = r * a.win_w > d ? r - 1u : ((r + 1u) * a.win_w <= d ? r + 1u : r);
+              const uint32_t jx = d - r * a.win_w - (org & 0xffffu);
+              atomicOr(scr + jj[k] * kWinWords + 2u * r + (jx >> 5), 1u << (jx & 31u));
             }
           }
         }
@@ -556,6 +574,8 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
   __syncthreads();
 
   // ---- the count: this warp's columns, kWinCols at a time --------------------
+  const uint32_t lane_off = (uint32_t)lane * wpr, row32 = 32u * wpr;
+  const bool learners = a.mask_prev && s_nl != 0u;  // s_nl is stable after the barrier
   for (uint32_t c = c0; c < hi; c += kWinCols * kStepWarps) {
 #if SP_WIN_PIPE
     uint4 nx[kWinCols];
@@ -565,7 +585,7 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
 #pragma unroll
     for (int j = 0; j < kWinCols; ++j) {
       const uint32_t cj = c + j * kStepWarps;
-      const uint32_t li = cj < hi ? s_lmap[cj - lo] : 0u;
+      const uint32_t li = (learners && cj < hi) ? s_lmap[cj - lo] : 0u;
       uint4 b = bm[j];
       if (li != 0u) {  // a learner: its bitmap as rewritten above
         if (li != 255u) {
@@ -575,7 +595,7 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
           b = __ldcg(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)cj * kWinWords) + lane);
         }
       }
-      cnt[j] = (ok && cj < hi) ? window_count(band, b, s_org[cj - lo], base, wpr, lane) : 0u;
+      cnt[j] = (ok && cj < hi) ? window_count(band, b, s_org[cj - lo], lane_off, row32) : 0u;
     }
     // lane j publishes the group's column j
     uint32_t mine = 0u;

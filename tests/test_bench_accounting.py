@@ -40,6 +40,18 @@ def test_compact_bytes_of_a_paper_scale_frame(frame_case):
     assert bench.compact_bytes_per_frame(c) == want == 713408
 
 
+def test_window_bytes_of_a_paper_scale_frame(frame_case):
+    c = frame_case
+    # bitmaps 512 KiB, origins 4 KiB, frame 64,800 B, overlaps 4 KiB, list
+    # 160 B; 40 learning columns each read 1 KiB of pool indices, read and
+    # write 1 KiB of permanences and rewrite a 512-byte bitmap
+    want = 524288 + 4096 + 64800 + 4096 + 160 + 40 * (1024 + 2048 + 512)
+    assert bench.window_bytes_per_frame(c) == want == 740800
+    assert bench.form_bytes_per_frame(c, "window") == want
+    assert bench.form_bytes_per_frame(c, "compact") == 713408
+    assert bench.form_bytes_per_frame(c, "full") == 2207168
+
+
 def test_compact_form_needs_s_multiple_of_32_and_a_narrow_span():
     idx = synth.pool_uniform(3, 64, 17, 100000)
     ragged = wl.Case("ragged", 100000, 1, 64, 17, idx, np.zeros((64, 17), np.float32),
