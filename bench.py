@@ -129,12 +129,13 @@ def algorithmic_bytes_per_frame(case, learn=True):
 
 
 def compact_form(case):
-    """Whether the batch runs this SP on its compact form: 16-bit pool offsets
-    from a per-column base plus one connected bit per synapse (S a multiple
-    of 32 up to 256, every pool spanning at most 65536 inputs)."""
+    """Whether an SP qualifies for the compact form: 16-bit pool offsets from
+    a per-column base plus one connected bit per synapse (S up to 256, rows
+    padded to a multiple of 32 synapses, every pool spanning at most 65536
+    inputs)."""
     if os.environ.get("SP_BATCH_COMPACT", "1").startswith("0"):
         return False
-    if case.S % 32 or case.S > 256:
+    if case.S > 256:
         return False
     return int((case.idx.max(axis=1) - case.idx.min(axis=1)).max()) <= 0xFFFF
 
@@ -172,13 +173,15 @@ def form_bytes_per_frame(case, form, learn=True):
 
 def compact_bytes_per_frame(case, learn=True):
     """Bytes one SP frame moves on the compact form: offsets (2 B) and
-    connected bits (1/8 B) per synapse, a base per column, the frame, the
-    overlaps, the winner list and, when learning, the winners' permanence rows
-    read and written plus their connected bits rewritten."""
-    b = (case.C * case.S * 2 + case.C * case.S // 8 + case.C * 4 + case.n_words * 4
+    connected bits (1/8 B) per synapse of rows padded to a multiple of 32, a
+    base per column, the frame, the overlaps, the winner list and, when
+    learning, the winners' permanence rows read and written plus their
+    connected bits rewritten."""
+    sp = (case.S + 31) // 32 * 32
+    b = (case.C * sp * 2 + case.C * sp // 8 + case.C * 4 + case.n_words * 4
          + case.C * 4 + case.k * 4)
     if learn:
-        b += case.k * case.S * 8 + case.k * case.S // 8
+        b += case.k * case.S * 8 + case.k * sp // 8
     return b
 
 

@@ -625,15 +625,16 @@ const uint32_t* handle_xspan(sp_handle* h, uint32_t n_ctas) {
 }
 
 // Derive the compact form of the handle's pools and connectivity from its
-// current state (S % 32 == 0, S <= 256, every pool spanning at most 65536
-// inputs); false if the SP does not qualify or the form cannot be had, which
-// leaves batches on the full form.  SP_BATCH_COMPACT=0 turns it off.
+// current state (S <= 256, every pool spanning at most 65536 inputs; rows
+// padded to a multiple of 32 synapses); false if the SP does not qualify or
+// the form cannot be had, which leaves batches on the full form.
+// SP_BATCH_COMPACT=0 turns it off.
 bool handle_compact(sp_handle* h) {
   if (const char* e = std::getenv("SP_BATCH_COMPACT"))
     if (e[0] == '0') return false;
-  if (h->S % 32u != 0u || h->S > 256u) return false;
+  if (h->S > 256u) return false;
   DeviceGuard g(h->device);
-  const size_t CS = (size_t)h->C * h->S;
+  const size_t CS = (size_t)h->C * ((h->S + 31u) & ~31u);  // rows padded to 32 synapses
   const size_t b_cidx = align256(CS * 2), b_base = align256((size_t)h->C * 4),
                b_conn = align256(CS / 8);
   if (!h->d_compact) {
@@ -711,8 +712,8 @@ bool handle_window(sp_handle* h, uint32_t n_ctas, uint32_t* win_bytes) {
   // other forms stream about as much (large pools), since a small pool is
   // cheaper as offsets (2 bytes and a bit per synapse) or indices and
   // permanences (8 bytes per synapse)
-  const bool compact_shape = h->S % 32u == 0u && h->S <= 256u;
-  const double other = compact_shape ? 2.125 * h->S + 4.0 : 8.0 * h->S;
+  const bool compact_shape = h->S <= 256u;
+  const double other = compact_shape ? 2.125 * ((h->S + 31u) & ~31u) + 4.0 : 8.0 * h->S;
   if (516.0 > 1.1 * other) return false;
   const uint32_t W = h->cfg.input_w;
   if (W % 32u != 0u || h->S > 4096u) {

@@ -146,10 +146,12 @@ cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_
 // One persistent launch over r.n_frames batch frames (grid sized to the
 // resident CTAs); r.work and r.abort must be 0.
 cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream);
-// Compact form of an SP's pools and connectivity (S % 32 == 0, S <= 256):
-// cbase[c] = min_s idx[c][s], cidx[c][s] = idx[c][s] - cbase[c],
-// conn[c][s / 32] bit s % 32 = perm[c][s] >= thr.  *wide is set to 1 if some
-// column's pool spans more than 65536 inputs (the form is unusable then).
+// Compact form of an SP's pools and connectivity (S <= 256), rows padded to
+// cS = S rounded up to a multiple of 32 synapses and laid out lane-strided
+// (see sp_step.cu): cbase[c] = min_s idx[c][s], 16-bit offsets idx[c][s] -
+// cbase[c], one connected bit (perm[c][s] >= thr) per synapse, padding
+// never connected.  *wide is set to 1 if some column's pool spans more than
+// 65536 inputs (the form is unusable then).
 cudaError_t launch_compact(const uint32_t* idx, const float* perm, uint32_t C, uint32_t S,
                            float thr, uint16_t* cidx, uint32_t* cbase, uint32_t* conn,
                            uint32_t* wide, cudaStream_t stream);

@@ -96,13 +96,11 @@ __device__ __forceinline__ void learn4(float4& p, const uint4& id, const StepArg
 #endif
 constexpr int kCompactCols = SP_COMPACT_COLS;
 
-// Lane l of a column holds synapses l, l + L, ..., l + 7L (L = S / 8 lanes in
-// use): the 8 offsets at positions 8l .. 8l + 7 and connected bits in byte l,
-// so the k-th gather of all lanes reads 32 neighbouring synapses of the
-// sorted pool (SP_COMPACT_STRIDED=0: lane l holds synapses 8l .. 8l + 7).
-#ifndef SP_COMPACT_STRIDED
-#define SP_COMPACT_STRIDED 1
-#endif
+// Rows are padded to cS = S rounded up to a multiple of 32 synapses (the
+// padding: offset 0, never connected).  Lane l of a column holds synapses l,
+// l + L, ..., l + 7L (L = cS / 8 lanes in use): the 8 offsets at positions
+// 8l .. 8l + 7 and connected bits in byte l, so the k-th gather of all lanes
+// reads 32 neighbouring synapses of the sorted pool.
 
 __device__ __forceinline__ uint32_t off16(const uint4& o, int k) {
   const uint32_t w = k < 2 ? o.x : (k < 4 ? o.y : (k < 6 ? o.z : o.w));
@@ -110,7 +108,8 @@ __device__ __forceinline__ uint32_t off16(const uint4& o, int k) {
 }
 
 // Apply the pending learning to column c (the lane's 8 synapses, as laid out
-// above) and return the lane's new byte of connected bits; writes perm and conn.
+// above; rows without padding, S a multiple of 32) and return the lane's new
+// byte of connected bits; writes perm and conn.
 // Rare (winners of the previous frame only), so kept out of line with its
 // own loads to leave the common path's registers alone.
 __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx,
@@ -123,7 +122,6 @@ __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx
   if (act) {
     const uint4 o = reinterpret_cast<const uint4*>(cidx + (uint64_t)c * S)[lane];
     const uint32_t base = cbase[c];
-#if SP_COMPACT_STRIDED
     float* prow = perm + (uint64_t)c * S + lane;
     const uint32_t L = S >> 3;
     float q[8];
@@ -135,24 +133,45 @@ __device__ __noinline__ uint32_t compact_learn(float* perm, const uint16_t* cidx
       nb |= (q[k] >= thr ? 1u : 0u) << k;
       prow[k * L] = q[k];
     }
-#else
-    float4* p4 = reinterpret_cast<float4*>(perm + (uint64_t)c * S) + 2 * lane;
-    float4 q[2] = {p4[0], p4[1]};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      float* f = k < 4 ? &q[0].x + k : &q[1].x + (k - 4);
-      *f = learn_one(*f, input_bit(x_prev, base + off16(o, k)), inc, dec);
-      nb |= (*f >= thr ? 1u : 0u) << k;
-    }
-    p4[0] = q[0];
-    p4[1] = q[1];
-#endif
   }
   uint32_t word = nb << (8u * (lane & 3));
   word |= __shfl_xor_sync(kFull, word, 1);
   word |= __shfl_xor_sync(kFull, word, 2);
   if (act && (lane & 3) == 0) conn[(uint64_t)c * (S >> 5) + (lane >> 2)] = word;
   return nb;
+}
+
+// Pending learning of a member whose compact rows are padded (S not a
+// multiple of 32), for the previous frame's winners among columns [lo, hi):
+// one warp per learner updates the permanences from the full form, then
+// rewrites the column's connected bits (synapse s: byte s % L, bit s / L,
+// L = cS / 8).  Run before the count, which then reads the new bits.
+__device__ void compact_learn_padded(const StepArgs& a, uint32_t lo, uint32_t hi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t cS = (a.S + 31u) & ~31u, L = cS >> 3;
+  uint32_t q = 0;
+  for (uint32_t base = lo; base < hi; base += 32u) {
+    const uint32_t c = base + (uint32_t)lane;
+    uint32_t m = __ballot_sync(kFull, c < hi && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u));
+    for (; m; m &= m - 1u, ++q) {
+      if ((q % kStepWarps) != (uint32_t)warp) continue;
+      const uint32_t cl = base + (uint32_t)(__ffs(m) - 1);
+      const uint64_t row = (uint64_t)cl * a.S;
+      for (uint32_t s = lane; s < a.S; s += 32)
+        a.perm[row + s] = learn_one(a.perm[row + s], input_bit(a.x_prev, __ldg(a.idx + row + s)),
+                                    a.inc, a.dec);
+      __syncwarp();
+      uint8_t* cb8 = reinterpret_cast<uint8_t*>(a.conn + (uint64_t)cl * (cS >> 5));
+      for (uint32_t l = lane; l < L; l += 32) {
+        uint32_t byte = 0;
+        for (uint32_t k = 0; k < 8u; ++k) {
+          const uint32_t s = l + k * L;
+          byte |= (s < a.S && a.perm[row + s] >= a.thr ? 1u : 0u) << k;
+        }
+        cb8[l] = (uint8_t)byte;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ uint32_t compact_count(const uint32_t* x, uint32_t base, const uint4& o,
@@ -274,12 +293,9 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
   }
 }
 
-// Columns of one SP given to CTA bid of nb: a contiguous range when
-// SP_CONTIG_COLUMNS (neighbouring receptive fields share cached input
-// words), else every nb-th group of kStepWarps columns.
-#ifndef SP_CONTIG_COLUMNS
-#define SP_CONTIG_COLUMNS 1
-#endif
+// Columns of one SP given to CTA bid of nb: a contiguous range of
+// ceil(C / nb) columns (neighbouring receptive fields share cached input
+// words, and a window-form CTA's boxes share one band of frame rows).
 
 #ifndef SP_STAGE_RING
 #define SP_STAGE_RING 3
@@ -632,33 +648,32 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     for (uint32_t i = bid * kStepThreads + threadIdx.x; i < a.n_words; i += nb * kStepThreads)
       a.x_save[i] = __ldg(a.x + i);
   }
-  uint32_t c_first, c_end, c_step;
-  if (SP_CONTIG_COLUMNS) {
-    const uint32_t per = (a.C + nb - 1u) / nb;
-    c_first = min(a.C, bid * per) + warp;
-    c_end = min(a.C, (bid + 1u) * per);
-    c_step = kStepWarps;
-  } else {
-    c_first = bid * kStepWarps + warp;
-    c_end = a.C;
-    c_step = nb * kStepWarps;
-  }
+  const uint32_t per = (a.C + nb - 1u) / nb;
+  const uint32_t c_lo = min(a.C, bid * per);
+  const uint32_t c_first = c_lo + warp, c_end = min(a.C, (bid + 1u) * per);
+  const uint32_t c_step = kStepWarps;
   auto publish = [&](uint32_t c, uint32_t raw) { publish_overlap(a, c, raw); };
   auto learning = [&](uint32_t c) {
     return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
-  if (STAGE && SP_CONTIG_COLUMNS && a.worg) {
-    window_item<STREAM>(a, min(a.C, c_first - (uint32_t)warp), c_end, __ldg(a.wband + 2u * bid),
+  if (STAGE && a.worg) {
+    window_item<STREAM>(a, c_lo, c_end, __ldg(a.wband + 2u * bid),
                         __ldg(a.wband + 2u * bid + 1u), dyn_smem, err);
   } else if (STAGE && a.cidx) {
     // compact form: kCompactCols columns per warp in flight; the input words
     // the CTA's pools index are first copied to shared memory when they fit
     // (the copy overlaps the first group's loads), so the bit gathers read
     // shared memory instead of making one L1 lookup per lane
-    const bool act = lane < (int)(a.S >> 3);
-    const uint32_t cw = a.S >> 5;
+    const uint32_t cS = (a.S + 31u) & ~31u;  // rows padded to 32 synapses
+    const bool padded = cS != a.S;
+    if (padded && a.mask_prev) {
+      compact_learn_padded(a, c_lo, c_end);
+      __syncthreads();  // the new bits and permanences before the count reads them
+    }
+    const bool act = lane < (int)(cS >> 3);
+    const uint32_t cw = cS >> 5;
     uint32_t xlo = 0u, xhi = 0u;
-    if (SP_CONTIG_COLUMNS && a.xspan) {
+    if (a.xspan) {
       xlo = __ldg(a.xspan + 2u * bid);
       xhi = __ldg(a.xspan + 2u * bid + 1u);
     }
@@ -680,7 +695,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
         const uint32_t c = c0 + j * c_step;
         const bool ok = c < c_end;
         oo[j] = (ok && act)
-                    ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.cidx + (uint64_t)c * a.S) + lane)
+                    ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.cidx + (uint64_t)c * cS) + lane)
                     : make_uint4(0u, 0u, 0u, 0u);
         cc[j] = (ok && act)
                     ? (ld_state<STREAM>(a.conn + (uint64_t)c * cw + (lane >> 2)) >> (8u * (lane & 3))) & 255u
@@ -693,7 +708,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
 #pragma unroll
       for (int j = 0; j < kCompactCols; ++j) {
         const uint32_t c = c0 + j * c_step;
-        if (c < c_end && learning(c))
+        if (!padded && c < c_end && learning(c))
           cb[j] = compact_learn(a.perm, a.cidx, a.cbase, a.conn, a.x_prev, c, a.S, a.thr, a.inc,
                                 a.dec);
       }
@@ -734,7 +749,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
         run_group(c0, count_g);
       }
     }
-  } else if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.S <= 512u &&
+  } else if (STAGE && VEC == 4 && a.S <= 512u &&
       kStepWarps * stage_ring_bytes(a.S) <= stage_cap) {
     // Each warp streams its columns' pool and permanence rows through a ring
     // of kRing shared-memory slots with bulk copies: the copies of the next
@@ -804,7 +819,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     __syncthreads();  // the rings become the last CTA's working memory
   } else {
     uint32_t xlo = 0u, xhi = 0u;
-    if (STAGE && VEC == 4 && SP_CONTIG_COLUMNS && a.xspan) {
+    if (STAGE && VEC == 4 && a.xspan) {
       xlo = __ldg(a.xspan + 2u * bid);
       xhi = __ldg(a.xspan + 2u * bid + 1u);
     }
@@ -944,7 +959,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   a.gh = d.gh;
   a.radius = d.radius;
   const uint32_t bid = blockIdx.x - cta_first;
-  if ((a.S & 3u) == 0u)
+  if ((a.S & 3u) == 0u || a.cidx)
     step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, ba.stage_cap, ba.err, ba.xspan_cap);
   else
     step_body<1, true>(a, bid, d.n_ctas, dyn_smem);
@@ -1074,7 +1089,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
     a.gh = d.gh;
     a.radius = d.radius;
     const uint32_t bid = k - d.cta_first;
-    if ((a.S & 3u) == 0u)
+    if ((a.S & 3u) == 0u || a.cidx)
       step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, r.stage_cap, r.err, r.xspan_cap,
                                r.done + inst, r.epoch + t + 1u);
     else
@@ -1118,24 +1133,19 @@ __global__ void __launch_bounds__(256) sp_compact_kernel(const uint32_t* idx, co
     if (lane == 0) atomicOr(wide, 1u);
     return;
   }
-#if SP_COMPACT_STRIDED
-  const uint32_t L = S >> 3;  // lanes in use; synapse s sits with lane s % L, slot s / L
-  for (uint32_t s = lane; s < S; s += 32)
-    cidx[(uint64_t)c * S + (s % L) * 8u + s / L] = (uint16_t)(row[s] - lo);
-  uint8_t* cb8 = reinterpret_cast<uint8_t*>(conn + (uint64_t)c * (S >> 5));
+  const uint32_t cS = (S + 31u) & ~31u;
+  const uint32_t L = cS >> 3;  // lanes in use; synapse s sits with lane s % L, slot s / L
+  for (uint32_t s = lane; s < cS; s += 32)
+    cidx[(uint64_t)c * cS + (s % L) * 8u + s / L] = s < S ? (uint16_t)(row[s] - lo) : (uint16_t)0;
+  uint8_t* cb8 = reinterpret_cast<uint8_t*>(conn + (uint64_t)c * (cS >> 5));
   for (uint32_t l = lane; l < L; l += 32) {
     uint32_t byte = 0;
-    for (uint32_t k = 0; k < 8u; ++k)
-      byte |= (perm[(uint64_t)c * S + l + k * L] >= thr ? 1u : 0u) << k;
+    for (uint32_t k = 0; k < 8u; ++k) {
+      const uint32_t s = l + k * L;
+      byte |= (s < S && perm[(uint64_t)c * S + s] >= thr ? 1u : 0u) << k;
+    }
     cb8[l] = (uint8_t)byte;
   }
-#else
-  for (uint32_t s = lane; s < S; s += 32) {
-    cidx[(uint64_t)c * S + s] = (uint16_t)(row[s] - lo);
-    const uint32_t bits = __ballot_sync(kFull, perm[(uint64_t)c * S + s] >= thr);
-    if (lane == 0) conn[(uint64_t)c * (S >> 5) + (s >> 5)] = bits;
-  }
-#endif
   if (lane == 0) cbase[c] = lo;
 }
 

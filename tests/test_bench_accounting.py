@@ -52,11 +52,18 @@ def test_window_bytes_of_a_paper_scale_frame(frame_case):
     assert bench.form_bytes_per_frame(c, "full") == 2207168
 
 
-def test_compact_form_needs_s_multiple_of_32_and_a_narrow_span():
-    idx = synth.pool_uniform(3, 64, 17, 100000)
-    ragged = wl.Case("ragged", 100000, 1, 64, 17, idx, np.zeros((64, 17), np.float32),
-                     np.ones(64, np.float32))
-    assert not bench.compact_form(ragged)  # S = 17
+def test_compact_form_pads_rows_and_needs_a_narrow_span():
+    idx = synth.pool_uniform(3, 64, 17, 60000)
+    ragged = wl.Case("ragged", 60000, 1, 64, 17, idx, np.zeros((64, 17), np.float32),
+                     np.ones(64, np.float32), k=2)
+    assert bench.compact_form(ragged)  # S = 17: rows padded to 32 synapses
+    # 64 columns x 32 padded synapses x (2 + 1/8) B, bases, frame (1875
+    # words), overlaps, list; 2 learners x (17 x 8 B + 32 bits)
+    want = 64 * 32 * 2 + 64 * 32 // 8 + 64 * 4 + 1875 * 4 + 64 * 4 + 2 * 4 + 2 * (17 * 8 + 4)
+    assert bench.compact_bytes_per_frame(ragged) == want
+    big = wl.Case("big", 60000, 1, 8, 257, synth.pool_uniform(5, 8, 257, 60000),
+                  np.zeros((8, 257), np.float32), np.ones(8, np.float32))
+    assert not bench.compact_form(big)  # S > 256
     wide_idx = synth.pool_uniform(4, 64, 32, 200000)
     wide = wl.Case("wide", 200000, 1, 64, 32, wide_idx, np.zeros((64, 32), np.float32),
                    np.ones(64, np.float32))
