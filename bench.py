@@ -69,8 +69,10 @@ def parse():
                     help="one API call (one launch) per step instead of one per run of steps")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default CTA split instead of autotuning it")
-    ap.add_argument("--serve-seconds", type=float, default=8.0,
-                    help="open-loop serving run (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="serving workload run, open loop at 30 fps per stream (0 = skip)")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=3.0,
+                    help="seconds of each load point of the serving sweep (0 = skip the sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -717,7 +719,7 @@ def main():
     if args.serve_seconds > 0 and rank == 0:
         from paper_1608_01966_gb300 import serve_sim
         serve = serve_sim.simulate(streams=32, fps=30.0, seconds=args.serve_seconds,
-                                   saturate_seconds=3.0)
+                                   saturate_seconds=3.0, sweep_seconds=args.serve_sweep_seconds)
 
     peak, peak_kind = read_peaks()
     canonical = sum(algorithmic_bytes_per_frame(c) for c in cases)

@@ -21,7 +21,7 @@ from ._binding import (  # noqa: F401
     sp_server_get_permanences, sp_server_get_stats, sp_server_open_stream, sp_server_poll,
     sp_server_submit, sp_server_submit_many, sp_server_submit_many_device,
     sp_server_submit_many_ptrs,
-    sp_step_noalloc, sp_sync,
+    sp_step_noalloc, sp_sync, sp_loadgen_run,
     SpEncoderConfig, sp_encode_compute, sp_encode_compute_device, sp_encode_device,
     sp_encoder_config_init, sp_encoder_create, sp_encoder_destroy, sp_encoder_get_info,
 )

@@ -66,6 +66,23 @@ class SpServerStats(ct.Structure):
                 ("reserved", ct.c_uint32), ("p50_us", ct.c_double), ("p99_us", ct.c_double)]
 
 
+class SpLoadgenConfig(ct.Structure):
+    _fields_ = [("n_streams", ct.c_uint32), ("stream_ids", ct.POINTER(ct.c_uint32)),
+                ("pools", ct.POINTER(ct.c_void_p)), ("pool_frames", ct.POINTER(ct.c_uint32)),
+                ("pool_stride_words", ct.POINTER(ct.c_uint64)),
+                ("rate_per_stream", ct.c_double), ("seconds", ct.c_double),
+                ("producers", ct.c_uint32), ("learn", ct.c_uint32), ("seed", ct.c_uint64)]
+
+
+class SpLoadgenReport(ct.Structure):
+    _fields_ = [("offered", ct.c_uint64), ("submitted", ct.c_uint64), ("refused", ct.c_uint64),
+                ("completed", ct.c_uint64), ("errors", ct.c_uint64), ("launches", ct.c_uint64),
+                ("seconds", ct.c_double), ("offered_per_s", ct.c_double),
+                ("frames_per_s", ct.c_double), ("p50_us", ct.c_double), ("p90_us", ct.c_double),
+                ("p99_us", ct.c_double), ("p999_us", ct.c_double), ("max_us", ct.c_double),
+                ("frames_per_launch", ct.c_double)]
+
+
 class SpInfo(ct.Structure):
     _fields_ = [
         ("num_columns", ct.c_uint32), ("synapses_per_column", ct.c_uint32),
@@ -172,6 +189,7 @@ def lib():
                                      ct.c_uint32, _u32p, ct.c_uint32]
         L.sp_server_get_permanences.argtypes = [vp, ct.c_uint32, _f32p]
         L.sp_server_get_stats.argtypes = [vp, ct.POINTER(SpServerStats), ct.c_int]
+        L.sp_loadgen_run.argtypes = [vp, ct.POINTER(SpLoadgenConfig), ct.POINTER(SpLoadgenReport)]
         L.sp_encoder_config_init.argtypes = [ct.POINTER(SpEncoderConfig)]
         L.sp_encoder_create.argtypes = [ct.POINTER(SpEncoderConfig), ct.POINTER(vp)]
         L.sp_encoder_destroy.argtypes = [vp]
@@ -611,6 +629,26 @@ def sp_server_get_stats(s, reset=False):
     st = SpServerStats()
     _check(lib().sp_server_get_stats(s, ct.byref(st), 1 if reset else 0), "sp_server_get_stats")
     return {f: getattr(st, f) for f, _ in SpServerStats._fields_}
+
+
+def sp_loadgen_run(srv, stream_ids, pools, rate_per_stream, seconds, producers=4, learn=True,
+                   seed=0):
+    """Drive the server with native producer threads (include/sp_loadgen.h).
+    pools: one C-contiguous uint32 [frames][words] host array per stream
+    (kept alive by the caller for the call).  rate_per_stream 0 = closed
+    loop.  Returns the report as a dict."""
+    n = len(stream_ids)
+    pools = [np.ascontiguousarray(p, dtype=np.uint32) for p in pools]
+    ids = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+    ptrs = (ct.c_void_p * n)(*[p.ctypes.data for p in pools])
+    nf = np.array([p.shape[0] for p in pools], np.uint32)
+    stride = np.array([p.shape[1] for p in pools], np.uint64)
+    cfg = SpLoadgenConfig(n, ids.ctypes.data_as(_u32p), ptrs, nf.ctypes.data_as(_u32p),
+                          stride.ctypes.data_as(ct.POINTER(ct.c_uint64)), float(rate_per_stream),
+                          float(seconds), producers, 1 if learn else 0, seed)
+    rep = SpLoadgenReport()
+    _check(lib().sp_loadgen_run(srv, ct.byref(cfg), ct.byref(rep)), "sp_loadgen_run")
+    return {f: getattr(rep, f) for f, _ in SpLoadgenReport._fields_}
 
 
 def sp_kernel_launch_count():

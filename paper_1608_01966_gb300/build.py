@@ -3,7 +3,8 @@
 - libsp_synth.so  : the seeded input generators (plain C, gcc).
 - libsp_gb300.so  : the CUDA Spatial Pooler library behind include/sp.h
                     (nvcc, sm_103a only, -fmad=false so every fp32 step is
-                    one round-to-nearest op).
+                    one round-to-nearest op) and include/sp_loadgen.h (host
+                    C++, g++).
 
 Objects are compiled in parallel and cached by modification time under
 _build/<arch>/; the shared objects land in _lib/<arch>/.  Both directories are ignored by
@@ -69,6 +70,11 @@ def cuda_sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def host_sources():
+    """Host-only C++ of the library (no device code): built with g++."""
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cpp"))
+
+
 def build_sp(force=False, jobs=None):
     """Compile every .cu under csrc/ for sm_103a and link libsp_gb300.so."""
     os.makedirs(LIB_DIR, exist_ok=True)
@@ -82,6 +88,13 @@ def build_sp(force=False, jobs=None):
         objs.append(obj)
         if force or _newer(obj, [src] + hdrs):
             jobs_list.append([NVCC] + NVCC_FLAGS + extra + ["-c", src, "-o", obj])
+    for src in host_sources():
+        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if force or _newer(obj, [src] + hdrs):
+            jobs_list.append(["g++", "-std=c++17", "-O2", "-fPIC", "-fvisibility=hidden",
+                              "-ffp-contract=off", "-Wall", "-DSP_BUILD_LIBRARY", "-I", INCLUDE,
+                              "-I", CSRC, "-c", src, "-o", obj])
     synth_obj = os.path.join(BUILD_DIR, "synth.c.o")
     objs.append(synth_obj)
     if force or _newer(synth_obj, [SYNTH_SRC, os.path.join(INCLUDE, "sp_synth.h")]):

@@ -4,10 +4,12 @@ S streams (default 32) with Poisson frame arrivals (default mean 30 fps
 each) at round-robin resolutions 320x180, 640x360 and 960x540 (blobbed binary
 frames, cycled from a seeded pool per resolution).  Each stream owns an SP of
 1024 columns x 256 synapses from a 64x64 window, learning on, duty cycles
-tracked.  An open-loop run submits frames at their arrival times and reports
-frames/s and per-frame latency (submit -> result on the host) p50/p99; a
+tracked.  The load comes from the library's native load generator
+(include/sp_loadgen.h: producer threads submit at the arrival times, a
+collector keeps every frame's latency, submit -> result on the host): a
 closed-loop run keeps every stream's queue full to find the saturation
-throughput.
+throughput, a sweep of open-loop loads at fractions of it gives p50/p99 at
+each, and the workload itself runs open loop at its own rate.
 
     python -m paper_1608_01966_gb300.serve_sim --seconds 60
 """
@@ -194,8 +196,29 @@ def run_closed_loop_device(srv, sids, res, pools, seconds):
     return out
 
 
-def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=5.0, seed=0x5EED0005,
-             budget_bytes=8 << 30):
+def _native(srv, sids, res, pools, rate, seconds, producers, seed):
+    """One load-generator run (native producer and collector threads)."""
+    r = spg.sp_loadgen_run(srv, sids, [pools[res[i]] for i in range(len(sids))], rate, seconds,
+                           producers=producers, learn=True, seed=seed)
+    return {"offered_per_s": r["offered_per_s"], "frames_per_s": r["frames_per_s"],
+            "frames": r["completed"], "refused": r["refused"], "errors": r["errors"],
+            "seconds": r["seconds"], "p50_ms": r["p50_us"] / 1000, "p90_ms": r["p90_us"] / 1000,
+            "p99_ms": r["p99_us"] / 1000, "p999_ms": r["p999_us"] / 1000,
+            "max_ms": r["max_us"] / 1000, "frames_per_launch": r["frames_per_launch"]}
+
+
+SWEEP = (0.1, 0.25, 0.5, 0.75, 0.9, 1.0)
+
+
+def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=3.0, sweep_seconds=3.0,
+             seed=0x5EED0005, budget_bytes=8 << 30, producers=4):
+    """The serving workload on the library's server, driven by the native
+    load generator (include/sp_loadgen.h): the closed-loop saturation
+    throughput; a sweep of open-loop Poisson loads at fractions of it
+    (p50/p99 latency at each, and the knee: the highest load whose p99 stays
+    within twice the lightest load's while at least 99 % of the offered frames
+    are served); and the workload itself, every stream at `fps`, for
+    `seconds`."""
     pools = _frame_pools(16, seed)
     words = max(p.shape[1] for p in pools.values())
     srv = spg.sp_server_create(max_streams=streams, queue_depth=4, max_input_words=words,
@@ -204,11 +227,30 @@ def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=5.0, seed=0x5E
         sids, res = open_streams(srv, streams, seed)
         out = {"streams": streams, "fps_per_stream": fps,
                "resolutions": "round-robin 320x180 / 640x360 / 960x540",
-               "open_loop": run_open_loop(srv, sids, res, pools, seconds, fps, seed)}
+               "producer": f"native load generator, {producers} producer threads + collector"}
+        sat = None
         if saturate_seconds > 0:
-            out["closed_loop"] = run_closed_loop(srv, sids, res, pools, saturate_seconds)
-            out["closed_loop_device_frames"] = run_closed_loop_device(srv, sids, res, pools,
-                                                                      saturate_seconds)
+            sat = _native(srv, sids, res, pools, 0.0, saturate_seconds, producers, seed + 1)
+            out["closed_loop"] = sat
+        if sat and sweep_seconds > 0:
+            pts = []
+            for k, frac in enumerate(SWEEP):
+                rate = frac * sat["frames_per_s"] / streams
+                pt = _native(srv, sids, res, pools, rate, sweep_seconds, producers, seed + 2 + k)
+                pt["fraction_of_saturation"] = frac
+                pts.append(pt)
+            out["sweep"] = pts
+            base = pts[0]["p99_ms"]
+            knee = None
+            for pt in pts:
+                if pt["p99_ms"] <= 2.0 * base and pt["frames"] >= 0.99 * pt["offered_per_s"] * sweep_seconds:
+                    knee = pt
+            out["knee"] = None if knee is None else {
+                "fraction_of_saturation": knee["fraction_of_saturation"],
+                "frames_per_s": knee["frames_per_s"], "p99_ms": knee["p99_ms"],
+                "rule": "highest load with p99 <= 2 x the 10 % load's p99 and >= 99 % served"}
+        if seconds > 0:
+            out["open_loop"] = _native(srv, sids, res, pools, fps, seconds, producers, seed)
         st = spg.sp_server_get_stats(srv)
         out["launches"] = st["launches"]
         out["frames_per_launch"] = st["frames_in_launches"] / max(1, st["launches"])
@@ -224,9 +266,10 @@ def main():
     ap.add_argument("--streams", type=int, default=32)
     ap.add_argument("--fps", type=float, default=30.0)
     ap.add_argument("--seconds", type=float, default=60.0)
-    ap.add_argument("--saturate-seconds", type=float, default=5.0)
+    ap.add_argument("--saturate-seconds", type=float, default=3.0)
+    ap.add_argument("--sweep-seconds", type=float, default=3.0)
     a = ap.parse_args()
-    print(json.dumps(simulate(a.streams, a.fps, a.seconds, a.saturate_seconds)))
+    print(json.dumps(simulate(a.streams, a.fps, a.seconds, a.saturate_seconds, a.sweep_seconds)))
 
 
 if __name__ == "__main__":

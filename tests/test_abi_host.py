@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1608_01966_gb300 as spg
@@ -26,12 +27,13 @@ def _exported(lib_path):
 
 @pytest.mark.parametrize("header,macro,which", [
     ("sp.h", "SP_API", "sp"),
+    ("sp_loadgen.h", "SP_API", "sp"),
     ("sp_synth.h", "SYNTH_API", "synth"),
 ])
 def test_library_exports_every_declared_symbol(header, macro, which):
     path = build.build_sp() if which == "sp" else build.build_synth()
     names = _declared(header, macro)
-    assert len(names) >= 8
+    assert len(names) >= (1 if header == "sp_loadgen.h" else 8)
     missing = [n for n in names if n not in _exported(path)]
     assert not missing, f"{os.path.basename(path)} lacks {missing}"
     import ctypes
@@ -125,3 +127,13 @@ def test_masks_to_dense_roundtrip():
     bits = (rng.random((3, 70)) < 0.3).astype(np.uint8)
     packed = synth.pack_frames(bits)
     np.testing.assert_array_equal(spg.masks_to_dense(packed, 70), bits)
+
+
+def test_load_generator_rejects_invalid_arguments():
+    """Argument checks happen before any call to the server."""
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_loadgen_run(None, [0], [np.zeros((1, 4), np.uint32)], 30.0, 1.0)
+    assert e.value.status == 1
+    with pytest.raises(spg.SpError) as e:
+        spg.sp_loadgen_run(1, [0], [np.zeros((1, 4), np.uint32)], -1.0, 1.0)
+    assert e.value.status == 1

@@ -213,3 +213,31 @@ def test_submit_many_matches_the_oracle(device):
     for sid in sids:
         spg.sp_server_close_stream(srv, sid)
     spg.sp_server_destroy(srv)
+
+
+def test_native_load_generator_open_and_closed_loop():
+    """The native load generator (include/sp_loadgen.h) on 6 streams: a
+    closed-loop second keeps every queue full, an open-loop second offers
+    Poisson arrivals at 200 fps per stream; every accepted frame comes back
+    without error, arrivals are either accepted or refused, and latencies are
+    positive and ordered."""
+    cases, frames = _streams(6, 8)
+    packed = [wl.pack(f) for f in frames]
+    words = max(p.shape[1] for p in packed)
+    srv = spg.sp_server_create(max_streams=8, queue_depth=4, max_input_words=words,
+                               device_budget_bytes=1 << 30, max_active=64)
+    sids = [spg.sp_server_open_stream(srv, c.config(), state=(c.idx, c.perm, c.boost))
+            for c in cases]
+    closed = spg.sp_loadgen_run(srv, sids, packed, 0.0, 1.0, producers=2, seed=1)
+    assert closed["errors"] == 0 and closed["completed"] == closed["submitted"] > 0
+    assert closed["frames_per_s"] > 1000
+    opened = spg.sp_loadgen_run(srv, sids, packed, 200.0, 1.0, producers=3, seed=2)
+    assert opened["errors"] == 0 and opened["completed"] == opened["submitted"]
+    assert opened["offered"] == opened["submitted"] + opened["refused"]
+    assert 0.5 * 1200 < opened["offered"] < 1.5 * 1200  # 6 streams x 200 fps x 1 s
+    assert 0 < opened["p50_us"] <= opened["p99_us"] <= opened["max_us"]
+    st = spg.sp_server_get_stats(srv)
+    assert st["completed"] >= closed["completed"] + opened["completed"]
+    for sid in sids:
+        spg.sp_server_close_stream(srv, sid)
+    spg.sp_server_destroy(srv)
