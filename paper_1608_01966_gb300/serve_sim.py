@@ -208,6 +208,7 @@ def _native(srv, sids, res, pools, rate, seconds, producers, seed):
 
 
 SWEEP = (0.1, 0.25, 0.5, 0.75, 0.9, 1.0)
+KNEE_P99_MS = 1.0  # latency objective of the knee
 
 
 def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=3.0, sweep_seconds=3.0,
@@ -216,9 +217,8 @@ def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=3.0, sweep_sec
     load generator (include/sp_loadgen.h): the closed-loop saturation
     throughput; a sweep of open-loop Poisson loads at fractions of it
     (p50/p99 latency at each, and the knee: the highest load whose p99 stays
-    within twice the lightest load's while at least 99 % of the offered frames
-    are served); and the workload itself, every stream at `fps`, for
-    `seconds`."""
+    within KNEE_P99_MS while at least 99 % of the offered frames are served);
+    and the workload itself, every stream at `fps`, for `seconds`."""
     pools = _frame_pools(16, seed)
     words = max(p.shape[1] for p in pools.values())
     srv = spg.sp_server_create(max_streams=streams, queue_depth=4, max_input_words=words,
@@ -240,15 +240,16 @@ def simulate(streams=32, fps=30.0, seconds=60.0, saturate_seconds=3.0, sweep_sec
                 pt["fraction_of_saturation"] = frac
                 pts.append(pt)
             out["sweep"] = pts
-            base = pts[0]["p99_ms"]
             knee = None
             for pt in pts:
-                if pt["p99_ms"] <= 2.0 * base and pt["frames"] >= 0.99 * pt["offered_per_s"] * sweep_seconds:
+                served = pt["frames"] / max(1.0, pt["offered_per_s"] * sweep_seconds)
+                if pt["p99_ms"] <= KNEE_P99_MS and served >= 0.99:
                     knee = pt
             out["knee"] = None if knee is None else {
                 "fraction_of_saturation": knee["fraction_of_saturation"],
                 "frames_per_s": knee["frames_per_s"], "p99_ms": knee["p99_ms"],
-                "rule": "highest load with p99 <= 2 x the 10 % load's p99 and >= 99 % served"}
+                "rule": f"highest load with p99 <= {KNEE_P99_MS} ms and >= 99 % of the offered "
+                        "frames served (the rest arrive at a full stream queue)"}
         if seconds > 0:
             out["open_loop"] = _native(srv, sids, res, pools, fps, seconds, producers, seed)
         st = spg.sp_server_get_stats(srv)
