@@ -494,6 +494,47 @@ def run_dense_tc(spg, torch, dev, stream, members=16, frames=256, steps=5):
                        "peak_kind": kind}}
 
 
+def run_batched_mixed(spg, torch, dev, stream, frames=256, steps=5):
+    """The batched workload as one call: the 64 uneven SPs and the 16 dense SPs
+    (1024 x 1024) in one batch, inference over 256 frames per
+    sp_batch_infer_device call (tensor cores for the dense members, one
+    persistent launch for the others)."""
+    from paper_1608_01966_gb300 import workloads as wl
+    unv, dens = wl.uneven_cases(64)
+    dcases, dfr = wl.dense_cases(16, frames)
+    cases = unv + dcases
+    fr = wl.uneven_frames(unv, dens, frames) + dfr
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, _ = spg.sp_batch_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    d = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in fr], fo, fw).view(np.int32)).to(dev)
+    mw = info["mask_words"]
+    dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        spg.sp_batch_infer_device(b, d, frames, fw, dm, mw, stream)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(steps):
+        spg.sp_batch_infer_device(b, d, frames, fw, dm, mw, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / steps
+    forms = [spg.FORM_NAMES[int(f)] for f in spg.sp_batch_forms(b)]
+    spg.sp_batch_destroy(b)
+    for h in hs:
+        spg.sp_destroy(h)
+    n = len(cases)
+    return {"workload": f"64 uneven SPs + 16 dense SPs (1024 x 1024) in one batch, inference, "
+                        f"{frames} frames per call (dense members on the tensor cores, the others "
+                        "in one persistent launch)",
+            "ms_per_call": ms, "frames_per_s": n * frames / (ms / 1000.0),
+            "column_updates_per_s": sum(c.C for c in cases) * frames / (ms / 1000.0),
+            "forms": {f: forms.count(f) for f in sorted(set(forms))}}
+
+
 def run_encoder(spg, torch, dev, stream, n_frames=128, steps=5, reduce=1):
     """Frame encoder over n_frames 960x540 colour frames in one call (inputs
     larger than L2), then the encoder feeding one frame-shaped SP (learning
@@ -706,9 +747,10 @@ def main():
     if not args.no_dense:
         dense_tc = run_dense_tc(spg, torch, dev, stream)
 
-    uneven = None
+    uneven = mixed = None
     if not args.no_dense:
         uneven = run_uneven_batch(spg, torch, dev, stream)
+        mixed = run_batched_mixed(spg, torch, dev, stream)
 
     encoder = None
     if not args.no_encoder:
@@ -784,6 +826,7 @@ def main():
             "single_sp": single,
             "dense_tc": dense_tc,
             "uneven_batch": uneven,
+            "batched_mixed": mixed,
             "encoder": encoder,
             "serve": serve,
             "cpu_baseline": cpu,

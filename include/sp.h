@@ -358,18 +358,20 @@ SP_API sp_status sp_batch_compute(sp_batch* b, const uint32_t* h_frames, uint32_
                                   uint64_t frame_stride_words, int learn, uint32_t* h_masks,
                                   uint64_t mask_stride_words);
 
-/* Inference (no learning) over n_frames batch frames for a batch whose
- * members all have dense pools (every column's pool is its whole input,
- * S = n_in): the overlaps of every member and frame are one {0,1} matrix
- * product per member on the tensor cores (tcgen05, e4m3 operands, fp32
- * accumulation; exact), all members in one launch, then Alg. 2 for every
- * frame of every member in a second launch; the frames are first laid out
- * as operands in one more launch, and a member's connection operand is
- * rebuilt (one launch for all such members) only when its permanences may
- * have changed since it was last built.  Learning pending from an earlier
- * batch step is applied first.  Results are those of n_frames calls of
- * sp_batch_compute_device with learn = 0.  Frame and mask layout as
- * sp_batch_compute_device.  SP_ENOTSUP if a member's pools are not dense. */
+/* Inference (no learning) over n_frames batch frames.  Members with dense
+ * pools (every column's pool is its whole input, S = n_in): the overlaps of
+ * every such member and frame are one {0,1} matrix product per member on the
+ * tensor cores (tcgen05, e4m3 operands, fp32 accumulation; exact), all of
+ * them in one launch, then Alg. 2 for every frame of every member in a second
+ * launch; the frames are first laid out as operands in one more launch, and
+ * a member's connection operand is rebuilt (one launch for all such members)
+ * only when its permanences may have changed since it was last built.  The
+ * other members run all n_frames in one persistent launch of the batch step
+ * (their CTAs only), before the tensor-core launches; such batches need
+ * d_frames 16-byte aligned and the stride a multiple of 4 words.  Learning
+ * pending from an earlier batch step is applied first.  Results are those of
+ * n_frames calls of sp_batch_compute_device with learn = 0.  Frame and mask
+ * layout as sp_batch_compute_device. */
 SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
                                        uint64_t frame_stride_words, uint32_t* d_masks,
                                        uint64_t mask_stride_words, void* stream);

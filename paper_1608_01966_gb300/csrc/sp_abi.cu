@@ -1216,6 +1216,10 @@ struct sp_batch {
   sp::BatchDesc* d_desc = nullptr;
   uint32_t* d_cta_inst = nullptr;
   uint32_t n_ctas = 0, max_C = 0;
+  // inference of a batch that mixes dense members (tensor cores) with others:
+  // the CTA map of the others alone, for their persistent launch
+  uint32_t* d_cta_sparse = nullptr;
+  uint32_t n_ctas_sparse = 0, max_C_sparse = 0;
   std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
   void* d_sync = nullptr;             // persistent launches: work counter, abort, done[n]
   uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
@@ -1335,6 +1339,33 @@ sp_status batch_wait(sp_batch* b) {
   }
 }
 
+// The CTA map of the members without dense pools, when the batch also has
+// dense ones (their inference runs on the tensor cores).
+sp_status build_sparse_map(sp_batch* b, const std::vector<uint32_t>& cta_inst) {
+  bool any_dense = false;
+  for (sp_handle* h : b->members) any_dense = any_dense || h->dense;
+  std::vector<uint32_t> sparse;
+  uint32_t max_C = 0;
+  if (any_dense)
+    for (uint32_t i : cta_inst)
+      if (!b->members[i]->dense) {
+        sparse.push_back(i);
+        max_C = std::max(max_C, b->members[i]->C);
+      }
+  if (b->d_cta_sparse) {
+    cudaStreamSynchronize(b->stream);
+    cudaFree(b->d_cta_sparse);
+    b->d_cta_sparse = nullptr;
+  }
+  b->n_ctas_sparse = 0;
+  b->max_C_sparse = max_C;
+  if (sparse.empty()) return SP_OK;
+  SP_CUDA(device_malloc((void**)&b->d_cta_sparse, sparse.size() * 4));
+  SP_CUDA(cudaMemcpy(b->d_cta_sparse, sparse.data(), sparse.size() * 4, cudaMemcpyHostToDevice));
+  b->n_ctas_sparse = (uint32_t)sparse.size();
+  return SP_OK;
+}
+
 void free_batch(sp_batch* b) {
   if (!b) return;
   DeviceGuard g(b->device);
@@ -1356,6 +1387,7 @@ void free_batch(sp_batch* b) {
   if (b->ev_wait) cudaEventDestroy(b->ev_wait);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   if (b->d_block) cudaFree(b->d_block);
+  if (b->d_cta_sparse) cudaFree(b->d_cta_sparse);
   if (b->d_infer_args) cudaFree(b->d_infer_args);
   if (b->h_infer_args) cudaFreeHost(b->h_infer_args);
   for (int i = 0; i < 2; ++i)
@@ -1604,6 +1636,11 @@ SP_API sp_status sp_batch_create(sp_handle* const* members, uint32_t n, sp_batch
     members[i]->pending = false;
     b->members.push_back(members[i]);
   }
+  if (build_sparse_map(b, cta_inst) != SP_OK) {
+    const std::string msg = sp_last_error();
+    sp_batch_destroy(b);
+    return fail(SP_ENOMEM, "%s", msg.c_str());
+  }
   *out = b;
   return SP_OK;
 }
@@ -1744,15 +1781,24 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
   if (reinterpret_cast<uintptr_t>(d_frames) % 4u || reinterpret_cast<uintptr_t>(d_masks) % 4u ||
       reinterpret_cast<uintptr_t>(d_overlaps) % 4u)
     return fail(SP_EINVAL, "device pointers must be 4-byte aligned");
-  for (sp_handle* h : b->members)
-    if (!h->dense) return fail(SP_ENOTSUP, "every member needs dense pools (S = n_in)");
   DeviceGuard g(b->device);
   sp_status st = batch_use_stream(b, static_cast<cudaStream_t>(stream));
   if (st != SP_OK) return st;
-  const uint32_t n = (uint32_t)b->members.size();
-  // learning left pending by the last batch step is applied first
-  if (b->pending) {
-    for (sp_handle* h : b->members) {
+  // dense members on the tensor cores, the others in one persistent launch
+  std::vector<uint32_t> dm;
+  for (uint32_t i = 0; i < (uint32_t)b->members.size(); ++i)
+    if (b->members[i]->dense) dm.push_back(i);
+  if (dm.size() < b->members.size() && (reinterpret_cast<uintptr_t>(d_frames) % 16u ||
+                                        (n_frames > 1 && stride % 4u)))
+    return fail(SP_EINVAL, "a batch with members of sparse pools needs 16-byte aligned frames");
+  const uint32_t n = (uint32_t)dm.size();
+  // learning left pending by the last batch step is applied first: by a
+  // learning pass for the dense members, by the persistent launch (which
+  // also keeps their compact or window form in step) for the others
+  const bool pend = b->pending;
+  if (pend) {
+    for (uint32_t i : dm) {
+      sp_handle* h = b->members[i];
       sp::LearnArgs l{};
       l.idx = h->d_idx;
       l.perm = h->d_perm;
@@ -1766,19 +1812,57 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     }
     b->pending = false;
   }
+  // the members without dense pools: one persistent launch of their CTAs
+  // (no learning; frame 0 applies what was pending), before the tensor-core
+  // launches
+  const uint32_t cur0 = (uint32_t)b->cur;
+  const uint32_t last_par = cur0 ^ ((n_frames - 1u) & 1u);  // the last frame's mask slot
+  if (b->n_ctas_sparse) {
+    sp::BatchRunArgs r{};
+    r.desc = b->d_desc;
+    r.cta_inst = b->d_cta_sparse;
+    r.items_per_frame = b->n_ctas_sparse;
+    r.n_frames = n_frames;
+    r.frames = d_frames;
+    r.stride = stride;
+    r.masks_out = d_masks;
+    r.mstride = mstride;
+    r.ov_out = d_overlaps;
+    r.ov_stride = ov_stride;
+    r.cur0 = cur0;
+    r.pending0 = pend ? 1u : 0u;
+    r.learn = 0u;
+    r.epoch = 0u;
+    r.work = static_cast<unsigned long long*>(b->d_sync);
+    r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
+    r.done = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 16);
+    r.err = b->d_err;
+    r.stage_cap = b->stage_cap;
+    r.xspan_cap = b->xspan_cap;
+    r.win_cap = b->win_cap;
+    r.wait_ns = b->wait_ns;
+    SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
+    SP_CUDA(sp::launch_batch_run(r, b->max_C_sparse, b->stream));
+  }
+  if (n == 0) {
+    b->cur ^= (int)(n_frames & 1u);
+    b->frames += n_frames;
+    return SP_OK;
+  }
   std::vector<sp::DenseArgs> dargs(n);
   std::vector<sp::FrameInhibitArgs> fargs(n);
   uint32_t max_C = 0, max_S = 0, max_K = 0;
   bool all_global = true, any_pack = false;
-  for (uint32_t i = 0; i < n; ++i) {
+  for (uint32_t ii = 0; ii < n; ++ii) {
+    const uint32_t i = dm[ii];
     sp_handle* h = b->members[i];
     if ((st = ensure_dense_buffers(h, n_frames)) != SP_OK) return st;
-    sp::DenseArgs& d = dargs[i];
+    sp::DenseArgs& d = dargs[ii];
     d = dense_args(h, d_frames + b->frame_off[i], n_frames, stride);
     any_pack = any_pack || d.pack != 0u;
     max_K = std::max(max_K, h->S);
     h->dense_used = true;
-    sp::FrameInhibitArgs& f = fargs[i];
+    sp::FrameInhibitArgs& f = fargs[ii];
     f.ov = h->d_run_ov;
     f.n_frames = n_frames;
     f.C = h->C;
@@ -1793,7 +1877,7 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     const bool duty = h->cfg.duty_period > 0.0f;
     f.masks_out = d_masks ? d_masks + b->mask_off[i] : (duty ? h->d_run_masks : nullptr);
     f.masks_stride = d_masks ? mstride : h->mask_words;
-    f.mask_last = h->d_mask[b->cur];
+    f.mask_last = h->d_mask[last_par];
     f.result = h->d_result;
     f.ov_last = h->d_ov;
     max_C = std::max(max_C, h->C);
@@ -1834,19 +1918,19 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     last.assign(h_args, h_args + arg_bytes);
   }
   if (any_pack) SP_CUDA(sp::launch_conn_image(d_dargs, n, max_C, max_K, b->stream));
-  for (sp_handle* h : b->members) h->bimg_stale = false;
+  for (uint32_t i : dm) b->members[i]->bimg_stale = false;
   // frame images, product, selection and duty cycles: the same launches for
   // the same frames, masks and slot, so they are recorded once and replayed
   uint64_t n_launch = 3;
-  for (sp_handle* h : b->members) n_launch += h->cfg.duty_period > 0.0f ? 1u : 0u;
+  for (uint32_t i : dm) n_launch += b->members[i]->cfg.duty_period > 0.0f ? 1u : 0u;
   auto enqueue = [&](cudaStream_t st) -> sp_status {
     SP_CUDA(sp::launch_frame_image(d_dargs, n, n_frames, max_K, st));
     SP_CUDA(sp::launch_dense_overlap_many(d_dargs, n, max_C, n_frames, st));
     SP_CUDA(sp::launch_frame_inhibit_many(d_fargs, n, max_C, max_S, n_frames, all_global, st));
-    for (uint32_t i = 0; i < n; ++i) {
-      sp_handle* h = b->members[i];
+    for (uint32_t ii = 0; ii < n; ++ii) {
+      sp_handle* h = b->members[dm[ii]];
       if (h->cfg.duty_period > 0.0f)
-        SP_CUDA(sp::launch_duty_run(fargs[i].masks_out, n_frames, (uint32_t)fargs[i].masks_stride,
+        SP_CUDA(sp::launch_duty_run(fargs[ii].masks_out, n_frames, (uint32_t)fargs[ii].masks_stride,
                                     h->C, h->d_duty, h->cfg.duty_period, st));
     }
     return SP_OK;
@@ -1858,7 +1942,7 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     // selection's histogram size and the members' run buffers (the duty
     // launches hold their masks' address) are part of the recorded launches
     uint64_t gens = 0;
-    for (sp_handle* h : b->members) gens += h->run_gen;
+    for (uint32_t i : dm) gens += b->members[i]->run_gen;
     GraphKey key{d_frames, n_frames, stride, 2, d_masks, b->cur, false, all_global, mstride};
     key.extra = (uint64_t)max_S | (gens << 32);
     GraphEntry* e = nullptr;
@@ -1897,15 +1981,15 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     sp::g_launches.fetch_add(n_launch, std::memory_order_relaxed);
   }
   if (d_overlaps) {
-    // each member's [n_frames][C] run overlaps into its columns of the record
-    for (uint32_t i = 0; i < n; ++i) {
+    // each dense member's [n_frames][C] run overlaps into its columns of the record
+    for (uint32_t i : dm) {
       sp_handle* h = b->members[i];
       SP_CUDA(cudaMemcpy2DAsync(d_overlaps + b->ov_off[i], ov_stride * 4, h->d_run_ov,
                                 (size_t)h->C * 4, (size_t)h->C * 4, n_frames,
                                 cudaMemcpyDeviceToDevice, b->stream));
     }
   }
-  b->cur ^= 1;
+  b->cur ^= (int)(n_frames & 1u);
   b->frames += n_frames;
   return SP_OK;
 }
@@ -1960,6 +2044,8 @@ sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
   b->n_ctas = (uint32_t)cta_inst.size();
   b->cols_per_warp = cols_per_warp;
   b->win_cap = win_cap;
+  sp_status sm = build_sparse_map(b, cta_inst);
+  if (sm != SP_OK) return sm;
   for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);  // recorded with the old grid
   b->graphs.clear();
   return SP_OK;

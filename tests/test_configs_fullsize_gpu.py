@@ -9,6 +9,8 @@ and the final permanences.
              16 frames -- exactly the benchmark's members and frames;
   dense      16 SPs with dense pools (1024 inputs x 1024 columns) inferring
              256 frames on the tensor cores;
+  mixed      both kinds in one batch and one inference call (tensor cores for
+             the dense members, one persistent launch for the others);
   serving    32 video streams at 320x180 / 640x360 / 960x540 through the
              library's continuous-batching server, learning on, frames
              submitted by several producer threads.
@@ -183,3 +185,51 @@ def test_serving_32_streams_three_resolutions():
 
     with cf.ThreadPoolExecutor(max_workers=8) as ex:
         list(ex.map(check, range(n)))
+
+
+def test_uneven_and_dense_members_in_one_inference_call():
+    """The batched workload as one call: the 64 uneven SPs and the 16 dense
+    SPs (1024 x 1024) in one batch, inference over 128 frames through
+    sp_batch_infer_overlaps_device -- the dense members on the tensor cores,
+    the others in one persistent launch -- then a learning frame for every
+    member and one more inference call: every member's overlaps and winners
+    of every frame equal the oracle's."""
+    unv, dens = wl.uneven_cases(64)
+    dcases, dframes = wl.dense_cases(16, 129)
+    F = 128
+    uframes = wl.uneven_frames(unv, dens, F + 1)
+    cases = unv + dcases
+    frames = uframes + dframes
+    hs, b, info, fo, mo, oo, ow, fw = _batch(cases)
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    st = torch.cuda.current_stream()
+    dm = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((F, ow), -1.0, dtype=torch.float32, device="cuda")
+    spg.sp_batch_infer_overlaps_device(b, d, F, fw, dm, mw, dov, ow, st)
+    # one learning frame through the batch step, then inference again
+    dm1 = torch.zeros((1, mw), dtype=torch.int32, device="cuda")
+    spg.sp_batch_compute_device(b, d[F], 1, fw, True, dm1, mw, st)
+    dm2 = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    dov2 = torch.full((F, ow), -1.0, dtype=torch.float32, device="cuda")
+    spg.sp_batch_infer_overlaps_device(b, d, F, fw, dm2, mw, dov2, ow, st)
+    spg.sp_batch_sync(b)
+    acts, ovs = _split(cases, dm.cpu().numpy().view(np.uint32), dov.cpu().numpy(), mo, oo)
+    acts2, ovs2 = _split(cases, dm2.cpu().numpy().view(np.uint32), dov2.cpu().numpy(), mo, oo)
+    spg.sp_batch_destroy(b)
+    for h in hs:
+        spg.sp_destroy(h)
+    first = [f[:F] for f in frames]
+    _compare(cases, first, False, acts, ovs, None, "mixed infer")
+
+    def after_learning(i):
+        c = cases[i]
+        _, perm, _ = oracle_run(c, frames[i][F:F + 1], True)
+        return oracle_run(c, frames[i][:F], False, perm=perm, want_ov=True)
+
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        res = list(ex.map(after_learning, range(len(cases))))
+    for i, (act, _, ov) in enumerate(res):
+        assert first_diff(ovs2[i], ov) is None, f"member {i} after learning: overlaps"
+        assert first_diff(acts2[i], act) is None, f"member {i} after learning: winners"
