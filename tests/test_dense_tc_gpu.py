@@ -329,3 +329,109 @@ def test_dense_batch_repeated_runs_replay_recorded_launches(monkeypatch, graphs)
         np.testing.assert_array_equal(spg.sp_get_duty_cycles(hs[i]), duty[i])
         np.testing.assert_array_equal(spg.sp_active_columns(hs[i]), np.flatnonzero(last[i]))
         spg.sp_destroy(hs[i])
+
+
+def _run_batch(cases, frames, F):
+    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+    b = spg.sp_batch_create(hs)
+    info = spg.sp_batch_get_info(b)
+    fo, mo = spg.sp_batch_offsets(b)
+    oo, ow = spg.sp_batch_overlap_offsets(b)
+    fw = (info["frame_words"] + 3) // 4 * 4
+    bf = wl.batch_frames([wl.pack(f) for f in frames], fo, fw)
+    d = torch.from_numpy(bf.view(np.int32)).cuda()
+    mw = info["mask_words"]
+    dm = torch.zeros((F, mw), dtype=torch.int32, device="cuda")
+    dov = torch.full((F, ow), -1.0, dtype=torch.float32, device="cuda")
+    spg.sp_batch_infer_overlaps_device(b, d, F, fw, dm, mw, dov, ow, torch.cuda.current_stream())
+    spg.sp_batch_sync(b)
+    masks = dm.cpu().numpy().view(np.uint32)
+    ovr = dov.cpu().numpy()
+    spg.sp_batch_destroy(b)
+    out = []
+    for i, c in enumerate(cases):
+        out.append((dense(masks[:, int(mo[i]):int(mo[i]) + (c.C + 31) // 32], c.C),
+                    ovr[:, int(oo[i]):int(oo[i]) + c.C], spg.sp_active_columns(hs[i]),
+                    spg.sp_get_overlaps(hs[i])))
+        spg.sp_destroy(hs[i])
+    return out
+
+
+def _check(case, frames, got, ovs, lst, gov):
+    act, _, ov = oracle_run(case, frames, False, want_ov=True)
+    assert first_diff(ovs, ov) is None
+    assert first_diff(got, act) is None
+    np.testing.assert_array_equal(lst, np.flatnonzero(act[-1]))
+    np.testing.assert_array_equal(gov, ov[-1])
+    return act, ov
+
+
+def test_dense_select_every_overlap_equal():
+    """Every synapse connected: all 1024 columns of a frame have the same
+    overlap, so the k winners are decided by column order alone (the k lowest
+    columns).  Zero frames in the run: no winner."""
+    case = _dense_case(1024, 512, 140, k=20, m=1, lo=0.25, hi=0.3)
+    frames = _frames(40, 512, 0.3, 141)
+    frames[5] = 0
+    frames[17] = 0
+    got, gov, lst, _, _, ovs = _run(case, frames)
+    act, _ = _check(case, frames, got, ovs, lst, gov)
+    assert act[5].sum() == 0 and act[17].sum() == 0
+    assert all(np.array_equal(np.flatnonzero(act[t]), np.arange(20)) for t in range(40)
+               if t not in (5, 17))
+
+
+@pytest.mark.parametrize("C,n_in,F,k,m,p", [
+    (1000, 1000, 600, 32, 4, 0.2),   # five 128-frame tiles, the last ragged
+    (130, 777, 257, 1, 1, 0.3),      # a column tile holding 130 columns, k = 1
+    (300, 640, 140, 16, 3, 0.15),    # two column tiles, the second ragged
+    (1024, 512, 50, 20, 6, 0.0),     # frames with fewer than k nonzero overlaps, and with more
+    (896, 1536, 256, 24, 2, 0.05),   # four column tiles, the last one ragged, twelve slices
+])
+def test_dense_select_shapes(C, n_in, F, k, m, p):
+    """The product and the per-frame selection at the edges of their tiling:
+    column, frame and input counts that fill no tile, k at both ends of the
+    range where the k-th largest lane maximum bounds the k-th overlap, runs
+    with fewer than k nonzero overlaps."""
+    case = _dense_case(C, n_in, 150 + C % 89, k=k, m=m)
+    if p > 0:
+        frames = _frames(F, n_in, p, 151 + k)
+    else:
+        # exactly 6 or 8 active inputs: with min_overlap 6 only the columns
+        # connected to all 6 (about 1 in 64: fewer than k) or to 6 of the 8
+        # (about 1 in 7) keep a nonzero overlap
+        rng = np.random.default_rng(153)
+        frames = np.zeros((F, n_in), np.uint8)
+        for t in range(F):
+            frames[t, rng.choice(n_in, 6 if t % 2 else 8, replace=False)] = 1
+    got, gov, lst, launches, _, ovs = _run(case, frames)
+    assert launches <= 4  # connection image, frame image, product, selection
+    act, ov = _check(case, frames, got, ovs, lst, gov)
+    if p == 0:
+        nz = (ov > 0).sum(axis=1)
+        assert ((nz > 0) & (nz < k)).any() and (nz >= k).any()  # the case is what it says
+
+
+def test_dense_select_non_unit_boosts_with_ties():
+    """Boosts that map different raw counts to one overlap and equal counts
+    to many: ties across column tiles resolve to the lowest columns, as Alg.
+    2's column order asks."""
+    C = 768
+    boost = np.where(np.arange(C) % 3 == 0, 1.5, 1.0).astype(np.float32)
+    boost[::7] = 0.75
+    case = _dense_case(C, 640, 160, k=17, m=2, boost=boost)
+    frames = _frames(100, 640, 0.25, 161)
+    got, gov, lst, _, _, ovs = _run(case, frames)
+    _check(case, frames, got, ovs, lst, gov)
+
+
+def test_dense_batch_members_of_mixed_widths_and_frames():
+    """A batch whose members have 1 to 4 column tiles and different input
+    sizes, over 300 frames (three frame tiles): every member's overlaps,
+    winners, last list and last overlaps."""
+    shapes = [(100, 300, 3), (1024, 1024, 20), (513, 700, 9), (256, 4096, 8)]
+    cases = [_dense_case(C, n, 170 + i, k=k, m=3) for i, (C, n, k) in enumerate(shapes)]
+    F = 300
+    frames = [_frames(F, c.n_in, 0.03 + 0.06 * i, 180 + i) for i, c in enumerate(cases)]
+    for i, (got, ovs, lst, gov) in enumerate(_run_batch(cases, frames, F)):
+        _check(cases[i], frames[i], got, ovs, lst, gov)
