@@ -327,41 +327,55 @@ def oracle_sample_parallel(cases, pool_u8, seconds, threads):
 def run_uneven_batch(spg, torch, dev, stream, members=64, frames=16, steps=5):
     """64 independent SPs of uneven shapes (columns 128..4096, synapses
     16..256, inputs 256..16384 bits at 2-20 % density, k = 2 % of columns,
-    learning on), autotuned, stepped by persistent launches of 16 frames."""
+    learning on), stepped by persistent launches of 16 frames: once with the
+    default schedule and splits, once autotuned (each from fresh handles)."""
     from paper_1608_01966_gb300 import workloads as wl
     cases, dens = wl.uneven_cases(members)
-    hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
-    b = spg.sp_batch_create(hs)
-    info = spg.sp_batch_get_info(b)
-    fo, mo = spg.sp_batch_offsets(b)
-    fw = (info["frame_words"] + 3) // 4 * 4
     fr = [wl.pack(f) for f in wl.uneven_frames(cases, dens, frames)]
-    d = torch.from_numpy(wl.batch_frames(fr, fo, fw).view(np.int32)).to(dev)
-    mw = info["mask_words"]
-    dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
-    cpw = spg.sp_batch_autotune(b, d, 4, fw)
-    spg.sp_batch_compute_device(b, d, frames, fw, True, dm, mw, stream)
-    spg.sp_batch_sync(b)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(steps):
+
+    def timed(tune):
+        hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
+        b = spg.sp_batch_create(hs)
+        info = spg.sp_batch_get_info(b)
+        fo, _ = spg.sp_batch_offsets(b)
+        fw = (info["frame_words"] + 3) // 4 * 4
+        d = torch.from_numpy(wl.batch_frames(fr, fo, fw).view(np.int32)).to(dev)
+        mw = info["mask_words"]
+        dm = torch.zeros((frames, mw), dtype=torch.int32, device=dev)
+        cpw = spg.sp_batch_autotune(b, d, 4, fw) if tune else 0
+        sched = spg.sp_batch_schedule(b, len(hs))
         spg.sp_batch_compute_device(b, d, frames, fw, True, dm, mw, stream)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    ms = s0.elapsed_time(s1) / (steps * frames)
-    forms_b = spg.sp_batch_forms(b)
-    spg.sp_batch_destroy(b)
-    for h in hs:
-        spg.sp_destroy(h)
+        spg.sp_batch_sync(b)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(steps):
+            spg.sp_batch_compute_device(b, d, frames, fw, True, dm, mw, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / (steps * frames)
+        forms_b = spg.sp_batch_forms(b)
+        spg.sp_batch_destroy(b)
+        for h in hs:
+            spg.sp_destroy(h)
+        return ms, cpw, sched, forms_b
+
+    ms0, _, _, _ = timed(False)
+    ms, cpw, sched, forms_b = timed(True)
     upd = sum(c.C for c in cases)
     peak, kind = read_peaks()
     forms = [spg.FORM_NAMES[int(f)] for f in forms_b]
     moved = sum(form_bytes_per_frame(c, f) for c, f in zip(cases, forms))
     gbs = moved / (ms / 1000.0) / 1e9
+    per = sched[2]
     return {"workload": f"{members} uneven SPs (C 128..4096, S 16..256, inputs 256..16384 bits), "
                         f"learning on, {frames} frames per persistent launch, autotuned",
-            "cols_per_warp": cpw, "us_per_batch_frame": ms * 1000.0,
+            "schedule": {"ctas_per_sm": sched[0], "cols_in_flight": sched[1],
+                         "cols_per_warp": cpw if cpw != spg.SP_MIXED_SPLIT else "per member",
+                         "member_cols_per_warp": {str(v): per.count(v) for v in sorted(set(per))}},
+            "us_per_batch_frame": ms * 1000.0,
+            "default_schedule_us_per_batch_frame": ms0 * 1000.0,
+            "tuning_gain": ms0 / ms,
             "frames_per_s": members / (ms / 1000.0),
             "column_updates_per_s": upd / (ms / 1000.0),
             "roofline": {"bound": "hbm", "kernel": "sp_batch_run_kernel", "achieved": gbs,
@@ -652,6 +666,7 @@ def main():
     if not args.no_autotune:  # set-up, outside the timed region
         cols_per_warp = spg.sp_batch_autotune(b, d_batch, 8, fw)
         info = spg.sp_batch_get_info(b)
+    sched = spg.sp_batch_schedule(b, n)
     forms = [spg.FORM_NAMES[int(f)] for f in spg.sp_batch_forms(b)]
 
     def step(t):
@@ -800,7 +815,10 @@ def main():
             "config": {"workload": WORKLOAD, "columns": 1024, "synapses": 256,
                        "input": "960x540", "winners_set_size": 40, "learn": True,
                        "instances_per_gpu": n, "frames_per_step_per_instance": 1,
-                       "cols_per_warp": cols_per_warp, "autotuned": cols_per_warp is not None,
+                       "cols_per_warp": (cols_per_warp if cols_per_warp != spg.SP_MIXED_SPLIT
+                                         else "per member"),
+                       "autotuned": cols_per_warp is not None,
+                       "schedule": {"ctas_per_sm": sched[0], "cols_in_flight": sched[1]},
                        "ctas_per_launch": int(info["ctas"]),
                        "state_bytes_per_gpu": int(sum(c.C * c.S * 8 for c in cases)),
                        "l2": "inputs larger than L2 (SP state streamed every step), no flush",

@@ -288,21 +288,57 @@ SP_API void sp_batch_destroy(sp_batch* b);
 
 SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out);
 
-/* Autotune the batch step's CTA shape on the caller's frames: for each
- * candidate split (each member's default, or 4 warps x {2, 4, 8, 16} columns
- * per warp for every member) run n_frames inference frames from d_frames
- * (device batch frames laid out as for sp_batch_compute_device, stride in
- * words) three times and keep the fastest; the default stays unless another
- * split is more than 3 % faster (inference frames leave out learning).
- * *cols_per_warp (nullable) receives the columns per warp chosen, 0 for the
- * default.  The members' permanences, learning and duty cycles are left as
- * they were; their last-frame overlaps and active columns are those of the
- * last tuning frame.  Tuning is a property of the workload and the device
- * (Section 4.4's sweeps show the cost moving with columns and synapses), so
- * call it once after sp_batch_create.  SP_EBUSY if learning is pending (tune
- * before the first learning frame); blocks until done (bounded waits). */
+/* Autotune the batch pass's schedule and CTA shapes on the caller's frames:
+ * run n_frames inference frames from d_frames (device batch frames laid out
+ * as for sp_batch_compute_device, stride in words) three times per candidate
+ * and keep the fastest, in three steps:
+ *   1. one CTA split for every member: each member's default, or 4 warps x
+ *      {2, 4, 8, 16} columns per warp;
+ *   2. the compiled schedule of the persistent pass (resident CTAs per SM,
+ *      which sets each thread's register budget, x columns per warp in
+ *      flight; sp_batch_schedule reports the choice);
+ *   3. when the members fall in several buckets (synapses per column <= 32,
+ *      <= 128 or more x input of at most 4096 bits or more), the split of
+ *      each bucket, largest bucket first, the others as chosen so far.
+ * A candidate replaces the best so far only if more than 3 % faster
+ * (inference frames leave out learning).  n_frames == 1 tunes the splits of
+ * single-frame launches only.  *cols_per_warp (nullable) receives the
+ * columns per warp chosen when every member has the same (0: the defaults),
+ * else SP_MIXED_SPLIT.  The members' permanences, learning and duty cycles
+ * are left as they were; their last-frame overlaps and active columns are
+ * those of the last tuning frame.  Tuning is a property of the workload and
+ * the device (Section 4.4's sweeps show the cost moving with columns and
+ * synapses), so call it once after sp_batch_create.  SP_EBUSY if learning is
+ * pending (tune before the first learning frame); blocks until done (bounded
+ * waits). */
+#define SP_MIXED_SPLIT 0xFFFFFFFFu
 SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32_t n_frames,
                                    uint64_t stride, uint32_t* cols_per_warp);
+
+/* The batch's schedule as set by sp_batch_autotune (before tuning: the
+ * default): resident CTAs per SM and columns per warp in flight of the
+ * persistent pass, and each member's columns per warp (an array of
+ * `members` entries, 0 for the member's default).  Any output may be NULL.
+ * Tuning machinery: the paper has no counterpart. */
+SP_API sp_status sp_batch_schedule(const sp_batch* b, uint32_t* ctas_per_sm,
+                                   uint32_t* cols_in_flight, uint32_t* member_cols_per_warp);
+
+/* The compiled schedules of the persistent pass (needs no device): *count
+ * (nullable) receives how many; ctas_per_sm[i] and cols_in_flight[i]
+ * (either nullable, room for cap entries, else SP_EINVAL) receive each.
+ * Entry 0 is the default.  Tuning machinery: the paper has no counterpart. */
+SP_API sp_status sp_batch_schedule_list(uint32_t* ctas_per_sm, uint32_t* cols_in_flight,
+                                        uint32_t cap, uint32_t* count);
+
+/* Set the batch's schedule without tuning (for instance one that
+ * sp_batch_autotune chose earlier on the same workload): the compiled
+ * schedule of ctas_per_sm x cols_in_flight (SP_ENOTSUP if none is
+ * compiled) and each member's columns per warp (array of `members` entries,
+ * 0 or NULL: the defaults; at most 64, else SP_EINVAL).  SP_EBUSY if
+ * learning is pending; blocks until the batch is idle.  Results do not
+ * depend on the schedule.  Tuning machinery: the paper has no counterpart. */
+SP_API sp_status sp_batch_set_schedule(sp_batch* b, uint32_t ctas_per_sm, uint32_t cols_in_flight,
+                                       const uint32_t* member_cols_per_warp);
 
 /* Per-member word offsets inside a batch frame and a batch mask record
  * (arrays of `members` entries; either may be NULL). */

@@ -7,7 +7,9 @@ from ._binding import (  # noqa: F401
     SP_ABI_VERSION, SP_INHIBIT_GLOBAL, SP_INHIBIT_LOCAL, SP_INHIBIT_PAPER_LITERAL,
     SP_MAX_COLUMNS, SP_POOL_DENSE, SP_POOL_UNIFORM, SP_POOL_WINDOW, SpConfig, SpError,
     SpatialPooler, lib, masks_to_dense,
-    sp_active_columns, sp_batch_autotune, sp_batch_compute, sp_batch_compute_device,
+    sp_active_columns, sp_batch_autotune, sp_batch_schedule, sp_batch_schedule_list,
+    sp_batch_set_schedule, SP_MIXED_SPLIT, sp_batch_compute,
+    sp_batch_compute_device,
     sp_batch_compute_overlaps_device, sp_batch_create, sp_batch_destroy, sp_batch_get_info,
     sp_batch_infer_device, sp_batch_infer_overlaps_device, sp_batch_offsets,
     sp_batch_overlap_offsets, sp_batch_set_device_wait_ns, sp_batch_sync, sp_batch_forms,

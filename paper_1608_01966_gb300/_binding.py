@@ -168,6 +168,9 @@ def lib():
         L.sp_batch_sync.argtypes = [vp]
         L.sp_batch_set_device_wait_ns.argtypes = [vp, ct.c_uint64]
         L.sp_batch_autotune.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, _u32p]
+        L.sp_batch_schedule.argtypes = [vp, _u32p, _u32p, _u32p]
+        L.sp_batch_schedule_list.argtypes = [_u32p, _u32p, ct.c_uint32, _u32p]
+        L.sp_batch_set_schedule.argtypes = [vp, ct.c_uint32, ct.c_uint32, _u32p]
         L.sp_batch_infer_device.argtypes = [vp, vp, ct.c_uint32, ct.c_uint64, vp, ct.c_uint64, vp]
         L.sp_server_create.argtypes = [ct.POINTER(SpServerConfig), ct.POINTER(vp)]
         L.sp_server_destroy.argtypes = [vp]
@@ -455,13 +458,47 @@ def sp_batch_infer_overlaps_device(b, d_frames, n_frames, stride_words, d_masks=
            "sp_batch_infer_overlaps_device")
 
 
+SP_MIXED_SPLIT = 0xFFFFFFFF
+
+
 def sp_batch_autotune(b, d_frames, n_frames, stride_words):
-    """Pick the batch step's CTA split on device batch frames; returns the
-    columns per warp chosen (0: each member's default)."""
+    """Pick the batch pass's schedule and CTA splits on device batch frames;
+    returns the columns per warp chosen when every member has the same (0:
+    the defaults), else SP_MIXED_SPLIT (sp_batch_schedule has each)."""
     out = ct.c_uint32(0)
     _check(lib().sp_batch_autotune(b, _addr(d_frames), n_frames, stride_words, ct.byref(out)),
            "sp_batch_autotune")
     return out.value
+
+
+def sp_batch_schedule(b, members):
+    """(ctas_per_sm, cols_in_flight, [columns per warp of each member, 0:
+    default]) of the batch's persistent pass."""
+    cps, cif = ct.c_uint32(0), ct.c_uint32(0)
+    per = (ct.c_uint32 * max(1, members))()
+    _check(lib().sp_batch_schedule(b, ct.byref(cps), ct.byref(cif), per), "sp_batch_schedule")
+    return cps.value, cif.value, [int(per[i]) for i in range(members)]
+
+
+def sp_batch_schedule_list():
+    """[(ctas_per_sm, cols_in_flight)] of the compiled schedules; the first is
+    the default."""
+    n = ct.c_uint32(0)
+    _check(lib().sp_batch_schedule_list(None, None, 0, ct.byref(n)), "sp_batch_schedule_list")
+    cps = (ct.c_uint32 * max(1, n.value))()
+    cif = (ct.c_uint32 * max(1, n.value))()
+    _check(lib().sp_batch_schedule_list(cps, cif, n.value, None), "sp_batch_schedule_list")
+    return [(int(cps[i]), int(cif[i])) for i in range(n.value)]
+
+
+def sp_batch_set_schedule(b, ctas_per_sm, cols_in_flight, member_cols_per_warp=None):
+    """Pin the batch's compiled schedule and each member's columns per warp
+    (None: the defaults)."""
+    per = None
+    if member_cols_per_warp is not None:
+        per = (ct.c_uint32 * len(member_cols_per_warp))(*member_cols_per_warp)
+    _check(lib().sp_batch_set_schedule(b, ctas_per_sm, cols_in_flight, per),
+           "sp_batch_set_schedule")
 
 
 def sp_batch_compute(b, frames, learn, masks_out=None):

@@ -1222,7 +1222,8 @@ struct sp_batch {
   uint32_t n_ctas_sparse = 0, max_C_sparse = 0;
   std::vector<sp::BatchDesc> h_desc;  // host copy of the descriptors
   void* d_sync = nullptr;             // persistent launches: work counter, abort, done[n]
-  uint32_t cols_per_warp = 0;         // 0: each member's default (batch_ctas)
+  std::vector<uint32_t> member_cpw;   // columns per warp of each member (0: batch_ctas' default)
+  uint32_t sched = 0;                 // compiled schedule of the persistent pass (0: default)
   uint32_t stage_cap = 0;             // shared memory for staging state by bulk copy
   uint32_t xspan_cap = 0;             // shared memory for each CTA's input words
   uint32_t win_cap = 0;               // shared memory of the widest window-form CTA
@@ -1481,7 +1482,7 @@ sp_status batch_run(sp_batch* b, const uint32_t* x_base, uint32_t n, uint64_t st
     // counter, abort word and done flags start at 0 in every launch, so a
     // launch recorded into a graph and replayed sees no stale flags
     SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
-    SP_CUDA(sp::launch_batch_run(r, b->max_C, b->stream));
+    SP_CUDA(sp::launch_batch_run(r, b->max_C, b->sched, b->stream));
     b->pending = learn != 0;
     b->cur ^= (int)(n & 1u);
     b->frames += n;
@@ -1842,7 +1843,7 @@ SP_API sp_status sp_batch_infer_overlaps_device(sp_batch* b, const uint32_t* d_f
     r.win_cap = b->win_cap;
     r.wait_ns = b->wait_ns;
     SP_CUDA(cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream));
-    SP_CUDA(sp::launch_batch_run(r, b->max_C_sparse, b->stream));
+    SP_CUDA(sp::launch_batch_run(r, b->max_C_sparse, b->sched, b->stream));
   }
   if (n == 0) {
     b->cur ^= (int)(n_frames & 1u);
@@ -2003,16 +2004,16 @@ SP_API sp_status sp_batch_infer_device(sp_batch* b, const uint32_t* d_frames, ui
 
 namespace {
 
-// Re-split every member into CTAs of 4 * cols_per_warp columns (0: each
+// Re-split member i into CTAs of 4 * cols_per_warp[i] columns (0: the
 // member's default) and upload the descriptors and CTA map.  The batch must
 // be idle.
-sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
+sp_status batch_relayout(sp_batch* b, const std::vector<uint32_t>& cols_per_warp) {
   std::vector<uint32_t> cta_inst;
   uint32_t win_cap = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {
     sp_handle* h = b->members[i];
     sp::BatchDesc& d = b->h_desc[i];
-    d.n_ctas = batch_ctas(h->C, h->S, cols_per_warp);
+    d.n_ctas = batch_ctas(h->C, h->S, cols_per_warp[i]);
     d.cta_first = (uint32_t)cta_inst.size();
     d.xspan = batch_xspan_cap() > 0u ? handle_xspan(h, d.n_ctas) : nullptr;
     uint32_t wb = 0;
@@ -2042,13 +2043,22 @@ sp_status batch_relayout(sp_batch* b, uint32_t cols_per_warp) {
                           cudaMemcpyHostToDevice, b->stream));
   SP_CUDA(cudaStreamSynchronize(b->stream));
   b->n_ctas = (uint32_t)cta_inst.size();
-  b->cols_per_warp = cols_per_warp;
+  b->member_cpw = cols_per_warp;
   b->win_cap = win_cap;
   sp_status sm = build_sparse_map(b, cta_inst);
   if (sm != SP_OK) return sm;
   for (auto& e : b->graphs) cudaGraphExecDestroy(e.exec);  // recorded with the old grid
   b->graphs.clear();
   return SP_OK;
+}
+
+// Tuning bucket of a member: its synapses per column (S <= 32, <= 128, more)
+// and its input (at most 4096 bits, more), the two sizes that set how a
+// column's pass streams its state and gathers its inputs.
+uint32_t tune_bucket(const sp_handle* h) {
+  const uint32_t sb = h->S <= 32u ? 0u : (h->S <= 128u ? 1u : 2u);
+  const uint32_t nb = h->n_words * 32u <= 4096u ? 0u : 1u;
+  return sb * 2u + nb;
 }
 
 }  // namespace
@@ -2082,19 +2092,16 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SP_CUDA(cudaEventCreate(&e0));
   SP_CUDA(cudaEventCreate(&e1));
-  const uint32_t candidates[] = {0u, 2u, 4u, 8u, 16u};  // 0: each member's default
-  std::vector<std::pair<uint32_t, float>> times;
-  uint32_t best = 0;
-  float best_ms = 0.0f;
-  bool any = false;
-  for (uint32_t cpw : candidates) {
-    s = batch_relayout(b, cpw);
-    if (s != SP_OK) break;
+  const bool persistent = n_frames >= 2 && persistent_enabled();
+  // the fastest of three runs of the tuning frames in the current layout and
+  // schedule, in the launch form sequences use (one persistent launch of
+  // inference frames), or one launch per frame for a single frame
+  auto time_layout = [&](float* best_of3) -> sp_status {
     float ms_min = 0.0f;
-    for (int rep = 0; rep < 3 && s == SP_OK; ++rep) {
+    sp_status st = SP_OK;
+    for (int rep = 0; rep < 3 && st == SP_OK; ++rep) {
       cudaError_t e = cudaEventRecord(e0, b->stream);
-      if (n_frames >= 2 && persistent_enabled()) {
-        // the launch form sequences use: one persistent launch, inference
+      if (persistent) {
         sp::BatchRunArgs r{};
         r.desc = b->d_desc;
         r.cta_inst = b->d_cta_inst;
@@ -2112,8 +2119,9 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         r.xspan_cap = b->xspan_cap;
         r.win_cap = b->win_cap;
         r.wait_ns = b->wait_ns;
-        e = cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream);
-        if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->stream);
+        if (e == cudaSuccess)
+          e = cudaMemsetAsync(b->d_sync, 0, 16 + b->members.size() * 4, b->stream);
+        if (e == cudaSuccess) e = sp::launch_batch_run(r, b->max_C, b->sched, b->stream);
       } else {
         for (uint32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
           sp::BatchArgs a{};
@@ -2129,24 +2137,80 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         }
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-      if (e == cudaSuccess) s = batch_wait(b);
-      else s = fail(SP_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+      if (e == cudaSuccess) st = batch_wait(b);
+      else st = fail(SP_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
       float ms = 0.0f;
-      if (s == SP_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+      if (st == SP_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
         ms_min = rep == 0 ? ms : std::min(ms_min, ms);
     }
-    if (s == SP_OK) times.emplace_back(cpw, ms_min);
-    if (s == SP_OK && (!any || ms_min < best_ms)) {
-      best = cpw;
-      best_ms = ms_min;
-      any = true;
+    *best_of3 = ms_min;
+    return st;
+  };
+  // A change is kept only if it is more than 3 % faster than the best so far
+  // (inference frames leave out learning, so small gains are not trusted).
+  constexpr float kGain = 1.03f;
+  const size_t n = b->members.size();
+  std::vector<uint32_t> cpw(n, 0u);
+  b->sched = 0u;
+  s = batch_relayout(b, cpw);
+  float best_ms = 0.0f;
+  if (s == SP_OK) s = time_layout(&best_ms);
+  const uint32_t candidates[] = {2u, 4u, 8u, 16u};
+  // 1. one split for every member
+  uint32_t uniform = 0u;
+  for (uint32_t c : candidates) {
+    if (s != SP_OK) break;
+    s = batch_relayout(b, std::vector<uint32_t>(n, c));
+    float ms = 0.0f;
+    if (s == SP_OK) s = time_layout(&ms);
+    if (s == SP_OK && ms * kGain < best_ms) {
+      best_ms = ms;
+      uniform = c;
     }
   }
-  // inference frames leave out the learning pass, so a split must beat the
-  // members' default by more than 3 % to replace it
-  for (auto& t : times)
-    if (t.first == 0u && t.second <= best_ms * 1.03f) best = 0u;
-  if (s == SP_OK) s = batch_relayout(b, best);
+  std::fill(cpw.begin(), cpw.end(), uniform);
+  if (s == SP_OK) s = batch_relayout(b, cpw);
+  // 2. the compiled schedule (resident CTAs per SM x columns in flight)
+  uint32_t best_sched = 0u;
+  for (uint32_t i = 1; persistent && s == SP_OK && i < sp::batch_schedule_count(); ++i) {
+    b->sched = i;
+    float ms = 0.0f;
+    s = time_layout(&ms);
+    if (s == SP_OK && ms * kGain < best_ms) {
+      best_ms = ms;
+      best_sched = i;
+    }
+  }
+  b->sched = best_sched;
+  // 3. the split of each bucket of members (members of one bucket share it),
+  // largest bucket first, the others as chosen so far
+  std::vector<uint32_t> bucket(n), count(6, 0u);
+  for (size_t i = 0; i < n; ++i) count[bucket[i] = tune_bucket(b->members[i])]++;
+  std::vector<uint32_t> order;
+  for (uint32_t k = 0; k < 6; ++k)
+    if (count[k]) order.push_back(k);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t x, uint32_t y) { return count[x] > count[y]; });
+  for (uint32_t k : order) {
+    if (order.size() < 2u) break;  // one bucket: step 1 has tried its splits
+    uint32_t keep = uniform;
+    for (uint32_t c : {0u, 2u, 4u, 8u, 16u}) {
+      if (s != SP_OK || c == uniform) continue;
+      std::vector<uint32_t> trial = cpw;
+      for (size_t i = 0; i < n; ++i)
+        if (bucket[i] == k) trial[i] = c;
+      s = batch_relayout(b, trial);
+      float ms = 0.0f;
+      if (s == SP_OK) s = time_layout(&ms);
+      if (s == SP_OK && ms * kGain < best_ms) {
+        best_ms = ms;
+        keep = c;
+      }
+    }
+    for (size_t i = 0; i < n; ++i)
+      if (bucket[i] == k) cpw[i] = keep;
+  }
+  if (s == SP_OK) s = batch_relayout(b, cpw);
   off = 0;
   for (auto& d : duty) {
     cudaMemcpyAsync(d.first, d_keep + off, d.second, cudaMemcpyDeviceToDevice, b->stream);
@@ -2156,8 +2220,62 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
   if (d_keep) cudaFree(d_keep);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (s == SP_OK && cols_per_warp) *cols_per_warp = best;
+  if (s == SP_OK && cols_per_warp) {
+    uint32_t one = cpw.empty() ? 0u : cpw[0];
+    for (uint32_t c : cpw)
+      if (c != one) one = SP_MIXED_SPLIT;
+    *cols_per_warp = one;
+  }
   return s;
+}
+
+SP_API sp_status sp_batch_schedule_list(uint32_t* ctas_per_sm, uint32_t* cols_in_flight,
+                                        uint32_t cap, uint32_t* count) {
+  const uint32_t n = sp::batch_schedule_count();
+  if (count) *count = n;
+  if (cap < n && (ctas_per_sm || cols_in_flight))
+    return fail(SP_EINVAL, "room for %u schedules needed, %u given", n, cap);
+  for (uint32_t i = 0; i < n; ++i)
+    sp::batch_schedule(i, ctas_per_sm ? ctas_per_sm + i : nullptr,
+                       cols_in_flight ? cols_in_flight + i : nullptr);
+  return SP_OK;
+}
+
+SP_API sp_status sp_batch_set_schedule(sp_batch* b, uint32_t ctas_per_sm, uint32_t cols_in_flight,
+                                       const uint32_t* member_cols_per_warp) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  uint32_t found = UINT32_MAX;
+  for (uint32_t i = 0; i < sp::batch_schedule_count(); ++i) {
+    uint32_t c = 0, f = 0;
+    sp::batch_schedule(i, &c, &f);
+    if (c == ctas_per_sm && f == cols_in_flight) found = i;
+  }
+  if (found == UINT32_MAX)
+    return fail(SP_ENOTSUP, "no compiled schedule of %u CTAs per SM x %u columns in flight",
+                ctas_per_sm, cols_in_flight);
+  std::vector<uint32_t> cpw(b->members.size(), 0u);
+  if (member_cols_per_warp)
+    for (size_t i = 0; i < cpw.size(); ++i) {
+      cpw[i] = member_cols_per_warp[i];
+      if (cpw[i] > 64u) return fail(SP_EINVAL, "member %zu: columns per warp above 64", i);
+    }
+  if (b->pending) return fail(SP_EBUSY, "learning is pending: set the schedule before learning");
+  DeviceGuard g(b->device);
+  sp_status s = batch_wait(b);
+  if (s != SP_OK) return s;
+  b->sched = found;
+  return batch_relayout(b, cpw);
+}
+
+SP_API sp_status sp_batch_schedule(const sp_batch* b, uint32_t* ctas_per_sm,
+                                   uint32_t* cols_in_flight, uint32_t* member_cols_per_warp) {
+  if (!b) return fail(SP_EINVAL, "NULL batch");
+  if (!sp::batch_schedule(b->sched, ctas_per_sm, cols_in_flight))
+    return fail(SP_EINVAL, "no such schedule");
+  if (member_cols_per_warp)
+    for (size_t i = 0; i < b->members.size(); ++i)
+      member_cols_per_warp[i] = i < b->member_cpw.size() ? b->member_cpw[i] : 0u;
+  return SP_OK;
 }
 
 SP_API sp_status sp_batch_set_device_wait_ns(sp_batch* b, uint64_t ns) {

@@ -144,8 +144,15 @@ struct BatchArgs {
 cudaError_t launch_batch_step(const BatchArgs& a, uint32_t n_ctas, uint32_t max_C,
                               cudaStream_t stream);
 // One persistent launch over r.n_frames batch frames (grid sized to the
-// resident CTAs); r.work and r.abort must be 0.
-cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream);
+// resident CTAs) with compiled schedule `schedule` (0: the default; out of
+// range: the default); r.work and r.abort must be 0.
+cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, uint32_t schedule,
+                             cudaStream_t stream);
+// The compiled schedules of the persistent batch pass: how many, and the
+// resident CTAs per SM and columns per warp in flight of schedule i (false
+// when i is out of range).
+uint32_t batch_schedule_count();
+bool batch_schedule(uint32_t i, uint32_t* ctas_per_sm, uint32_t* cols_in_flight);
 // Compact form of an SP's pools and connectivity (S <= 256), rows padded to
 // cS = S rounded up to a multiple of 32 synapses and laid out lane-strided
 // (see sp_step.cu): cbase[c] = min_s idx[c][s], 16-bit offsets idx[c][s] -

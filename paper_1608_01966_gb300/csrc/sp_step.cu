@@ -435,7 +435,7 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
 // lie in frame rows [y0, y0 + nr) (see above).  If the band's copy does not
 // complete in time the error word is set, the copy is waited for (bounded)
 // and the columns publish 0.
-template <bool STREAM>
+template <bool STREAM, int COLS = kWinCols>
 __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint32_t hi,
                                             uint32_t y0, uint32_t nr, uint32_t* dyn_smem,
                                             uint32_t* err) {
@@ -488,10 +488,10 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
     const uint32_t org = __ldg(a.worg + lo + i), ox = org & 0xffffu;
     s_org[i] = (((org >> 16) * wpr + (ox >> 5) - base) << 5) | (ox & 31u);
   }
-  uint4 bm[kWinCols];
-  auto load_group = [&](uint32_t c, uint4(&b)[kWinCols]) {
+  uint4 bm[COLS];
+  auto load_group = [&](uint32_t c, uint4(&b)[COLS]) {
 #pragma unroll
-    for (int j = 0; j < kWinCols; ++j) {
+    for (int j = 0; j < COLS; ++j) {
       const uint32_t cj = c + j * kStepWarps;
       b[j] = cj < hi ? ld_state<STREAM>(reinterpret_cast<const uint4*>(a.wbits + (uint64_t)cj * kWinWords) + lane)
                      : make_uint4(0u, 0u, 0u, 0u);
@@ -589,17 +589,17 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
   }
   __syncthreads();
 
-  // ---- the count: this warp's columns, kWinCols at a time --------------------
+  // ---- the count: this warp's columns, COLS at a time --------------------
   const uint32_t lane_off = (uint32_t)lane * wpr, row32 = 32u * wpr;
   const bool learners = a.mask_prev && s_nl != 0u;  // s_nl is stable after the barrier
-  for (uint32_t c = c0; c < hi; c += kWinCols * kStepWarps) {
+  for (uint32_t c = c0; c < hi; c += COLS * kStepWarps) {
 #if SP_WIN_PIPE
-    uint4 nx[kWinCols];
-    load_group(c + kWinCols * kStepWarps, nx);
+    uint4 nx[COLS];
+    load_group(c + COLS * kStepWarps, nx);
 #endif
-    uint32_t cnt[kWinCols];
+    uint32_t cnt[COLS];
 #pragma unroll
-    for (int j = 0; j < kWinCols; ++j) {
+    for (int j = 0; j < COLS; ++j) {
       const uint32_t cj = c + j * kStepWarps;
       const uint32_t li = (learners && cj < hi) ? s_lmap[cj - lo] : 0u;
       uint4 b = bm[j];
@@ -616,17 +616,17 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
     // lane j publishes the group's column j
     uint32_t mine = 0u;
 #pragma unroll
-    for (int j = 0; j < kWinCols; ++j) {
+    for (int j = 0; j < COLS; ++j) {
       const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
       mine = lane == j ? r : mine;
     }
-    if (lane < kWinCols && c + (uint32_t)lane * kStepWarps < hi)
+    if (lane < COLS && c + (uint32_t)lane * kStepWarps < hi)
       publish_overlap(a, c + (uint32_t)lane * kStepWarps, mine);
 #if SP_WIN_PIPE
 #pragma unroll
-    for (int j = 0; j < kWinCols; ++j) bm[j] = nx[j];
+    for (int j = 0; j < COLS; ++j) bm[j] = nx[j];
 #else
-    load_group(c + kWinCols * kStepWarps, bm);
+    load_group(c + COLS * kStepWarps, bm);
 #endif
   }
   __syncthreads();  // the band becomes the last CTA's working memory
@@ -636,7 +636,7 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
 // One frame of one SP, run by nb CTAs of which this is number bid.  With
 // STAGE, a CTA whose columns' state fits in stage_cap bytes of dynamic
 // shared memory stages it there by bulk copy first.
-template <int VEC, bool STREAM, bool STAGE = false>
+template <int VEC, bool STREAM, bool STAGE = false, int COLS = kCompactCols>
 __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint32_t nb,
                                           uint32_t* dyn_smem, uint32_t stage_cap = 0u,
                                           uint32_t* err = nullptr, uint32_t xspan_cap = 0u,
@@ -657,10 +657,10 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     return a.mask_prev && ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u);
   };
   if (STAGE && a.worg) {
-    window_item<STREAM>(a, c_lo, c_end, __ldg(a.wband + 2u * bid),
+    window_item<STREAM, COLS>(a, c_lo, c_end, __ldg(a.wband + 2u * bid),
                         __ldg(a.wband + 2u * bid + 1u), dyn_smem, err);
   } else if (STAGE && a.cidx) {
-    // compact form: kCompactCols columns per warp in flight; the input words
+    // compact form: COLS columns per warp in flight; the input words
     // the CTA's pools index are first copied to shared memory when they fit
     // (the copy overlaps the first group's loads), so the bit gathers read
     // shared memory instead of making one L1 lookup per lane
@@ -686,12 +686,12 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
                      : "memory");
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    uint4 o[kCompactCols];
-    uint32_t cb[kCompactCols], base[kCompactCols];
-    auto load_into = [&](uint32_t c0, uint4(&oo)[kCompactCols], uint32_t(&cc)[kCompactCols],
-                         uint32_t(&bb)[kCompactCols]) {
+    uint4 o[COLS];
+    uint32_t cb[COLS], base[COLS];
+    auto load_into = [&](uint32_t c0, uint4(&oo)[COLS], uint32_t(&cc)[COLS],
+                         uint32_t(&bb)[COLS]) {
 #pragma unroll
-      for (int j = 0; j < kCompactCols; ++j) {
+      for (int j = 0; j < COLS; ++j) {
         const uint32_t c = c0 + j * c_step;
         const bool ok = c < c_end;
         oo[j] = (ok && act)
@@ -706,17 +706,17 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
     auto load_group = [&](uint32_t c0) { load_into(c0, o, cb, base); };
     auto run_group = [&](uint32_t c0, auto count) {
 #pragma unroll
-      for (int j = 0; j < kCompactCols; ++j) {
+      for (int j = 0; j < COLS; ++j) {
         const uint32_t c = c0 + j * c_step;
         if (!padded && c < c_end && learning(c))
           cb[j] = compact_learn(a.perm, a.cidx, a.cbase, a.conn, a.x_prev, c, a.S, a.thr, a.inc,
                                 a.dec);
       }
-      uint32_t cnt[kCompactCols];
+      uint32_t cnt[COLS];
 #pragma unroll
-      for (int j = 0; j < kCompactCols; ++j) cnt[j] = count(base[j], o[j], cb[j]);
+      for (int j = 0; j < COLS; ++j) cnt[j] = count(base[j], o[j], cb[j]);
 #pragma unroll
-      for (int j = 0; j < kCompactCols; ++j) {
+      for (int j = 0; j < COLS; ++j) {
         const uint32_t c = c0 + j * c_step;
         const uint32_t r = __reduce_add_sync(kFull, cnt[j]);
         if (c < c_end && lane == 0) publish(c, r);
@@ -735,7 +735,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
         }
         return n;
       };
-      for (uint32_t c0 = c_first; c0 < c_end; c0 += kCompactCols * c_step) {
+      for (uint32_t c0 = c_first; c0 < c_end; c0 += COLS * c_step) {
         if (c0 != c_first) load_group(c0);
         run_group(c0, count_s);
       }
@@ -744,7 +744,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, uint32_t bid, uint3
       auto count_g = [&](uint32_t b, const uint4& q, uint32_t m) {
         return compact_count(a.x, b, q, m);
       };
-      for (uint32_t c0 = c_first; c0 < c_end; c0 += kCompactCols * c_step) {
+      for (uint32_t c0 = c_first; c0 < c_end; c0 += COLS * c_step) {
         load_group(c0);
         run_group(c0, count_g);
       }
@@ -999,7 +999,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_run_kernel(const BatchRunArgs r) {
+// MINB resident CTAs per SM (the register budget a thread gets) and COLS
+// columns per warp in flight: one compiled schedule of the persistent batch
+// pass (batch_schedule lists those compiled; the autotuner picks one).
+template <int MINB, int COLS>
+__global__ void __launch_bounds__(kStepThreads, MINB) sp_batch_run_kernel(const BatchRunArgs r) {
   extern __shared__ __align__(128) uint32_t dyn_smem[];
   __shared__ uint32_t s_t, s_k, s_go;
   const unsigned long long total = (unsigned long long)r.items_per_frame * r.n_frames;
@@ -1090,13 +1094,40 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_ru
     a.radius = d.radius;
     const uint32_t bid = k - d.cta_first;
     if ((a.S & 3u) == 0u || a.cidx)
-      step_body<4, true, true>(a, bid, d.n_ctas, dyn_smem, r.stage_cap, r.err, r.xspan_cap,
-                               r.done + inst, r.epoch + t + 1u);
+      step_body<4, true, true, COLS>(a, bid, d.n_ctas, dyn_smem, r.stage_cap, r.err,
+                                     r.xspan_cap, r.done + inst, r.epoch + t + 1u);
     else
-      step_body<1, true>(a, bid, d.n_ctas, dyn_smem, 0u, nullptr, 0u, r.done + inst,
-                         r.epoch + t + 1u);
+      step_body<1, true, false, COLS>(a, bid, d.n_ctas, dyn_smem, 0u, nullptr, 0u,
+                                      r.done + inst, r.epoch + t + 1u);
     __syncthreads();  // shared memory is reused by the next item
   }
+}
+
+namespace {
+
+// The compiled schedules of the persistent batch pass; entry 0 is the default.
+struct RunSchedule {
+  void (*kernel)(const BatchRunArgs);
+  uint32_t ctas_per_sm, cols_in_flight;
+};
+const RunSchedule kRunSchedules[] = {
+    {sp_batch_run_kernel<SP_BATCH_MIN_BLOCKS, kCompactCols>, SP_BATCH_MIN_BLOCKS, kCompactCols},
+    {sp_batch_run_kernel<12, 2>, 12, 2},
+    {sp_batch_run_kernel<8, 4>, 8, 4},
+    {sp_batch_run_kernel<8, 6>, 8, 6},
+    {sp_batch_run_kernel<10, 2>, 10, 2},
+};
+constexpr uint32_t kNumRunSchedules = sizeof(kRunSchedules) / sizeof(kRunSchedules[0]);
+
+}  // namespace
+
+uint32_t batch_schedule_count() { return kNumRunSchedules; }
+
+bool batch_schedule(uint32_t i, uint32_t* ctas_per_sm, uint32_t* cols_in_flight) {
+  if (i >= kNumRunSchedules) return false;
+  if (ctas_per_sm) *ctas_per_sm = kRunSchedules[i].ctas_per_sm;
+  if (cols_in_flight) *cols_in_flight = kRunSchedules[i].cols_in_flight;
+  return true;
 }
 
 cudaError_t kernels_init() {
@@ -1107,8 +1138,9 @@ cudaError_t kernels_init() {
   e = cudaFuncSetAttribute(sp_batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sp_batch_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           bytes);
+  for (uint32_t i = 0; i < kNumRunSchedules && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(kRunSchedules[i].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sp_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               bytes);
@@ -1278,20 +1310,21 @@ cudaError_t launch_xspan(const uint32_t* idx, uint32_t C, uint32_t S, uint32_t n
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, cudaStream_t stream) {
+cudaError_t launch_batch_run(const BatchRunArgs& r, uint32_t max_C, uint32_t schedule,
+                             cudaStream_t stream) {
+  const RunSchedule& rs = kRunSchedules[schedule < kNumRunSchedules ? schedule : 0u];
   const size_t smem = std::max<size_t>(step_smem_bytes(max_C),
                                        std::max(std::max(r.stage_cap, r.xspan_cap), r.win_cap));
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sp_batch_run_kernel, kStepThreads,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rs.kernel, kStepThreads, smem);
   if (e != cudaSuccess) return e;
   const unsigned long long total = (unsigned long long)r.items_per_frame * r.n_frames;
   const unsigned long long resident = (unsigned long long)std::max(1, sms * std::max(1, per_sm));
   const uint32_t grid = (uint32_t)std::min(total, resident);
-  sp_batch_run_kernel<<<grid, kStepThreads, smem, stream>>>(r);
+  rs.kernel<<<grid, kStepThreads, smem, stream>>>(r);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

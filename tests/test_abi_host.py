@@ -137,3 +137,20 @@ def test_load_generator_rejects_invalid_arguments():
     with pytest.raises(spg.SpError) as e:
         spg.sp_loadgen_run(1, [0], [np.zeros((1, 4), np.uint32)], -1.0, 1.0)
     assert e.value.status == 1
+
+
+def test_compiled_batch_schedules_are_listed():
+    """The persistent batch pass is compiled in several schedules (resident
+    CTAs per SM x columns per warp in flight) for the autotuner to choose
+    from; the default (10 x 4) comes first and no pair repeats."""
+    import paper_1608_01966_gb300 as spg
+    lst = spg.sp_batch_schedule_list()
+    assert lst[0] == (10, 4)
+    assert len(set(lst)) == len(lst) >= 4
+    assert all(8 <= c <= 12 and 2 <= f <= 8 for c, f in lst)
+    with pytest.raises(spg.SpError):  # no room for the list
+        import ctypes as ct
+        a = (ct.c_uint32 * 1)()
+        spg._binding._check(spg.lib().sp_batch_schedule_list(a, a, 1, None), "list")
+    with pytest.raises(spg.SpError):  # no such batch
+        spg.sp_batch_set_schedule(None, 10, 4)

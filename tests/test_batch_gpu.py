@@ -19,12 +19,18 @@ def _member_frames(cases, dens, n):
     return [wl.bernoulli_frames(i, c.n_in, dens[i], n) for i, c in enumerate(cases)]
 
 
-def _run_batch(cases, frames_u8, learn, calls, boosts=None):
-    """Create handles + batch, run the batch frames split into `calls` (list of
-    frame counts) through sp_batch_compute_overlaps_device, return per-member
-    active [n][C], final perms, and overlaps of every frame [n][C]."""
+def _run_batch(cases, frames_u8, learn, calls, boosts=None, schedule=None):
+    """Create handles + batch (schedule: (ctas_per_sm, cols_in_flight,
+    member columns per warp) to pin, or None), run the batch frames split
+    into `calls` (list of frame counts) through
+    sp_batch_compute_overlaps_device, return per-member active [n][C], final
+    perms, and overlaps of every frame [n][C]."""
     hs = [spg.sp_create_from_state(c.config(), c.idx, c.perm, c.boost) for c in cases]
     b = spg.sp_batch_create(hs)
+    if schedule is not None:
+        spg.sp_batch_set_schedule(b, *schedule)
+        assert spg.sp_batch_schedule(b, len(hs)) == (schedule[0], schedule[1],
+                                                     list(schedule[2] or [0] * len(hs)))
     info = spg.sp_batch_get_info(b)
     fo, mo = spg.sp_batch_offsets(b)
     oo, ow = spg.sp_batch_overlap_offsets(b)
@@ -105,6 +111,37 @@ def test_batch_uneven_shapes_and_modes():
             frames.append(wl.bernoulli_frames(i, c.n_in, dens[i], 12))
     acts, perms, ovs = _run_batch(cases, frames, True, [3, 9])
     _check(cases, frames, True, acts, perms, ovs, "uneven")
+
+
+def _schedules():
+    try:
+        return spg.sp_batch_schedule_list()
+    except Exception:  # library not built: the test fails when it runs instead
+        return [(10, 4)]
+
+
+@pytest.mark.parametrize("sched", _schedules())
+@pytest.mark.parametrize("split", ["default", "mixed"])
+def test_batch_every_compiled_schedule(sched, split):
+    """Every compiled schedule of the persistent pass (resident CTAs per SM x
+    columns per warp in flight), with each member's default split and with
+    per-member splits of 2 to 16 columns per warp: window-form, compact-form
+    and full-form members learning over runs of several frames, against the
+    oracle frame by frame."""
+    cases = [wl.frame_case(seed=wl.BASE_SEED + 700 + i) for i in range(2)]
+    unv, dens = wl.uneven_cases(4, c_range=(128, 1500), n_in_range=(256, 4096))
+    cases += unv
+    rag = wl.Case("ragged", 1000, 1, 300, 17, synth.pool_uniform(3, 300, 17, 1000),
+                  synth.perm_uniform(4, (300, 17), 0.1, 0.3), synth.perm_uniform(5, (300,), 0.5, 2.0),
+                  k=9, min_overlap=2)
+    cases.append(rag)
+    frames = [wl.blob_frames(10, seed=wl.BASE_SEED + 700 + i) for i in range(2)]
+    frames += [wl.bernoulli_frames(i, c.n_in, dens[i], 10) for i, c in enumerate(unv)]
+    frames.append(wl.bernoulli_frames(9, rag.n_in, 0.3, 10))
+    per = None if split == "default" else [(2, 4, 8, 16)[i % 4] for i in range(len(cases))]
+    acts, perms, ovs = _run_batch(cases, frames, True, [1, 4, 5],
+                                  schedule=(sched[0], sched[1], per))
+    _check(cases, frames, True, acts, perms, ovs, f"schedule {sched} {split}")
 
 
 @pytest.mark.parametrize("cpw", ["1", "4", "8"])
@@ -242,7 +279,11 @@ def test_batch_autotune_keeps_state():
     fw = (info["frame_words"] + 3) // 4 * 4
     d_tune = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in tune], fo, fw).view(np.int32)).cuda()
     cpw = spg.sp_batch_autotune(b, d_tune, 3, fw)
-    assert cpw in (0, 2, 4, 8, 16)
+    assert cpw in (0, 2, 4, 8, 16, spg.SP_MIXED_SPLIT)
+    ctas, cols, per = spg.sp_batch_schedule(b, len(hs))
+    assert (ctas, cols) in spg.sp_batch_schedule_list()
+    assert all(c in (0, 2, 4, 8, 16) for c in per)
+    assert cpw == spg.SP_MIXED_SPLIT or per == [cpw] * len(hs)
     d_real = torch.from_numpy(wl.batch_frames([wl.pack(f) for f in real], fo, fw).view(np.int32)).cuda()
     mw = info["mask_words"]
     dm = torch.zeros((6, mw), dtype=torch.int32, device="cuda")
