@@ -12,12 +12,17 @@
 //   1. the input band its columns' pools cover (a contiguous word range of
 //      the packed frame) arrives in shared memory by cp.async, issued during
 //      the previous frame (double-buffered);
-//   2. Alg. 1 for its columns from shared memory, one warp per column;
-//      the boosted overlaps are published in shared memory;
+//   2. Alg. 1 for its columns from shared memory, each warp counting four
+//      columns side by side; the boosted overlaps are published in shared
+//      memory;
 //   3. one cluster barrier (barrier.cluster arrive.release / wait.acquire);
-//   4. every CTA gathers all C overlaps through DSMEM and runs Alg. 2 on
-//      them (the same deterministic answer in every CTA), keeping the
-//      decisions for its own columns;
+//   4. with global inhibition and unit boosts (counts are the overlaps),
+//      each CTA has published a count histogram of its columns in step 2;
+//      warp 0 of every CTA reads the cluster's histograms from the top, 32
+//      bins a round, until it reaches the k-th largest count, and decides its
+//      own columns; otherwise every CTA gathers all C overlaps through DSMEM
+//      and runs Alg. 2 on them (the same deterministic answer in every CTA),
+//      keeping the decisions for its own columns;
 //   5. learning (Section 1.1) of its winning columns in shared memory, with
 //      the frame band still resident.
 //
@@ -50,6 +55,7 @@ using dev::kFull;
 using dev::learn_one;
 
 constexpr int kSeqWarps = kSeqThreads / 32;
+constexpr int kSeqCols = 4;  // columns a warp counts side by side
 
 __device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gmem_src) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
@@ -78,7 +84,7 @@ __device__ __forceinline__ void issue_band(uint32_t* dst, const uint32_t* frame,
 
 // Shared-memory layout of one CTA (all offsets in 4-byte words).
 struct SeqLayout {
-  uint32_t idx, perm, boost, band, ov, raw, hpub, gsum, psum, all, hist, mask, dirty, total;
+  uint32_t idx, perm, boost, band, ov, raw, hstride, hpub, all, hist, mask, dirty, total;
   __host__ __device__ SeqLayout(uint32_t Cq, uint32_t S, uint32_t band_max, uint32_t C) {
     const uint32_t CqS = Cq * S;
     idx = 0;
@@ -87,10 +93,9 @@ struct SeqLayout {
     band = (boost + Cq + 3u) & ~3u;  // 16-byte aligned
     ov = band + 2u * band_max;
     raw = ov + 2u * Cq;
-    hpub = raw + Cq;                  // [2][S + 1] published count histograms
-    gsum = hpub + 2u * (S + 1u);      // [S + 1] cluster-wide histogram
-    psum = gsum + (S + 1u);           // [S + 1] histogram of the lower-ranked CTAs
-    all = psum + (S + 1u);
+    hstride = (S + 4u) & ~3u;         // bins 0..S, rounded up to whole 16-byte words
+    hpub = (raw + Cq + 3u) & ~3u;     // [2][hstride] published count histograms, bin 0 the max
+    all = hpub + 2u * hstride;
     hist = all + C;
     const uint32_t hw = (S + 1u) > 256u ? (S + 1u) : 256u;
     mask = hist + hw;
@@ -99,73 +104,86 @@ struct SeqLayout {
   }
 };
 
-// Global inhibition with unit boosts, decided by each CTA for its own
-// columns from count histograms.  g/p are this thread's sums over its bins
-// (a contiguous descending run, see the caller) of the cluster-wide
-// histogram and of the lower-ranked CTAs' histogram.  One block scan gives,
-// per bin, the columns strictly above it; the k-th largest count T, the
-// number of T-valued columns that still win (`need`), and how many winners
-// and ties lie in lower-ranked CTAs follow.  A second scan ranks this CTA's
-// own ties in index order.  s_raw holds each own column's count (0 below
-// min_overlap); one column per thread.  Sets this CTA's words of s_mask;
-// when list != nullptr writes this CTA's slots of the ascending winner list.
-// Returns the cluster-wide number of winners.
-__device__ uint32_t decide_unit_global(uint32_t g, uint32_t p, uint32_t top, uint32_t nbins,
-                                       const uint32_t* gsum, const uint32_t* psum,
-                                       const uint32_t* s_raw, uint32_t k, uint32_t c0,
-                                       uint32_t nc, uint32_t* s_mask, uint32_t* list,
-                                       uint32_t* sh, uint32_t* s2) {
-  constexpr int NW = kSeqThreads / 32;
-  const uint32_t t = threadIdx.x;
-  const int lane = t & 31, warp = t >> 5;
-  uint32_t ex_g, ex_p, nz_tot, p_tot;
-  dev::block_scan2<NW>(g, p, ex_g, ex_p, nz_tot, p_tot, sh);
-  if (k == 0u) {
-    if (t == 0) {
-      s2[0] = 0xffffffffu;  // nobody wins
-      s2[1] = s2[2] = s2[3] = 0u;
-    }
-  } else if (nz_tot <= k) {
-    if (t == 0) {
-      s2[0] = 0u;  // every surviving column wins
-      s2[1] = 0u;
-      s2[2] = p_tot;
-      s2[3] = 0u;
-    }
-  } else if (ex_g < k && ex_g + g >= k) {
-    // this thread's bins hold the k-th largest count
-    uint32_t acc = ex_g, accp = ex_p;
-    for (uint32_t b = 0; b < nbins; ++b) {
-      const uint32_t bin = top - b;
-      const uint32_t hb = gsum[bin];
-      if (acc + hb >= k) {
-        s2[0] = bin;
-        s2[1] = k - acc;     // ties at T that still win
-        s2[2] = accp;        // lower CTAs' columns strictly above T
-        s2[3] = psum[bin];   // lower CTAs' columns equal to T
+// Global inhibition with unit boosts, decided by warp 0 of each CTA for the
+// CTA's own columns from the count histograms the CTAs publish in shared
+// memory (hpub: bin b holds how many of the publishing CTA's columns count b;
+// bin 0 holds its largest count).  The warp reads the Q largest counts, then
+// gathers 32 bins at a time from the top (lane l: bin top - l, from every
+// CTA; usually one or two rounds reach the k-th largest count T), with one
+// warp scan per round for the columns above each bin, in the whole cluster
+// and in the lower-ranked CTAs.  That gives T, the ties at T that still win
+// (`need`) and the winners and ties of the lower-ranked CTAs.  The CTA's
+// columns (count in s_raw, 0 below min_overlap) are then decided 32 at a
+// time: a ballot ranks the ties in column order, another gives the mask
+// word.  When list != nullptr the winners' slots of the ascending list are
+// written.  Returns the cluster-wide number of winners (every lane gets it).
+template <typename Cluster>
+__device__ uint32_t decide_unit_global(const Cluster& cluster, const uint32_t* hpub,
+                                       const uint32_t* s_raw, uint32_t k, uint32_t q,
+                                       uint32_t c0, uint32_t nc, uint32_t* s_mask,
+                                       uint32_t* list) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t Q = cluster.num_blocks();
+  const uint32_t top0 = __reduce_max_sync(kFull, lane < Q ? cluster.map_shared_rank(hpub, lane)[0] : 0u);
+  // T: 0xffffffff nobody wins; 0 every counted column wins (at most k)
+  uint32_t T = 0xffffffffu, need = 0u, above_lower = 0u, ties_lower = 0u;
+  uint32_t acc_g = 0u, acc_p = 0u;  // columns above the current round's bins
+  if (k != 0u) {
+    T = 0u;                           // reaching bin 0: at most k counted columns
+    for (uint32_t top = top0; top >= 1u; top = top > 32u ? top - 32u : 0u) {
+      const uint32_t bin = top >= lane + 1u ? top - lane : 0u;  // 0: past the last bin
+      uint32_t v[kSeqMaxCluster];
+#pragma unroll
+      for (uint32_t r = 0; r < kSeqMaxCluster; ++r)
+        v[r] = (r < Q && bin != 0u) ? cluster.map_shared_rank(hpub, r)[bin] : 0u;
+      uint32_t g = 0u, p = 0u;
+#pragma unroll
+      for (uint32_t r = 0; r < kSeqMaxCluster; ++r) {
+        g += v[r];
+        p += r < q ? v[r] : 0u;
+      }
+      uint32_t ig = g, ip = p;  // inclusive sums from the top
+#pragma unroll
+      for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t yg = __shfl_up_sync(kFull, ig, o), yp = __shfl_up_sync(kFull, ip, o);
+        if (lane >= o) {
+          ig += yg;
+          ip += yp;
+        }
+      }
+      const uint32_t hit = __ballot_sync(kFull, acc_g + ig - g < k && acc_g + ig >= k);
+      if (hit) {
+        const int src = __ffs(hit) - 1;
+        T = __shfl_sync(kFull, bin, src);
+        need = k - (acc_g + __shfl_sync(kFull, ig - g, src));
+        above_lower = acc_p + __shfl_sync(kFull, ip - p, src);
+        ties_lower = __shfl_sync(kFull, p, src);
         break;
       }
-      acc += hb;
-      accp += psum[bin];
+      acc_g += __shfl_sync(kFull, ig, 31);
+      acc_p += __shfl_sync(kFull, ip, 31);
     }
+    if (T == 0u) above_lower = acc_p;  // every counted column of the lower CTAs wins
   }
-  __syncthreads();
-  const uint32_t T = s2[0], need = s2[1], above_lower = s2[2], ties_lower = s2[3];
   const bool real_T = T != 0u && T != 0xffffffffu;
-  const uint32_t r = t < nc ? s_raw[t] : 0u;
-  const uint32_t tie = (real_T && r == T) ? 1u : 0u;
-  uint32_t tie_ex, e1, tie_tot, z;
-  dev::block_scan2<NW>(tie, 0u, tie_ex, e1, tie_tot, z, sh);
-  const bool win = r != 0u && T != 0xffffffffu &&
-                   (T == 0u || r > T || (tie && ties_lower + tie_ex < need));
-  const uint32_t wb = __ballot_sync(dev::kFull, win);
-  if (lane == 0 && (uint32_t)warp * 32u < nc) s_mask[(c0 >> 5) + warp] = wb;
-  if (list) {
-    uint32_t w_ex, e2, w_tot, z2;
-    dev::block_scan2<NW>(win ? 1u : 0u, 0u, w_ex, e2, w_tot, z2, sh);
-    if (win) list[above_lower + min(ties_lower, need) + w_ex] = c0 + t;
+  const uint32_t base = above_lower + min(ties_lower, need);  // this CTA's first list slot
+  uint32_t ties_before = 0u, wins_before = 0u;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t j = 0; j < nc; j += 32u) {
+    const uint32_t r = j + lane < nc ? s_raw[j + lane] : 0u;
+    const bool tie = real_T && r == T;
+    const uint32_t tm = __ballot_sync(kFull, tie);
+    const bool win = r != 0u && T != 0xffffffffu &&
+                     (T == 0u || r > T ||
+                      (tie && ties_lower + ties_before + (uint32_t)__popc(tm & lt) < need));
+    const uint32_t wm = __ballot_sync(kFull, win);
+    if (lane == 0u) s_mask[(c0 >> 5) + (j >> 5)] = wm;
+    if (list && win) list[base + wins_before + (uint32_t)__popc(wm & lt)] = c0 + j + lane;
+    ties_before += (uint32_t)__popc(tm);
+    wins_before += (uint32_t)__popc(wm);
   }
-  return T == 0xffffffffu ? 0u : (T == 0u ? nz_tot : k);
+  // T = 0: every counted column wins, acc_g of them (every bin was summed)
+  return T == 0xffffffffu ? 0u : (T == 0u ? acc_g : k);
 }
 
 __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const SeqArgs a) {
@@ -188,8 +206,6 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
   float* s_ov = reinterpret_cast<float*>(sm + L.ov);
   uint32_t* s_raw = sm + L.raw;
   uint32_t* s_hpub = sm + L.hpub;
-  uint32_t* s_gsum = sm + L.gsum;
-  uint32_t* s_psum = sm + L.psum;
   uint32_t* s_all = sm + L.all;
   uint32_t* s_hist = sm + L.hist;
   uint32_t* s_mask = sm + L.mask;
@@ -213,7 +229,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
   }
   for (uint32_t i = t; i < nc; i += kSeqThreads) s_boost[i] = __ldg(a.boost + c0 + i);
   for (uint32_t i = t; i < Cq / 32u; i += kSeqThreads) s_dirty[i] = 0u;
-  for (uint32_t i = t; i < 2u * (S + 1u); i += kSeqThreads) s_hpub[i] = 0u;
+  for (uint32_t i = t; i < 2u * L.hstride; i += kSeqThreads) s_hpub[i] = 0u;
   const bool fast = a.inhibition == 0u && a.unit_boost != 0u;
   // input band of this CTA: the 16-byte aligned word range covering its pools
   uint32_t mn = 0xffffffffu, mx = 0u;
@@ -271,25 +287,44 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
                  w_lo, nbw, a.vec16);
 
     // ---- Alg. 1 for this CTA's columns --------------------------------------
-    uint32_t* hpub = s_hpub + par * (S + 1u);
-    for (uint32_t lc = warp; lc < nc; lc += kSeqWarps) {
-      const uint32_t* ri = s_idx + lc * S;
-      const float* rp = s_perm + lc * S;
-      uint32_t cnt = 0;
+    // warp w counts columns w, w + 16, w + 32, w + 48 (kSeqCols of them) side
+    // by side, so the loads of all four are in flight together; lane j then
+    // publishes column j's count
+    uint32_t* hpub = s_hpub + par * L.hstride;
+    for (uint32_t lc0 = warp; lc0 < nc; lc0 += kSeqWarps * kSeqCols) {
+      uint32_t cnt[kSeqCols];
+#pragma unroll
+      for (int j = 0; j < kSeqCols; ++j) {
+        const uint32_t lc = lc0 + (uint32_t)j * kSeqWarps;
+        cnt[j] = 0u;
+        if (lc < nc) {
+          const uint32_t* ri = s_idx + lc * S;
+          const float* rp = s_perm + lc * S;
 #pragma unroll 8
-      for (uint32_t s = lane; s < S; s += 32) {
-        const uint32_t id = ri[s];
-        const uint32_t w = (id >> 5) - w_lo;
-        cnt += (rp[s] >= a.thr) ? ((band[w] >> (id & 31u)) & 1u) : 0u;
+          for (uint32_t s = lane; s < S; s += 32) {
+            const uint32_t id = ri[s];
+            const uint32_t w = (id >> 5) - w_lo;
+            cnt[j] += (rp[s] >= a.thr) ? ((band[w] >> (id & 31u)) & 1u) : 0u;
+          }
+        }
       }
-      cnt = __reduce_add_sync(kFull, cnt);
-      if (lane == 0) {
-        const bool keep = cnt >= a.min_overlap && cnt != 0u;
-        s_raw[lc] = keep ? cnt : 0u;
+      uint32_t mine = 0u;
+#pragma unroll
+      for (int j = 0; j < kSeqCols; ++j) {
+        const uint32_t c = __reduce_add_sync(kFull, cnt[j]);
+        if (lane == (uint32_t)j) mine = c;
+      }
+      const uint32_t lc = lc0 + lane * kSeqWarps;
+      if (lane < (uint32_t)kSeqCols && lc < nc) {
+        const bool keep = mine >= a.min_overlap && mine != 0u;
+        s_raw[lc] = keep ? mine : 0u;
         if (fast) {
-          if (keep) atomicAdd(hpub + cnt, 1u);
+          if (keep) {
+            atomicAdd(hpub + mine, 1u);
+            atomicMax(hpub, mine);  // bin 0: this CTA's largest count
+          }
         } else {
-          ov_pub[lc] = dev::boosted(cnt, a.min_overlap, s_boost[lc]);
+          ov_pub[lc] = dev::boosted(mine, a.min_overlap, s_boost[lc]);
         }
       }
     }
@@ -297,35 +332,12 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sp_seq_cluster_kernel(const Se
     const bool last = f + 1u == a.n_frames;
     uint32_t total;
     if (fast) {
-      // cluster-wide and lower-rank count histograms; thread t owns the
-      // descending run of bins top .. top - nbins + 1 (bins 1..S)
-      const uint32_t pb = (S + kSeqThreads - 1u) / kSeqThreads;
-      const uint32_t top = S >= t * pb ? S - t * pb : 0u;
-      const uint32_t nbins = top == 0u ? 0u : min(pb, top);
-      uint32_t g = 0, p = 0;
-      const uint32_t Q = cluster.num_blocks();
-      for (uint32_t b = 0; b < nbins; ++b) {
-        const uint32_t bin = top - b;
-        // issue every remote load before the first use
-        uint32_t v[kSeqMaxCluster];
-#pragma unroll
-        for (uint32_t r = 0; r < kSeqMaxCluster; ++r)
-          v[r] = r < Q ? cluster.map_shared_rank(hpub, r)[bin] : 0u;
-        uint32_t gb = 0, pbn = 0;
-#pragma unroll
-        for (uint32_t r = 0; r < kSeqMaxCluster; ++r) {
-          gb += v[r];
-          pbn += r < q ? v[r] : 0u;
-        }
-        s_gsum[bin] = gb;
-        s_psum[bin] = pbn;
-        g += gb;
-        p += pbn;
-      }
-      total = decide_unit_global(g, p, top, nbins, s_gsum, s_psum, s_raw, a.k, c0, nc, s_mask,
-                                 last ? a.result + 1 : nullptr, sh, s2);
+      total = 0u;
+      if (warp == 0)
+        total = decide_unit_global(cluster, hpub, s_raw, a.k, q, c0, nc, s_mask,
+                                   last ? a.result + 1 : nullptr);
       // the previous frame's published histogram is no longer read by anyone
-      for (uint32_t b = t; b <= S; b += kSeqThreads) s_hpub[(par ^ 1u) * (S + 1u) + b] = 0u;
+      for (uint32_t b = t; b < L.hstride; b += kSeqThreads) s_hpub[(par ^ 1u) * L.hstride + b] = 0u;
     } else {
 
     // ---- gather all overlaps through DSMEM -------------------------------------
