@@ -501,6 +501,14 @@ __device__ __forceinline__ void window_item(const StepArgs& a, uint32_t lo, uint
   if (!a.mask_prev) {
     load_group(c0, bm);  // in flight during the band copy
   } else {
+    // the first group's bitmaps are asked of L2 during the band copy and the
+    // learning (four 128-byte lines a column)
+#pragma unroll
+    for (int j = 0; j < COLS; ++j) {
+      const uint32_t cj = c0 + j * kStepWarps;
+      if (cj < hi && lane < 4)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.wbits + (uint64_t)cj * kWinWords + lane * 32u));
+    }
     for (uint32_t i = t; i < n; i += kStepThreads) {
       const uint32_t c = lo + i;
       if ((__ldcg(a.mask_prev + (c >> 5)) >> (c & 31u)) & 1u) {
