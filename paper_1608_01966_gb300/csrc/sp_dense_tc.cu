@@ -652,10 +652,14 @@ __global__ void __launch_bounds__(256) sp_conn_image_kernel(const DenseLaunch L)
 // X[f][i] = bit i of frame f as e4m3 {0, 1}; bits at or past K are zero
 // whatever the frame's unused high bits hold.
 __global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L) {
-  // the product may be scheduled now (it waits for this grid); the image is
-  // written only once the previous run has finished with it
+  // the product may be scheduled now (it waits for this grid).  The image is
+  // written at once: this grid starts only after the previous kernel on the
+  // stream let it, and a run's selection does so only after its own wait on
+  // that run's product, the image's last reader.  The wait for the previous
+  // kernel comes at the end, so that the product, which waits for this grid,
+  // also finds the previous run's selection complete before it overwrites
+  // the overlaps the selection reads.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   DenseArgs a;
   if (L.many)
     a = L.many[blockIdx.y];
@@ -676,6 +680,7 @@ __global__ void __launch_bounds__(256) sp_frame_image_kernel(const DenseLaunch L
         make_uint4(fp8_nibble(bits & 15u), fp8_nibble((bits >> 4) & 15u),
                    fp8_nibble((bits >> 8) & 15u), fp8_nibble(bits >> 12));
   }
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
 }  // namespace
