@@ -289,7 +289,7 @@ SP_API void sp_batch_destroy(sp_batch* b);
 SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out);
 
 /* Autotune the batch pass's schedule and CTA shapes on the caller's frames:
- * run n_frames inference frames from d_frames (device batch frames laid out
+ * run n_frames learning frames from d_frames (device batch frames laid out
  * as for sp_batch_compute_device, stride in words) three times per candidate
  * and keep the fastest, in three steps:
  *   1. one CTA split for every member: each member's default, or 4 warps x
@@ -300,14 +300,17 @@ SP_API sp_status sp_batch_get_info(const sp_batch* b, sp_batch_info* out);
  *   3. when the members fall in several buckets (synapses per column <= 32,
  *      <= 128 or more x input of at most 4096 bits or more), the split of
  *      each bucket, largest bucket first, the others as chosen so far.
- * A candidate replaces the best so far only if more than 3 % faster
- * (inference frames leave out learning).  n_frames == 1 tunes the splits of
- * single-frame launches only.  *cols_per_warp (nullable) receives the
- * columns per warp chosen when every member has the same (0: the defaults),
- * else SP_MIXED_SPLIT.  The members' permanences, learning and duty cycles
- * are left as they were; their last-frame overlaps and active columns are
- * those of the last tuning frame.  Tuning is a property of the workload and
- * the device (Section 4.4's sweeps show the cost moving with columns and
+ * A candidate replaces the best so far only if more than 3 % faster.  The
+ * state learning writes (permanences, the derived window and compact forms)
+ * and the duty cycles are copied aside on the device first and put back
+ * after (a temporary allocation of that size); if it cannot be had, or
+ * n_frames == 1 (which tunes the splits of single-frame launches only), the
+ * frames are timed as inference.  So the members' permanences, learning and
+ * duty cycles are left as they were; their last-frame overlaps and active
+ * columns are those of the last tuning frame.  *cols_per_warp (nullable)
+ * receives the columns per warp chosen when every member has the same (0:
+ * the defaults), else SP_MIXED_SPLIT.  Tuning is a property of the workload
+ * and the device (Section 4.4's sweeps show the cost moving with columns and
  * synapses), so call it once after sp_batch_create.  SP_EBUSY if learning is
  * pending (tune before the first learning frame); blocks until done (bounded
  * waits). */

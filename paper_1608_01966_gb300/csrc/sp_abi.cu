@@ -2074,18 +2074,36 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
   DeviceGuard g(b->device);
   sp_status s = batch_wait(b);
   if (s != SP_OK) return s;
-  // duty cycles advance on every frame: keep a copy and put it back after
-  std::vector<std::pair<float*, size_t>> duty;
-  size_t duty_bytes = 0;
-  for (sp_handle* h : b->members)
+  // The tuning frames learn, as the batch's own frames do: the state that
+  // learning writes (permanences, window bitmaps, compact connected bits)
+  // and the duty cycles, which advance on every frame, are copied aside and
+  // put back after.  Without room for the copy the frames are timed as
+  // inference and only the duty cycles are kept.
+  std::vector<std::pair<void*, size_t>> duty, learnt;
+  size_t duty_bytes = 0, learnt_bytes = 0;
+  for (sp_handle* h : b->members) {
     if (h->cfg.duty_period > 0.0f) {
       duty.emplace_back(h->d_duty, (size_t)h->C * 4);
       duty_bytes += align256((size_t)h->C * 4);
     }
+    learnt.emplace_back(h->d_perm, (size_t)h->C * h->S * 4);
+    if (h->d_wbits) learnt.emplace_back(h->d_wbits, (size_t)h->C * 512);
+    if (h->d_cconn) learnt.emplace_back(h->d_cconn, (size_t)h->C * ((h->S + 31u) & ~31u) / 8);
+  }
+  for (auto& d : learnt) learnt_bytes += align256(d.second);
   char* d_keep = nullptr;
-  if (duty_bytes) SP_CUDA(device_malloc((void**)&d_keep, duty_bytes));
+  bool learn_tune = n_frames >= 2 && persistent_enabled() &&
+                    device_malloc((void**)&d_keep, duty_bytes + learnt_bytes) == cudaSuccess;
+  if (!learn_tune) {
+    cudaGetLastError();  // a failed allocation is not an error here
+    d_keep = nullptr;
+    learnt.clear();
+    if (duty_bytes) SP_CUDA(device_malloc((void**)&d_keep, duty_bytes));
+  }
+  std::vector<std::pair<void*, size_t>> kept = duty;
+  kept.insert(kept.end(), learnt.begin(), learnt.end());
   size_t off = 0;
-  for (auto& d : duty) {
+  for (auto& d : kept) {
     SP_CUDA(cudaMemcpyAsync(d_keep + off, d.first, d.second, cudaMemcpyDeviceToDevice, b->stream));
     off += align256(d.second);
   }
@@ -2110,6 +2128,8 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
         r.frames = d_frames;
         r.stride = stride;
         r.cur0 = (uint32_t)b->cur;
+        r.pending0 = 0u;  // every timing run starts with nothing pending
+        r.learn = learn_tune ? 1u : 0u;
         r.epoch = 0u;
         r.work = static_cast<unsigned long long*>(b->d_sync);
         r.abort = reinterpret_cast<uint32_t*>(static_cast<char*>(b->d_sync) + 8);
@@ -2210,14 +2230,16 @@ SP_API sp_status sp_batch_autotune(sp_batch* b, const uint32_t* d_frames, uint32
     for (size_t i = 0; i < n; ++i)
       if (bucket[i] == k) cpw[i] = keep;
   }
-  if (s == SP_OK) s = batch_relayout(b, cpw);
   off = 0;
-  for (auto& d : duty) {
+  for (auto& d : kept) {
     cudaMemcpyAsync(d.first, d_keep + off, d.second, cudaMemcpyDeviceToDevice, b->stream);
     off += align256(d.second);
   }
   cudaStreamSynchronize(b->stream);
   if (d_keep) cudaFree(d_keep);
+  // the final split after the state is back, so that forms derived from the
+  // permanences (a compact form a split needs) derive from the kept ones
+  if (s == SP_OK) s = batch_relayout(b, cpw);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s == SP_OK && cols_per_warp) {

@@ -258,19 +258,27 @@ def test_batch_rejects_bad_members():
 
 
 def test_batch_autotune_keeps_state():
-    """Autotuning times inference frames on every candidate split and keeps
-    the fastest; permanences, learning and duty cycles continue exactly as
-    if it had not run (oracle over the real frames only)."""
+    """Autotuning times learning frames on every candidate (schedules and
+    splits) and keeps the fastest; it puts back what the learning wrote, so
+    permanences, window and compact forms, learning and duty cycles continue
+    exactly as if it had not run (oracle over the real frames only).
+    Window-form, compact-form and full-form members."""
     import oracle
     from helpers import oracle_params
     cases = [wl.frame_case(seed=wl.BASE_SEED + 500 + i) for i in range(2)]
     unv, dens = wl.uneven_cases(3, c_range=(200, 900), n_in_range=(512, 4096))
     cases += unv
+    rag = wl.Case("ragged", 1000, 1, 300, 17, synth.pool_uniform(3, 300, 17, 1000),
+                  synth.perm_uniform(4, (300, 17), 0.1, 0.3), np.ones(300, np.float32),
+                  k=9, min_overlap=2)
+    cases.append(rag)
     period = 25.0
     real = [wl.blob_frames(6, seed=wl.BASE_SEED + 500 + i) for i in range(2)]
     real += [wl.bernoulli_frames(i, c.n_in, dens[i], 6) for i, c in enumerate(unv)]
+    real.append(wl.bernoulli_frames(7, rag.n_in, 0.3, 6))
     tune = [wl.blob_frames(3, seed=wl.BASE_SEED + 520 + i) for i in range(2)]
     tune += [wl.bernoulli_frames(i, c.n_in, dens[i], 3, start=100) for i, c in enumerate(unv)]
+    tune.append(wl.bernoulli_frames(8, rag.n_in, 0.3, 3))
     hs = [spg.sp_create_from_state(c.config(duty_period=period), c.idx, c.perm, c.boost)
           for c in cases]
     b = spg.sp_batch_create(hs)
