@@ -206,6 +206,22 @@ def test_tie_stress_global(seq_path):
     np.testing.assert_array_equal(np.flatnonzero(act[-1]), np.arange(40))
 
 
+@pytest.mark.parametrize("k", [300, 700])
+def test_wide_overlap_spread_global(k, seq_path):
+    """Columns from never to always connected (each column's permanence range
+    is shifted by its index), so a frame's overlaps spread over about a
+    hundred values and the k-th largest lies several 32-value rounds below the
+    largest: the cluster path's decision reads the CTAs' count histograms
+    round by round from the top."""
+    C, S, n = 1024, 256, 4096
+    idx = synth.pool_uniform(synth.derive_seed(91, 1, 0), C, S, n)
+    u = synth.perm_uniform(synth.derive_seed(91, 2, 0), (C, S), 0.0, 0.2)
+    perm = (u + np.linspace(0.0, 0.4, C, dtype=np.float32)[:, None]).astype(np.float32)
+    case = wl.Case("spread", n, 1, C, S, idx, perm, np.ones(C, np.float32), k=k, min_overlap=1)
+    act = assert_same(case, _bern(12, n, 0.5, 10), True, f"spread k={k} {seq_path}")
+    assert (act.sum(axis=1) == k).all()
+
+
 def test_local_inhibition_non_square_grid_and_radius_zero(seq_path):
     for gw, gh, r, k in ((40, 25, 3, 5), (33, 7, 0, 1), (16, 16, 20, 9)):
         C = gw * gh
