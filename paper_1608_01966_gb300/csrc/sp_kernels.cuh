@@ -56,6 +56,8 @@ struct StepArgs {
   uint32_t min_overlap, k;
   uint32_t inhibition;       // 0 global, 1 local
   uint32_t gw, gh, radius;   // column grid for local inhibition
+  uint32_t learn_next;       // 1: the SP's next frame learns this frame's winners, so
+                             // the last CTA asks L2 for their indices and permanences
 };
 
 // One SP of a batch (device-resident descriptor; pointers into its handle).

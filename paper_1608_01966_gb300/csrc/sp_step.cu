@@ -271,6 +271,17 @@ __device__ void last_cta_inhibit(const StepArgs& a, uint32_t* sv, uint32_t* smas
   }
   __syncthreads();
   if (t == 0u) a.result[0] = total;
+  if (a.learn_next) {
+    // the SP's next frame learns these winners first thing: ask L2 for their
+    // pool indices and permanences now
+    const uint32_t lines = (a.S * 4u + 127u) / 128u;
+    for (uint32_t i = t; i < C; i += kStepThreads)
+      if ((smask[i >> 5] >> (i & 31u)) & 1u)
+        for (uint32_t l = 0; l < lines; ++l) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.idx + (uint64_t)i * a.S + 32u * l));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.perm + (uint64_t)i * a.S + 32u * l));
+        }
+  }
   if (a.hist)
     for (uint32_t b = t; b <= a.S; b += kStepThreads) a.hist[b] = 0u;
   for (uint32_t i = t; i < a.mask_words; i += kStepThreads) {
@@ -907,6 +918,7 @@ __global__ void __launch_bounds__(kStepThreads, SP_BATCH_MIN_BLOCKS) sp_batch_st
   const uint32_t inst = __ldg(ba.cta_inst + blockIdx.x);
   const BatchDesc& d = ba.desc[inst];
   StepArgs a;
+  a.learn_next = 0u;
   a.idx = d.idx;
   a.perm = d.perm;
   a.boost = d.boost;
@@ -1056,6 +1068,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) sp_batch_run_kernel(const 
       if (!s_go) return;
     }
     StepArgs a;
+    a.learn_next = r.learn;
     const uint32_t cur = r.cur0 ^ (t & 1u);
     const uint32_t pending = t > 0u ? r.learn : r.pending0;
     const uint32_t save = t + 1u == r.n_frames ? 1u : 0u;
